@@ -1,0 +1,512 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed form,
+a symbolic evaluation of Eq. (1), an exact amplification factor of the
+two-step Lax-Wendroff scheme (Eqs. 3-4), a published quasinormal frequency,
+a symmetry, or a convergence rate.  No GPU is needed.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1206_0270_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Tortoise coordinate
+# ---------------------------------------------------------------------------
+
+def test_tortoise_schwarzschild_closed_form():
+    # a = 0: r* = r + 2 ln(r/2 - 1) (the constant fixed by the reading).
+    for r in [2.001, 2.5, 3.0, 6.0, 10.0, 100.0, 1000.0]:
+        assert O.rstar_of_r(r, 0.0) == pytest.approx(r + 2.0 * math.log(r / 2.0 - 1.0), rel=1e-14, abs=1e-13)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.3, 0.7, 0.9, 0.99])
+def test_tortoise_inverse_and_derivative(a):
+    rp = 1.0 + math.sqrt(1.0 - a * a)
+    for rs in [-20.0, -5.0, 0.0, 1.6, 10.0, 100.0, 600.0, 3000.0]:
+        r, D = O.r_of_rstar(rs, a)
+        assert O.rstar_of_r(r, a) == pytest.approx(rs, abs=1e-9 * max(1.0, abs(rs)))
+        assert D == pytest.approx(r * r - 2 * r + a * a, rel=1e-9)
+        # d r*/dr = (r^2 + a^2) / Delta, by a centred difference of the forward map
+        eps = 1e-4 * (r - rp)
+        r1, r2 = r + eps, r - eps
+        num = (O.rstar_of_r(r1, a) - O.rstar_of_r(r2, a)) / (r1 - r2)
+        assert num == pytest.approx((r * r + a * a) / D, rel=1e-6)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9])
+def test_tortoise_deep_near_horizon(a):
+    # For x = r - r+ -> 0:  r* -> r+ + k+ ln(x/2) - k- ln((r+ - r-)/2), so
+    # x = 2 exp((r* - r+ + k- ln((r+ - r-)/2)) / k+) and Delta -> x (r+ - r-).
+    q = math.sqrt(1 - a * a)
+    rp, rm = 1 + q, 1 - q
+    kp, km = 2 * rp / (rp - rm), 2 * rm / (rp - rm)
+    for rs in [-100.0, -300.0]:
+        x = 2 * math.exp((rs - rp + km * math.log((rp - rm) / 2)) / kp)
+        r, D = O.r_of_rstar(rs, a)
+        assert D == pytest.approx(x * (rp - rm), rel=1e-9)
+        assert D > 0
+
+
+# ---------------------------------------------------------------------------
+# Coefficients of the first-order system against Eq. (1), symbolically
+# ---------------------------------------------------------------------------
+
+def _eq1_residual_checker(a_val, s_val, m_val):
+    sp = pytest.importorskip("sympy")
+    mpmath = pytest.importorskip("mpmath")
+    t, r, th, ph = sp.symbols("t r theta phi", real=True)
+    a = sp.nsimplify(a_val)
+    s, m = sp.Integer(s_val), sp.Integer(m_val)
+    Mbh = 1
+    Delta = r ** 2 - 2 * Mbh * r + a ** 2
+    omega = sp.Rational(3, 10) - sp.Rational(1, 20) * sp.I
+    # a smooth test field Phi(t, r, theta)
+    Phi = (sp.exp(-sp.I * omega * t) * sp.exp(-(r - 7) ** 2 / 9)
+           * (1 + sp.cos(th)) ** 2 * (1 + sp.sin(th) / 3 + sp.cos(th) / 5))
+    Psi = sp.exp(sp.I * m * ph) * r ** 3 * Phi                     # Eq. (2)
+    E1 = (-((r ** 2 + a ** 2) ** 2 / Delta - a ** 2 * sp.sin(th) ** 2) * sp.diff(Psi, t, 2)
+          - 4 * Mbh * a * r / Delta * sp.diff(Psi, t, ph)
+          - 2 * s * (r - Mbh * (r ** 2 - a ** 2) / Delta + sp.I * a * sp.cos(th)) * sp.diff(Psi, t)
+          + Delta ** (-s) * sp.diff(Delta ** (s + 1) * sp.diff(Psi, r), r)
+          + 1 / sp.sin(th) * sp.diff(sp.sin(th) * sp.diff(Psi, th), th)
+          + (1 / sp.sin(th) ** 2 - a ** 2 / Delta) * sp.diff(Psi, ph, 2)
+          + 2 * s * (a * (r - Mbh) / Delta + sp.I * sp.cos(th) / sp.sin(th) ** 2) * sp.diff(Psi, ph)
+          - (s ** 2 * sp.cot(th) ** 2 - s) * Psi)                      # Eq. (1), T = 0
+    # normalise so that the coefficient of Phi_tt is +1
+    norm = 1 / ((r ** 2 + a ** 2) ** 2 / Delta - a ** 2 * sp.sin(th) ** 2)
+    target = -norm * E1 * sp.exp(-sp.I * m * ph) / r ** 3
+    drs = lambda f: Delta / (r ** 2 + a ** 2) * sp.diff(f, r)    # d/dr* from the tortoise map
+    ex = dict(Phi=Phi, Phi_t=sp.diff(Phi, t), Phi_tt=sp.diff(Phi, t, 2), Phi_rs=drs(Phi),
+              Phi_rsrs=drs(drs(Phi)), Phi_trs=drs(sp.diff(Phi, t)), Phi_th=sp.diff(Phi, th),
+              Phi_thth=sp.diff(Phi, th, 2))
+    fns = {k: sp.lambdify((t, r, th), v, "mpmath") for k, v in ex.items()}
+    ftarget = sp.lambdify((t, r, th, ph), target, "mpmath")
+    mpmath.mp.dps = 30
+
+    def check(tv, rv, thv):
+        D = rv * rv - 2 * rv + a_val * a_val
+        c = O.coefficients(rv, D, thv, a_val, s_val, m_val)
+        v = {k: complex(f(tv, rv, thv)) for k, f in fns.items()}
+        b = c["b"]
+
+        def bof(rr):
+            return O.coefficients(rr, rr * rr - 2 * rr + a_val * a_val, thv, a_val, s_val, m_val)["b"]
+        # d b / d r* by a fourth-order centred difference of the oracle's own b
+        e = 1e-3
+        dbdr = (8 * (bof(rv + e) - bof(rv - e)) - (bof(rv + 2 * e) - bof(rv - 2 * e))) / (12 * e)
+        dbdrs = D / (rv * rv + a_val * a_val) * dbdr
+        Pi = v["Phi_t"] + b * v["Phi_rs"]
+        Pi_t = v["Phi_tt"] + b * v["Phi_trs"]
+        Pi_rs = v["Phi_trs"] + dbdrs * v["Phi_rs"] + b * v["Phi_rsrs"]
+        Lth = v["Phi_thth"] + math.cos(thv) / math.sin(thv) * v["Phi_th"]
+        # the oracle's system:  Pi_t - d Phi_{r*} - b Pi_{r*} + c_t Pi + W Phi - kappa L Phi = source
+        lhs = Pi_t - c["d"] * v["Phi_rs"] - b * Pi_rs + c["ct"] * Pi + c["W"] * v["Phi"] - c["kappa"] * Lth
+        tgt = complex(ftarget(tv, rv, thv, 0.0))
+        return lhs, tgt
+    return check
+
+
+@pytest.mark.parametrize("a,s,m", [(0.9, -2, 2), (0.5, 2, -1), (0.0, -2, 2), (0.7, 0, 3), (0.3, -2, 1)])
+def test_coefficients_reproduce_eq1(a, s, m):
+    check = _eq1_residual_checker(a, s, m)
+    for (tv, rv, thv) in [(0.3, 3.1, 0.7), (1.1, 6.0, 2.0), (0.0, 2.4, 1.3), (0.5, 15.0, 2.9)]:
+        lhs, tgt = check(tv, rv, thv)
+        assert abs(lhs - tgt) <= 1e-9 * max(abs(tgt), 1e-30), (rv, thv, lhs, tgt)
+
+
+def test_coefficients_horizon_and_infinity_limits():
+    # At the horizon (Delta = 0): b = 1, kappa = 0 and the local operator is
+    # (d_t + i m Omega_H)^2 for s = 0, i.e. c_t = 2 i m Omega_H, W = -(m Omega_H)^2,
+    # Omega_H = a / (2 r+).
+    a, m = 0.8, 3
+    rp = 1 + math.sqrt(1 - a * a)
+    c = O.coefficients(rp, 0.0, 1.1, a, 0, m)
+    OmH = a / (2 * rp)
+    assert c["b"] == pytest.approx(1.0, rel=1e-15)
+    assert c["kappa"] == 0.0
+    assert c["ct"] == pytest.approx(2j * m * OmH, rel=1e-14)
+    assert c["W"] == pytest.approx(-(m * OmH) ** 2, rel=1e-14)
+    # Far away: b -> 1, kappa ~ 1/r^2
+    r = 1e5
+    c = O.coefficients(r, r * r - 2 * r + a * a, 0.9, a, -2, 2)
+    assert c["b"] == pytest.approx(1.0, abs=1e-9)
+    assert c["kappa"] * r * r == pytest.approx(1.0, rel=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# Angular operator: second-order centred differences are exact on quadratics
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nth", [8, 33, 64])
+def test_angular_operator_exact_on_quadratics(nth):
+    th = inputs.theta_grid(nth)
+    cot = np.cos(th) / np.sin(th)
+    # Even about theta = 0 (parity +1 ghost is exact there): theta^2 -> 2 + 2 theta cot
+    out = O.angular_op(th ** 2 + 0j, +1)
+    ok = slice(0, nth - 1)   # the theta = pi ghost is not exact for theta^2
+    np.testing.assert_allclose(out[ok].real, (2 + 2 * th * cot)[ok], rtol=1e-11, atol=1e-9)
+    # Odd about theta = 0 (parity -1): theta -> cot
+    out = O.angular_op(th + 0j, -1)
+    np.testing.assert_allclose(out[ok].real, cot[ok], rtol=1e-11, atol=1e-9)
+    # Even about theta = pi: (theta - pi)^2
+    out = O.angular_op((th - np.pi) ** 2 + 0j, +1)
+    ok2 = slice(1, nth)
+    np.testing.assert_allclose(out[ok2].real, (2 + 2 * (th - np.pi) * cot)[ok2], rtol=1e-11, atol=1e-9)
+    # Odd about theta = pi: theta - pi
+    out = O.angular_op(1j * (th - np.pi), -1)
+    np.testing.assert_allclose(out[ok2].imag, cot[ok2], rtol=1e-11, atol=1e-9)
+    # A constant is annihilated exactly with the even (d Phi/d theta = 0) rule.
+    out = O.angular_op(np.full(nth, 3.0 - 2.0j), +1)
+    assert np.all(out == 0)
+
+
+# ---------------------------------------------------------------------------
+# Eqs. (3)-(4): exact amplification matrix for constant coefficients
+# ---------------------------------------------------------------------------
+
+def _lw_amplification(k, h, dt, b, d, ct, W):
+    """Closed-form one-step amplification of the two-step Lax-Wendroff scheme
+    for u_t + D u_x = Lambda u with constant D = [[b,0],[-d,-b]],
+    Lambda = [[0,1],[-W,-ct]], on a Fourier mode e^{ikx}:
+      P = cos(kh/2)(I + dt/2 Lambda) - (dt/h) i sin(kh/2) D          (predictor)
+      G = I - dt [ (2 i sin(kh/2)/h) D - cos(kh/2) Lambda ] P        (corrector)"""
+    D = np.array([[b, 0], [-d, -b]], dtype=complex)
+    L = np.array([[0, 1], [-W, -ct]], dtype=complex)
+    I2 = np.eye(2)
+    c, s = math.cos(k * h / 2), math.sin(k * h / 2)
+    P = c * (I2 + dt / 2 * L) - (dt / h) * 1j * s * D
+    return I2 - dt * ((2j * s / h) * D - c * L) @ P
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lax_wendroff_exact_fourier_amplification(seed):
+    rng = np.random.default_rng(seed)
+    nr, nth, nsteps = 120, 4, 12
+    h, dt = 0.1, 0.07
+    b = rng.uniform(0.6, 1.2)
+    d, ct, W = (complex(rng.normal(), rng.normal()) * 0.5 for _ in range(3))
+    k = rng.uniform(0.5, 20.0)
+    uhat = np.array([complex(rng.normal(), rng.normal()), complex(rng.normal(), rng.normal())])
+    x = h * np.arange(nr)
+    Phi = np.repeat((uhat[0] * np.exp(1j * k * x))[:, None], nth, axis=1)
+    Pi = np.repeat((uhat[1] * np.exp(1j * k * x))[:, None], nth, axis=1)
+    full = lambda v, rows: np.full((rows, nth), v)
+    fields = dict(b_node=full(b, nr), b_mid=full(b, nr - 1), d_node=full(d, nr), d_mid=full(d, nr - 1),
+                  ct_node=full(ct, nr), ct_mid=full(ct, nr - 1), W_node=full(W, nr), W_mid=full(W, nr - 1),
+                  kap_node=full(0.37, nr), kap_mid=full(0.37, nr - 1),
+                  cot=np.cos(inputs.theta_grid(nth)) / np.sin(inputs.theta_grid(nth)))
+    for _ in range(nsteps):
+        Phi, Pi = O.lw_step_generic(Phi, Pi, h=h, dt=dt, parity=+1, **fields)
+    G = np.linalg.matrix_power(_lw_amplification(k, h, dt, b, d, ct, W), nsteps)
+    expect = G @ uhat
+    # points outside the boundaries' domain of influence (one point per step)
+    sel = slice(nsteps + 1, nr - 1 - nsteps)
+    ph = np.exp(1j * k * x[sel])
+    for j in range(nth):
+        np.testing.assert_allclose(Phi[sel, j], expect[0] * ph, rtol=1e-12, atol=1e-12 * abs(expect).max())
+        np.testing.assert_allclose(Pi[sel, j], expect[1] * ph, rtol=1e-12, atol=1e-12 * abs(expect).max())
+    # radial boundary rows are exactly zero
+    assert np.all(Phi[0] == 0) and np.all(Phi[-1] == 0) and np.all(Pi[0] == 0) and np.all(Pi[-1] == 0)
+
+
+def test_lax_wendroff_source_enters_pi_row():
+    # With D = 0, Lambda = 0 and a constant profile G, one step adds exactly
+    # dt * G * phase_half to Pi at interior nodes (Eq. 4 with S = F) and leaves Phi
+    # changed only by dt/2 * dt * G * phase_n (the predictor's Pi feeds S_Phi = Pi).
+    nr, nth = 10, 3
+    z = lambda rows: np.zeros((rows, nth))
+    zc = lambda rows: np.zeros((rows, nth), complex)
+    G = 0.8
+    ph_n, ph_h = np.exp(-0.3j), np.exp(-0.45j)
+    dt = 0.2
+    Phi, Pi = O.lw_step_generic(zc(nr), zc(nr), h=0.1, dt=dt, parity=1, b_node=z(nr), b_mid=z(nr - 1),
+                                d_node=zc(nr), d_mid=zc(nr - 1), ct_node=zc(nr), ct_mid=zc(nr - 1),
+                                W_node=zc(nr), W_mid=zc(nr - 1), kap_node=z(nr), kap_mid=z(nr - 1),
+                                cot=np.ones(nth), G_node=np.full((nr, nth), G),
+                                G_mid=np.full((nr - 1, nth), G), phase_n=ph_n, phase_half=ph_h)
+    np.testing.assert_allclose(Pi[1:-1], dt * G * ph_h, rtol=1e-14)
+    np.testing.assert_allclose(Phi[1:-1], dt * (dt / 2) * G * ph_n, rtol=1e-14)
+
+
+def test_solver_uses_time_levels_of_eqs_3_and_4():
+    # Eq. (3) evaluates S at time level n, Eq. (4) at n + 1/2: the source phase
+    # e^{-i m Omega t} enters the predictor at t_n and the corrector at
+    # t_n + dt/2.  The solver must equal the (pinned) generic step driven with
+    # its own coefficient fields and those phases.
+    nr, nth, a, s, m = 60, 8, 0.7, -2, 3
+    rmin, rmax = -10.0, 30.0
+    dt = 0.05
+    S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    phi, pi = inputs.random_fields(nr, nth, seed=4)
+    S.set_initial(phi, pi)
+    S.set_source(r0=6.0, sigma=1.0, amplitude=3.0)
+    cn, cm = S.coefficient_fields(), S.coefficient_fields(mid=True)
+    Gn, Gm = S.source_profile(), S.source_profile(mid=True)
+    th = inputs.theta_grid(nth)
+    Om = O.orbit_omega(6.0, a, True)
+    P, Q = S.state()
+    for n in range(3):
+        t_n = n * dt
+        P, Q = O.lw_step_generic(P, Q, h=(rmax - rmin) / (nr - 1), dt=dt, parity=-1,
+                                 b_node=cn["b"], b_mid=cm["b"], d_node=cn["d"], d_mid=cm["d"],
+                                 ct_node=cn["ct"], ct_mid=cm["ct"], W_node=cn["W"], W_mid=cm["W"],
+                                 kap_node=cn["kappa"], kap_mid=cm["kappa"], cot=np.cos(th) / np.sin(th),
+                                 G_node=Gn, G_mid=Gm, phase_n=np.exp(-1j * m * Om * t_n),
+                                 phase_half=np.exp(-1j * m * Om * (t_n + dt / 2)))
+    S.step(3)
+    P2, Q2 = S.state()
+    np.testing.assert_allclose(P2, P, rtol=0, atol=1e-13 * abs(P).max())
+    np.testing.assert_allclose(Q2, Q, rtol=0, atol=1e-13 * abs(Q).max())
+
+
+# ---------------------------------------------------------------------------
+# Source and orbit
+# ---------------------------------------------------------------------------
+
+def test_orbit_frequency():
+    for r0 in [6.0, 10.0, 37.5]:
+        assert O.orbit_omega(r0, 0.0, True) == pytest.approx(r0 ** -1.5, rel=1e-15)  # Kepler, exact at a = 0
+        assert O.orbit_omega(r0, 0.0, False) == pytest.approx(-(r0 ** -1.5), rel=1e-15)
+        # reversing both the spin and the orbit direction mirrors the motion
+        assert O.orbit_omega(r0, 0.6, True) == pytest.approx(-O.orbit_omega(r0, -0.6, False), rel=1e-15)
+    # large radius: Newtonian limit
+    assert O.orbit_omega(1e6, 0.9, True) * 1e9 == pytest.approx(1.0, rel=1e-8)
+
+
+def test_source_normalisation_and_support():
+    nr, nth = 401, 64
+    S = O.Solver(nr, nth, -50.0, 150.0, 0.01, 0.9, -2, 2)
+    S.set_source(r0=10.0, sigma=0.4, amplitude=2.5)
+    G = S.source_profile()
+    h, dth = 200.0 / (nr - 1), math.pi / nth
+    assert G.sum() * h * dth == pytest.approx(2.5, rel=1e-13)
+    rs0 = O.rstar_of_r(10.0, 0.9)
+    i0 = int(round((rs0 + 50.0) / h))
+    assert np.unravel_index(np.argmax(G), G.shape)[0] in (i0 - 1, i0, i0 + 1)
+    # symmetric about the equator up to rounding of theta_j
+    np.testing.assert_allclose(G, G[:, ::-1], rtol=1e-9, atol=1e-12 * G.max())
+    # compact support (exponent cut at 50)
+    assert np.count_nonzero(G) < 0.05 * G.size
+
+
+def test_forced_steady_state_frequency():
+    # Once the switch-on transients have left, the field oscillates as
+    # e^{-i m Omega t}.  s = 0 settles within ~40M; the outer-boundary
+    # reflection reaches the observer after ~110M.
+    a, s, m, r0 = 0.5, 0, 2, 6.0
+    nr, nth = 481, 16
+    rmin, rmax = -40.0, 80.0
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
+    S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    S.set_initial(np.zeros((nr, nth), complex))
+    S.set_source(r0=r0, sigma=1.0)
+    every = 20
+    S.set_extraction(20.0, every)
+    S.step(int(105.0 / dt))
+    t, phi = S.samples()
+    late = (t > 55.0) & (t < 105.0)
+    z = phi[late, nth // 2 - 1]
+    Om = O.orbit_omega(r0, a, True)
+    # the phase advances at -m Omega
+    slope = np.polyfit(t[late], np.unwrap(np.angle(z)), 1)[0]
+    assert slope == pytest.approx(-m * Om, rel=2e-3)
+    # and the amplitude is steady
+    assert np.ptp(abs(z)) < 0.05 * abs(z).mean()
+
+
+# ---------------------------------------------------------------------------
+# Symmetries, linearity, limits
+# ---------------------------------------------------------------------------
+
+def test_m_reflection_symmetry():
+    # Eq. (1) maps onto itself under m -> -m, theta -> pi - theta and complex
+    # conjugation, so Phi_{-m}(t, r, theta) = conj Phi_m(t, r, pi - theta) for
+    # reflected, conjugated data and source.
+    nr, nth, a, s, m = 121, 16, 0.7, -2, 2
+    rmin, rmax = -20.0, 40.0
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
+    phi0, pi0 = inputs.random_fields(nr, nth, seed=11)
+    A = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    B = O.Solver(nr, nth, rmin, rmax, dt, a, s, -m)
+    A.set_initial(phi0, pi0)
+    B.set_initial(np.conj(phi0[:, ::-1]), np.conj(pi0[:, ::-1]))
+    A.set_source(r0=8.0, sigma=0.5)
+    B.set_source(r0=8.0, sigma=0.5)
+    A.step(300)
+    B.step(300)
+    pa, qa = A.state()
+    pb, qb = B.state()
+    scale = max(abs(pa).max(), abs(qa).max())
+    assert abs(pb - np.conj(pa[:, ::-1])).max() <= 1e-11 * scale
+    assert abs(qb - np.conj(qa[:, ::-1])).max() <= 1e-11 * scale
+
+
+def test_linearity_and_superposition():
+    nr, nth, a, s, m = 101, 8, 0.9, -2, 1
+    rmin, rmax = -20.0, 40.0
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
+    u1 = inputs.random_fields(nr, nth, seed=1)
+    u2 = inputs.random_fields(nr, nth, seed=2)
+
+    def run(u, amp):
+        S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+        S.set_initial(*u)
+        if amp:
+            S.set_source(r0=7.0, sigma=0.5, amplitude=amp)
+        S.step(150)
+        return S.state()
+    p1, q1 = run(u1, 1.0)
+    p2, q2 = run((2 * u1[0], 2 * u1[1]), 2.0)
+    assert np.array_equal(p2, 2 * p1) and np.array_equal(q2, 2 * q1)   # scaling by 2 is exact
+    pa, qa = run(u1, 0.0)
+    pb, qb = run(u2, 1.0)
+    pc, qc = run((u1[0] + u2[0], u1[1] + u2[1]), 1.0)
+    sc = abs(pc).max()
+    assert abs(pc - (pa + pb)).max() <= 1e-12 * sc
+    assert abs(qc - (qa + qb)).max() <= 1e-12 * abs(qc).max()
+
+
+def test_kerr_terms_switch_off_continuously():
+    nr, nth, s, m = 101, 8, -2, 2
+    rmin, rmax = -20.0, 40.0
+    dt = O.stable_dt(nr, nth, rmin, rmax, 0.0, s, m)
+    u = inputs.random_fields(nr, nth, seed=5)
+    out = []
+    for a in [0.0, 1e-7]:
+        S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+        S.set_initial(*u)
+        S.step(100)
+        out.append(S.state()[0])
+    rel = abs(out[1] - out[0]).max() / abs(out[0]).max()
+    assert 1e-12 < rel < 1e-5
+
+
+def test_radial_boundary_rows_stay_zero():
+    nr, nth = 64, 8
+    dt = O.stable_dt(nr, nth, -10.0, 20.0, 0.5, 2, 3)
+    S = O.Solver(nr, nth, -10.0, 20.0, dt, 0.5, 2, 3)
+    S.set_initial(*inputs.random_fields(nr, nth, seed=3))
+    S.set_source(r0=5.0, sigma=0.5)
+    S.step(50)
+    p, q = S.state()
+    for X in (p, q):
+        assert np.all(X[0] == 0) and np.all(X[-1] == 0)
+
+
+def test_time_step_rule_matches_limits():
+    # a = 0: b = 1 exactly, so the radial limit is c_r h.
+    nr, nth = 257, 8
+    h = 100.0 / (nr - 1)
+    assert O.stable_dt(nr, nth, -50.0, 50.0, 0.0, -2, 2, c_r=0.5, c_theta=1e9) == pytest.approx(0.5 * h, rel=1e-15)
+    # the angular limit scales like dtheta as nth doubles (pole term dominates)
+    d1 = O.stable_dt(nr, 32, -50.0, 50.0, 0.0, -2, 2, c_r=1e9, c_theta=0.1)
+    d2 = O.stable_dt(nr, 64, -50.0, 50.0, 0.0, -2, 2, c_r=1e9, c_theta=0.1)
+    assert 1.9 < d1 / d2 < 2.1
+
+
+def test_bounded_evolution_with_source():
+    # s = 0 (no r^3-weighted growth of ingoing waves): with a persistent source
+    # the field settles to a bounded, periodic state (h = M/4; see the
+    # time-step rule: at h = M/4 a light-ring-trapped mode grows slowly).
+    nr, nth = 1201, 16
+    rmin, rmax = -50.0, 100.0
+    dt = O.stable_dt(nr, nth, rmin, rmax, 0.9, 0, 2)
+    S = O.Solver(nr, nth, rmin, rmax, dt, 0.9, 0, 2)
+    S.set_initial(np.zeros((nr, nth), complex))
+    S.set_source(r0=8.0, sigma=0.5)
+    S.step(int(125 / dt))
+    p1 = abs(S.state()[0]).max()
+    S.step(int(100 / dt))
+    p2 = abs(S.state()[0]).max()
+    assert np.isfinite(p2) and p2 < 1.5 * p1
+
+
+# ---------------------------------------------------------------------------
+# Convergence and physics
+# ---------------------------------------------------------------------------
+
+def test_second_order_convergence():
+    a, s, m = 0.5, -2, 2
+    rmin, rmax, T, rs_obs = -40.0, 60.0, 16.0, 10.0
+    levels = [(201, 8), (401, 16), (801, 32)]
+    dt_f = O.stable_dt(*levels[-1], rmin, rmax, a, s, m)
+    n_f = int(math.ceil(T / dt_f / 4)) * 4
+    dt_f = T / n_f
+    Q = []
+    for lvl, (nr, nth) in enumerate(levels):
+        fac = 2 ** (2 - lvl)
+        S = O.Solver(nr, nth, rmin, rmax, dt_f * fac, a, s, m)
+        S.set_initial(inputs.gaussian_pulse(nr, nth, rmin, rmax, s, m, center=15.0, width=4.0))
+        S.step(n_f // fac)
+        phi = S.state()[0]
+        th = inputs.theta_grid(nth)
+        i = int(round((rs_obs - rmin) / ((rmax - rmin) / (nr - 1))))
+        Q.append(np.sum(phi[i] * np.sin(th)) * (math.pi / nth))
+    ratio = abs(Q[0] - Q[1]) / abs(Q[1] - Q[2])
+    assert 3.4 < ratio < 4.6, (ratio, Q)
+
+
+def test_second_order_convergence_with_source():
+    # Zero initial data driven by the Gaussian source: the same rate 4 must hold,
+    # which needs the corrector's source at t_n + dt/2 (a source frozen at t_n
+    # is first order in time).  A fast orbit (r0 = 4M) makes the time level matter.
+    a, s, m, r0, sigma = 0.5, -2, 2, 4.0, 2.0
+    rmin, rmax, T, rs_obs = -40.0, 60.0, 12.0, 14.0
+    levels = [(201, 16), (401, 32), (801, 64)]
+    dt_f = O.stable_dt(*levels[-1], rmin, rmax, a, s, m)
+    n_f = int(math.ceil(T / dt_f / 4)) * 4
+    dt_f = T / n_f
+    Q = []
+    for lvl, (nr, nth) in enumerate(levels):
+        fac = 2 ** (2 - lvl)
+        S = O.Solver(nr, nth, rmin, rmax, dt_f * fac, a, s, m)
+        S.set_initial(np.zeros((nr, nth), complex))
+        S.set_source(r0=r0, sigma=sigma)
+        S.step(n_f // fac)
+        phi = S.state()[0]
+        th = inputs.theta_grid(nth)
+        i = int(round((rs_obs - rmin) / ((rmax - rmin) / (nr - 1))))
+        Q.append(np.sum(phi[i] * np.sin(th)) * (math.pi / nth))
+    ratio = abs(Q[0] - Q[1]) / abs(Q[1] - Q[2])
+    assert 3.4 < ratio < 4.6, (ratio, Q)
+
+
+def _fit_damped(t, y):
+    from scipy.optimize import least_squares
+    t0 = t[0]
+
+    def res(p):
+        A, g, w, ph = p
+        return A * np.exp(-g * (t - t0)) * np.cos(w * t + ph) - y
+    best = None
+    for ph0 in np.linspace(0, 2 * np.pi, 8, endpoint=False):
+        r = least_squares(res, [abs(y).max(), 0.09, 0.37, ph0])
+        if best is None or r.cost < best.cost:
+            best = r
+    return best.x[2], best.x[1]
+
+
+def test_schwarzschild_l2_quasinormal_ringdown():
+    re_w, im_w = np.loadtxt(os.path.join(GOLDEN, "qnm_schwarzschild_l2.txt"))
+    s, m = -2, 2
+    nr, nth, rmin, rmax = 1301, 16, -60.0, 200.0
+    dt = O.stable_dt(nr, nth, rmin, rmax, 0.0, s, m)
+    S = O.Solver(nr, nth, rmin, rmax, dt, 0.0, s, m)
+    S.set_initial(inputs.gaussian_pulse(nr, nth, rmin, rmax, s, m, center=10.0, width=2.0))
+    S.set_extraction(50.0, max(1, int(round(0.5 / dt))))
+    S.step(int(145.0 / dt))
+    t, phi = S.samples()
+    y = phi[:, 0].real
+    assert np.all(np.abs(phi[:, 0].imag) == 0)     # real data and real coefficients at a = 0
+    sel = (t >= 90.0) & (t <= 140.0)
+    w, g = _fit_damped(t[sel], y[sel])
+    assert w == pytest.approx(re_w, rel=5e-3)
+    assert g == pytest.approx(-im_w, rel=3e-2)
