@@ -1,0 +1,314 @@
+"""Benchmark: FP64 grid-point updates/s of the time-domain Teukolsky step on GB300.
+
+Workload: Kerr a = 0.9M, s = -2, m = 2, grid 8192 r* x 128 theta,
+r* in [-100M, 600M], circular equatorial orbit r0 = 10M with a Gaussian source
+of width 0.05M, waveform sampled at r* = 500M every 10 steps, FP64.  One
+benchmark step = `--chunk` time steps of Eqs. (3)-(4) (graph replays of the
+fused kernel), on inputs resident in HBM.  The per-step working set (state
+2 x 33.5 MB + coefficient planes 193 MB) is larger than the 129 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--chunk C] [--impl reference]
+
+Under torchrun (N > 1) every rank evolves its own copy of the workload
+(independent problems, no collective on the data path); `value` is the sum
+over ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the reference arm) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "kerr_a0.9_s-2_m2_8192x128_r0_10"
+METRIC = "FP64 grid-pt updates/s"
+UNIT = "grid-pt updates/s"
+# FP64 work of one interior point update in the folded formulation of
+# Eqs. (3)-(4): 4 adds + 4 multiplies + 52 FMAs = 60 FP64 instructions = 112 flops.
+FLOPS_PER_UPDATE = 112
+# Algorithmic HBM bytes of one point update: read u^n, write u^{n+1} (4 doubles each).
+BYTES_PER_UPDATE_ALG = 64
+# Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
+FP64_PEAK_FLOPS = 1.25e12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload():
+    from paper_1206_0270_gb300 import inputs
+    return dict(inputs.WORKLOADS[WORKLOAD])
+
+
+# ---------------------------------------------------------------------------
+# Reference arm / CPU baseline: the oracle on host cores
+# ---------------------------------------------------------------------------
+
+def oracle_rate(steps_per_sample: int, samples: int, warmup: int = 0):
+    """Time the oracle on the full 8192 x 128 grid of the workload."""
+    from oracle import oracle as O
+    w = workload()
+    dt = O.stable_dt(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"],
+                     w["c_r"], w["c_theta"])
+    S = O.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+    S.set_initial(np.zeros((w["nr"], w["nth"]), complex))
+    S.set_source(**w["source"])
+    S.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"])
+    for _ in range(warmup):
+        S.step(steps_per_sample)
+    times = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        S.step(steps_per_sample)
+        times.append(time.perf_counter() - t0)
+    upd = (w["nr"] - 2) * w["nth"] * steps_per_sample
+    return upd, times
+
+
+def cores_used():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    per = args.ref_steps
+    upd, times = oracle_rate(per, args.steps, warmup=args.warmup)
+    total = sum(times)
+    value = upd * args.steps / total
+    sample = ("FP64 C oracle (OpenMP over r* rows), 8192x128 Kerr a=0.9 grid with source, "
+              "%d time steps per benchmark step" % per)
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * total / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, nr=8192, nth=128, time_steps_per_step=per),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores_used(), kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1206_0270_gb300 import build
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_1206_0270_gb300 import teuk as T
+
+    w = workload()
+    nr, nth = w["nr"], w["nth"]
+    dt = T.stable_dt(nr, nth, w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], w["c_r"], w["c_theta"])
+    stream = torch.cuda.Stream()
+    S = T.Solver(nr, nth, w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"], stream=stream)
+    S.set_initial(np.zeros((nr, nth), complex), np.zeros((nr, nth), complex))
+    S.set_source(**w["source"])
+    ex = w["extraction"]
+    samples_per_step = args.chunk // ex["every"]
+    S.set_extraction(ex["rstar"], ex["every"], capacity=max(16, 2 * samples_per_step * (args.steps + args.warmup + 2)))
+    upd_per_step = (nr - 2) * nth * args.chunk
+
+    # ---- device-resident throughput -------------------------------------------------
+    for _ in range(args.warmup):
+        S.step(args.chunk)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            S.step(args.chunk)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    assert S.check_finite(), "state became non-finite"
+    launches = args.steps * S.launches_for(args.chunk)
+    value = ws * upd_per_step * args.steps / (total_ms / 1e3)
+
+    # ---- dominant kernel: average launch duration over the timed region --------------
+    per_launch_s = (total_ms / 1e3) / (args.steps * args.chunk)
+    upd_per_launch = (nr - 2) * nth
+    achieved = FLOPS_PER_UPDATE * upd_per_launch / per_launch_s
+    roofline = dict(bound="alu", achieved=achieved / 1e12, peak=FP64_PEAK_FLOPS / 1e12, unit="TFLOP/s",
+                    frac=achieved / FP64_PEAK_FLOPS, traffic=None,
+                    peak_source="nominal FP64 (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz)",
+                    hbm_alg_gbs=BYTES_PER_UPDATE_ALG * upd_per_launch / per_launch_s / 1e9)
+
+    # ---- end to end through the C ABI with host buffers ------------------------------
+    pin = lambda: torch.zeros((nr, nth), dtype=torch.complex128, pin_memory=True).numpy()
+    phi_h, pi_h = pin(), pin()
+    t_buf = np.zeros(samples_per_step + 1)
+    w_buf = torch.zeros((samples_per_step + 1, nth), dtype=torch.complex128, pin_memory=True).numpy()
+    E = T.Solver(nr, nth, w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"], stream=stream)
+    E.set_source(**w["source"])
+    E.set_extraction(ex["rstar"], ex["every"], capacity=samples_per_step + 1)
+    import ctypes as C
+
+    def e2e_step():
+        E.set_initial(phi_h, pi_h)           # H2D of the step's input state (pinned)
+        E.step(args.chunk)
+        n = C.c_long()
+        rc = T.teuk_extract(E.h, t_buf.ctypes.data_as(T._dp), w_buf.ctypes.data_as(T._dp), len(t_buf),
+                            C.byref(n))      # D2H of the step's waveform samples (synchronises)
+        T._check(rc, E.h, "teuk_extract")
+        return n.value
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nsamp = 0
+    for _ in range(args.steps):
+        nsamp = e2e_step()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = dict(value=ws * upd_per_step * args.steps / e2e_s, unit=UNIT,
+               h2d_bytes_per_step=2 * nr * nth * 16, d2h_bytes_per_step=nsamp * (nth * 16 + 8))
+    E.close()
+
+    if rank != 0:
+        S.close()
+        return 0
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, nr=nr, nth=nth, a=w["a"], s=w["s"], m=w["m"],
+                            rstar=[w["rstar_min"], w["rstar_max"]], dt=dt, time_steps_per_step=args.chunk,
+                            kernel="fused radial-marching, CUDA-graph replay",
+                            l2="inputs larger than L2 (state 2x33.5 MB + coefficients 193 MB per time step)",
+                            parallelism="replicas" if ws > 1 else "single GPU"),
+                roofline=roofline, e2e=e2e, gpu_launches=int(launches),
+                step_ms_min=min(step_ms), step_ms_median=statistics.median(step_ms))
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if ws == 1 and not args.no_cpu_baseline:
+        per = args.cpu_sample_steps
+        upd, times = oracle_rate(per, 1)
+        line["cpu_baseline"] = dict(value=upd / times[0], unit=UNIT, cores=cores_used(), kind="oracle",
+                                    sample="%d time steps of the 8192x128 workload grid, FP64 C oracle "
+                                           "(OpenMP over r* rows)" % per)
+    print(json.dumps(line), flush=True)
+    S.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=640, help="time steps per benchmark step")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-steps", type=int, default=10, help="oracle time steps per reference step")
+    ap.add_argument("--cpu-sample-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * teuk.h -- C ABI of the GB300 time-domain Teukolsky solver (libteuk.so).
+ *
+ * The solver advances one azimuthal mode m of the spin-weight-s Teukolsky
+ * equation on a Kerr background (McKennon, Forrester & Khanna,
+ * arXiv:1206.0270, section "Teukolsky Code"):
+ *   - Eq. (1) is the master equation; Eq. (2) factors Psi = e^{i m phi} r^3 Phi_m.
+ *   - The state is u = {Phi_R, Phi_I, Pi_R, Pi_I} (complex Phi and its
+ *     momentum Pi = d_t Phi + b d_{r*} Phi) on an (r*, theta) grid.
+ *   - One time step is the two-step Lax-Wendroff update of Eqs. (3) and (4)
+ *     with second-order centred angular differences, the pole rule (even |m|:
+ *     dPhi/dtheta = 0, odd |m|: Phi = 0) and Phi = Pi = 0 on both radial
+ *     boundaries.
+ *   - The point particle is a narrow Gaussian ("Mathematical Advances",
+ *     item 1) moving on a circular equatorial orbit; the waveform is Phi
+ *     sampled at an extraction radius.
+ * Units: black-hole mass M = 1.  All arithmetic is IEEE FP64.
+ *
+ * Grid: r*_i = rstar_min + i h, h = (rstar_max - rstar_min)/(nr - 1),
+ * i = 0..nr-1; theta_j = (j + 1/2) pi / nth, j = 0..nth-1 (the poles are not
+ * grid points).  Host and device field arrays are row-major [i][j] (theta
+ * fastest) of interleaved complex doubles (re, im): 2 * nr * nth doubles.
+ *
+ * Errors: every call returns TEUK_OK (0) or a negative TEUK_ERR_* code; the
+ * handle keeps a message readable with teuk_last_error().  A call that fails
+ * leaves the handle usable unless the code is TEUK_ERR_CUDA.
+ *
+ * Streams: all device work of a handle is issued on the CUDA stream given to
+ * teuk_create (NULL = the legacy default stream).  teuk_step is asynchronous;
+ * calls that return host data synchronise that stream.  A handle must not be
+ * used from two threads at once; distinct handles are independent.
+ *
+ * Ownership: the handle owns its device memory (allocated in teuk_create and
+ * teuk_set_extraction, released in teuk_destroy).  Host buffers passed in are
+ * owned by the caller and are only read or written during the call.
+ */
+#ifndef TEUK_H
+#define TEUK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TEUK_OK 0
+#define TEUK_ERR_BAD_ARG (-1)   /* an argument is out of range or a pointer is NULL */
+#define TEUK_ERR_OOM (-2)       /* device or host allocation failed */
+#define TEUK_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define TEUK_ERR_NONFINITE (-4) /* the state holds a NaN or infinity */
+#define TEUK_ERR_STATE (-5)     /* call not valid in the handle's current state */
+#define TEUK_ERR_OVERFLOW (-6)  /* waveform samples were overwritten before extraction */
+
+typedef struct teuk_handle teuk_handle;
+
+/* Grid and time step.  nr >= 4, 2 <= nth <= 4096, rstar_min < rstar_max,
+ * rstar_min >= -1000, dt > 0 (see teuk_stable_dt). */
+typedef struct {
+    int nr;
+    int nth;
+    double rstar_min;
+    double rstar_max;
+    double dt;
+} teuk_grid;
+
+/* Circular equatorial orbit at Boyer-Lindquist radius r0 (> r+), smeared into
+ * a Gaussian of width sigma in r* and sigma / r0 in theta around
+ * (r*(r0), pi/2), normalised so that sum_ij G_ij h dtheta = 1 and cut to zero
+ * where its exponent exceeds 50.  The source added to the Pi equation is
+ * amplitude * G * exp(-i m Omega t) with Omega = 1/(r0^{3/2} + a) (prograde)
+ * or -1/(r0^{3/2} - a) (retrograde).  This Gaussian stands in for the
+ * paper's point-particle source T of Eq. (1). */
+typedef struct {
+    double r0;
+    double sigma;
+    double amplitude;
+    int prograde;
+} teuk_orbit;
+
+/* Time-step rule (the paper gives none): dt = min(c_r h / max b,
+ * c_theta / omega_max), where b = (r^2 + a^2)/Sigma_hat is the radial
+ * characteristic speed and omega_max^2 is the Gershgorin bound of the
+ * discrete angular-plus-potential operator over all nodes and mid-points.
+ * The source terms of Eqs. (3)-(4) integrate oscillations of frequency omega
+ * like explicit midpoint RK2, whose amplification per step is
+ * sqrt(1 + (omega dt)^4 / 4); c_theta = 0.1 keeps the stiffest mode's growth
+ * below e^{1.25} over 1e5 steps.  Uses g->nr, nth, rstar_min, rstar_max
+ * (g->dt is ignored).  Host-only, no GPU needed. */
+int teuk_stable_dt(const teuk_grid *g, double a, int s, int m, double c_r, double c_theta,
+                   double *dt_out);
+
+/* Create a solver for spin weight s in {-2, 0, 2}, |a| < 1, any integer m.
+ * Allocates the state (two copies of Phi and Pi, 64 B per point) and the
+ * precomputed scheme coefficients (184 B per point) on the current device,
+ * builds the coefficients with a setup kernel, zeroes the state.
+ * cuda_stream: a cudaStream_t (or NULL).  On success *out receives the handle. */
+int teuk_create(const teuk_grid *g, double a, int s, int m, void *cuda_stream, teuk_handle **out);
+
+/* Release all device memory of the handle (synchronises its stream). */
+int teuk_destroy(teuk_handle *h);
+
+/* Initial data from HOST arrays phi, pi (interleaved complex [nr][nth]).
+ * pi == NULL selects time-symmetric data, d_t Phi = 0, i.e.
+ * Pi_i = b_i (Phi_{i+1} - Phi_{i-1}) / (2h).  The radial boundary rows are
+ * forced to zero.  Resets the step counter and the waveform buffer. */
+int teuk_set_initial(teuk_handle *h, const double *phi, const double *pi);
+
+/* Same as teuk_set_initial with DEVICE arrays (same layout), stream-ordered. */
+int teuk_set_initial_device(teuk_handle *h, const double *phi_dev, const double *pi_dev);
+
+/* Set (orbit != NULL) or remove (orbit == NULL) the Gaussian point-particle
+ * source.  TEUK_ERR_BAD_ARG if r0 <= r+, sigma <= 0, or r*(r0) lies outside
+ * the grid. */
+int teuk_set_source(teuk_handle *h, const teuk_orbit *orbit);
+
+/* Waveform sampling: after every step n (counted from the last
+ * teuk_set_initial) with n % every == 0, Phi(r*_k, theta_j), j < nth, is copied
+ * into a device ring buffer of `capacity` samples, k the node nearest to
+ * rstar_ext.  Allocates the ring buffer; clears earlier samples. */
+int teuk_set_extraction(teuk_handle *h, double rstar_ext, int every, long capacity);
+
+/* Advance n >= 0 time steps, asynchronously on the handle's stream.  Full
+ * chunks of steps replay a captured CUDA graph. */
+int teuk_step(teuk_handle *h, long n);
+
+/* Copy the waveform samples taken since the previous call (oldest first) to
+ * the host: t_out[k] and phi_out[k][nth] (interleaved complex), at most cap
+ * samples; *n_out receives the number copied.  Synchronises the stream.
+ * TEUK_ERR_OVERFLOW if more samples than the ring capacity were taken since
+ * the previous call (the newest `capacity` samples are returned). */
+int teuk_extract(teuk_handle *h, double *t_out, double *phi_out, long cap, long *n_out);
+
+/* Copy the current state to HOST arrays (either may be NULL).  Synchronises. */
+int teuk_get_state(teuk_handle *h, double *phi, double *pi);
+
+/* Copy the current state to DEVICE arrays (stream-ordered, asynchronous). */
+int teuk_get_state_device(teuk_handle *h, double *phi_dev, double *pi_dev);
+
+/* Steps taken since the last teuk_set_initial. */
+long teuk_step_count(const teuk_handle *h);
+
+/* Reduce the state for NaN/Inf on the device; *finite = 1 if all finite.
+ * Returns TEUK_ERR_NONFINITE when not.  Synchronises. */
+int teuk_check_finite(teuk_handle *h, int *finite);
+
+/* Select the step kernel: 0 = fused radial-marching kernel (default),
+ * 1 = two-kernel predictor/corrector with a half-step buffer in device
+ * memory.  Both compute the same Eqs. (3)-(4). */
+int teuk_set_kernel(teuk_handle *h, int variant);
+
+/* Number of kernel launches one teuk_step(h, n) issues for this handle's
+ * configuration (graph replays count their kernel nodes). */
+long teuk_launches_for(const teuk_handle *h, long n);
+
+/* Message of the last failed call on this handle ("" if none). */
+const char *teuk_last_error(const teuk_handle *h);
+
+/* Static description of an error code. */
+const char *teuk_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TEUK_H */

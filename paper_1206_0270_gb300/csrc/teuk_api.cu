@@ -1,0 +1,639 @@
+// teuk_api.cu -- C ABI of libteuk (declared in include/teuk.h).
+//
+// Host side: argument checking, the inverse tortoise map and the
+// time-step rule, device memory layout, the Gaussian source window, the
+// waveform ring buffer, and CUDA-graph replay of chunks of time steps.  Every
+// arithmetic step of the time evolution runs in the kernels of
+// teuk_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "teuk.h"
+#include "teuk_internal.h"
+#include "teuk_physics.h"
+
+using namespace teuk;
+
+static const double kPi = 3.14159265358979323846;
+static const int kChunk = 64;  // time steps per captured CUDA graph (even: ping-pong returns)
+
+struct teuk_handle {
+    int nr = 0, nth = 0, s = 0, m = 0, parity = 1;
+    double a = 0, rstar_min = 0, rstar_max = 0, h = 0, dth = 0, dt = 0;
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    bool own_stream = false;
+
+    char *arena = nullptr;         // state, planes, tables, counters
+    double2 *phi[2] = {nullptr, nullptr}, *pi[2] = {nullptr, nullptr};
+    double2 *phiH = nullptr, *piH = nullptr;  // half-step buffer of the two-kernel variant
+    double *b_node = nullptr;
+    long long *d_step = nullptr;
+    unsigned long long *d_count = nullptr;
+    StepParams sp{};
+
+    double *d_src = nullptr;       // source windows (gP then gC)
+    double2 *d_ring = nullptr;
+    long long drained = 0;
+
+    int cur = 0;
+    long long nstep = 0;
+    int variant = 0;
+    int rows_per_block = 1, nblocks = 1;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// Helpers
+// ---------------------------------------------------------------------------
+
+static int fail(teuk_handle *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(h, TEUK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void horizons(double a, double *rp, double *rm)
+{
+    const double q = std::sqrt(1.0 - a * a);
+    *rp = 1.0 + q;
+    *rm = 1.0 - q;
+}
+
+// r*(r) = r + 2 r+/(r+ - r-) ln((r - r+)/2) - 2 r-/(r+ - r-) ln((r - r-)/2).
+static double rstar_of_r(double r, double a)
+{
+    double rp, rm;
+    horizons(a, &rp, &rm);
+    return r + 2.0 * rp / (rp - rm) * std::log((r - rp) / 2.0) - 2.0 * rm / (rp - rm) * std::log((r - rm) / 2.0);
+}
+
+// Inverse tortoise map: safeguarded Newton iteration on y = ln(r - r+), where
+// r*(y) is increasing with d r*/dy = (r^2 + a^2)/(r - r-).  Returns r and
+// Delta = x (x + r+ - r-), x = r - r+, accurate near the horizon.
+static void r_of_rstar(double rs, double a, double *r_out, double *D_out)
+{
+    double rp, rm;
+    horizons(a, &rp, &rm);
+    const double kp = 2.0 * rp / (rp - rm), km = 2.0 * rm / (rp - rm);
+    const double dr = rp - rm;
+    auto f = [&](double y) {
+        const double x = std::exp(y);
+        return rp + x + kp * (y - std::log(2.0)) - km * std::log((x + dr) / 2.0) - rs;
+    };
+    double lo = -1500.0, hi = 30.0;
+    // starting guess: near-horizon asymptote, or r ~ r* far out
+    double y = rs < 10.0 ? (rs - rp + km * std::log(dr / 2.0)) / kp + std::log(2.0)
+                         : std::log(std::max(rs - rp, 1.0));
+    y = std::min(std::max(y, lo), hi);
+    for (int it = 0; it < 200; ++it) {
+        const double fy = f(y);
+        if (fy == 0.0) break;
+        if (fy < 0) lo = y; else hi = y;
+        const double x = std::exp(y);
+        const double r = rp + x;
+        const double dfy = (r * r + a * a) / (x + dr);
+        double yn = y - fy / dfy;
+        if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+        if (std::fabs(yn - y) <= 4e-16 * std::max(1.0, std::fabs(y))) { y = yn; break; }
+        y = yn;
+    }
+    const double x = std::exp(y);
+    *r_out = rp + x;
+    *D_out = x * (x + dr);
+}
+
+static bool valid_grid(const teuk_grid *g)
+{
+    return g && g->nr >= 4 && g->nth >= 2 && g->nth <= 4096 && g->rstar_min >= -1000.0 &&
+           g->rstar_max > g->rstar_min && std::isfinite(g->rstar_max) && g->rstar_max <= 1e6;
+}
+
+static bool valid_physics(double a, int s)
+{
+    return std::isfinite(a) && std::fabs(a) < 1.0 && (s == -2 || s == 0 || s == 2);
+}
+
+static void destroy_graphs(teuk_handle *h)
+{
+    for (auto &row : h->graph)
+        for (auto &g : row)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+// ---------------------------------------------------------------------------
+// Time-step rule
+// ---------------------------------------------------------------------------
+
+extern "C" int teuk_stable_dt(const teuk_grid *g, double a, int s, int m, double c_r, double c_theta,
+                              double *dt_out)
+{
+    if (!valid_grid(g) || !valid_physics(a, s) || !(c_r > 0) || !(c_theta > 0) || !dt_out)
+        return TEUK_ERR_BAD_ARG;
+    const int nr = g->nr, nth = g->nth;
+    const double hh = (g->rstar_max - g->rstar_min) / (nr - 1);
+    const double dth = kPi / nth;
+    const int rows = 2 * nr - 1;  // nodes then mid-points
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<double> bmax(nt, 0.0), gmax(nt, 0.0);
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; ++t)
+        pool.emplace_back([&, t]() {
+            for (int row = (int)t; row < rows; row += (int)nt) {
+                const double rs = row < nr ? g->rstar_min + row * hh : g->rstar_min + (row - nr + 0.5) * hh;
+                double r, D;
+                r_of_rstar(rs, a, &r, &D);
+                for (int j = 0; j < nth; ++j) {
+                    const double th = (j + 0.5) * dth;
+                    const PhysCoef c = phys_coef(r, D, std::sin(th), std::cos(th), a, s, m);
+                    const double cot = std::cos(th) / std::sin(th);
+                    const double A = 1.0 / (dth * dth) + cot / (2.0 * dth);
+                    const double C = 1.0 / (dth * dth) - cot / (2.0 * dth);
+                    const double gb = std::hypot(c.W_re, c.W_im) +
+                                      c.kappa * (2.0 / (dth * dth) + std::fabs(A) + std::fabs(C));
+                    bmax[t] = std::max(bmax[t], c.b);
+                    gmax[t] = std::max(gmax[t], gb);
+                }
+            }
+        });
+    for (auto &th : pool) th.join();
+    const double b = *std::max_element(bmax.begin(), bmax.end());
+    const double om = std::sqrt(*std::max_element(gmax.begin(), gmax.end()));
+    *dt_out = std::min(c_r * hh / b, c_theta / om);
+    return TEUK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Create / destroy
+// ---------------------------------------------------------------------------
+
+namespace {
+struct Arena {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count)
+    {
+        const size_t o = off;
+        off += ((count * sizeof(T) + 255) / 256) * 256;
+        return o;
+    }
+};
+}  // namespace
+
+static void choose_launch(teuk_handle *h)
+{
+    const int threads = fused_block_threads(h->nth);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(), threads,
+                                                      fused_smem_bytes(h->nth)) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int rows = h->nr - 2;
+    const int target = std::max(1, h->num_sms * per_sm);
+    h->rows_per_block = std::max(1, (rows + target - 1) / target);
+    h->nblocks = (rows + h->rows_per_block - 1) / h->rows_per_block;
+}
+
+extern "C" int teuk_destroy(teuk_handle *h)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    if (h->stream || h->own_stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    if (h->d_src) cudaFree(h->d_src);
+    if (h->d_ring) cudaFree(h->d_ring);
+    if (h->phiH) cudaFree(h->phiH);
+    if (h->arena) cudaFree(h->arena);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cuda_stream, teuk_handle **out)
+{
+    if (!out) return TEUK_ERR_BAD_ARG;
+    *out = nullptr;
+    if (!valid_grid(g) || !valid_physics(a, s) || !(g->dt > 0) || !std::isfinite(g->dt) ||
+        std::abs(m) > 1000000)
+        return TEUK_ERR_BAD_ARG;
+    teuk_handle *h = new (std::nothrow) teuk_handle();
+    if (!h) return TEUK_ERR_OOM;
+    h->nr = g->nr;
+    h->nth = g->nth;
+    h->s = s;
+    h->m = m;
+    h->a = a;
+    h->parity = (std::abs(m) % 2 == 0) ? 1 : -1;
+    h->rstar_min = g->rstar_min;
+    h->rstar_max = g->rstar_max;
+    h->h = (g->rstar_max - g->rstar_min) / (g->nr - 1);
+    h->dth = kPi / g->nth;
+    h->dt = g->dt;
+    auto bail = [&](int code) { teuk_destroy(h); return code; };
+
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(TEUK_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+        return bail(TEUK_ERR_CUDA);
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(TEUK_ERR_CUDA);
+        h->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(TEUK_ERR_CUDA);
+
+    const int nr = h->nr, nth = h->nth;
+    const size_t N = (size_t)nr * nth, Nm = (size_t)(nr - 1) * nth;
+
+    // radial tables (nodes, mid-points) and angular tables
+    std::vector<double> tab(2 * (size_t)nr + 2 * (size_t)(nr - 1) + 3 * (size_t)nth);
+    double *r_node = tab.data(), *D_node = r_node + nr, *r_mid = D_node + nr, *D_mid = r_mid + (nr - 1);
+    double *sin_th = D_mid + (nr - 1), *cos_th = sin_th + nth, *cot_th = cos_th + nth;
+    for (int i = 0; i < nr; ++i) r_of_rstar(h->rstar_min + i * h->h, a, &r_node[i], &D_node[i]);
+    for (int i = 0; i < nr - 1; ++i) r_of_rstar(h->rstar_min + (i + 0.5) * h->h, a, &r_mid[i], &D_mid[i]);
+    for (int j = 0; j < nth; ++j) {
+        const double th = (j + 0.5) * h->dth;
+        sin_th[j] = std::sin(th);
+        cos_th[j] = std::cos(th);
+        cot_th[j] = cos_th[j] / sin_th[j];
+    }
+
+    Arena ar;
+    size_t o_phi[2], o_pi[2];
+    for (int b = 0; b < 2; ++b) { o_phi[b] = ar.take<double2>(N); o_pi[b] = ar.take<double2>(N); }
+    const size_t o_pa = ar.take<double>(Nm), o_pb = ar.take<double>(Nm), o_KAp = ar.take<double>(Nm),
+                 o_KCp = ar.take<double>(Nm);
+    const size_t o_P1 = ar.take<double2>(Nm), o_P2 = ar.take<double2>(Nm), o_Q1 = ar.take<double2>(Nm),
+                 o_Q2 = ar.take<double2>(Nm);
+    const size_t o_tb = ar.take<double>(N), o_KAc = ar.take<double>(N), o_KCc = ar.take<double>(N);
+    const size_t o_R1 = ar.take<double2>(N), o_R2 = ar.take<double2>(N), o_R3 = ar.take<double2>(N),
+                 o_R4 = ar.take<double2>(N);
+    const size_t o_b = ar.take<double>(N);
+    const size_t o_tab = ar.take<double>(tab.size());
+    const size_t o_step = ar.take<long long>(1), o_cnt = ar.take<unsigned long long>(1);
+    if (cudaMalloc(&h->arena, ar.off) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(TEUK_ERR_OOM);
+    }
+    char *A = h->arena;
+    for (int b = 0; b < 2; ++b) {
+        h->phi[b] = (double2 *)(A + o_phi[b]);
+        h->pi[b] = (double2 *)(A + o_pi[b]);
+    }
+    h->b_node = (double *)(A + o_b);
+    h->d_step = (long long *)(A + o_step);
+    h->d_count = (unsigned long long *)(A + o_cnt);
+    double *d_tab = (double *)(A + o_tab);
+
+    SetupParams su{};
+    su.nr = nr; su.nth = nth; su.s = s; su.m = m; su.parity = h->parity;
+    su.a = a; su.h = h->h; su.dth = h->dth; su.dt = h->dt;
+    su.r_node = d_tab; su.D_node = d_tab + nr; su.r_mid = d_tab + 2 * nr; su.D_mid = su.r_mid + (nr - 1);
+    su.sin_th = su.D_mid + (nr - 1); su.cos_th = su.sin_th + nth; su.cot_th = su.cos_th + nth;
+    su.pa = (double *)(A + o_pa); su.pb = (double *)(A + o_pb);
+    su.KAp = (double *)(A + o_KAp); su.KCp = (double *)(A + o_KCp);
+    su.P1 = (double2 *)(A + o_P1); su.P2 = (double2 *)(A + o_P2);
+    su.Q1 = (double2 *)(A + o_Q1); su.Q2 = (double2 *)(A + o_Q2);
+    su.tb = (double *)(A + o_tb); su.KAc = (double *)(A + o_KAc); su.KCc = (double *)(A + o_KCc);
+    su.R1 = (double2 *)(A + o_R1); su.R2 = (double2 *)(A + o_R2);
+    su.R3 = (double2 *)(A + o_R3); su.R4 = (double2 *)(A + o_R4);
+    su.b_node = h->b_node;
+
+    if (cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(h->arena, 0, o_pa, h->stream) != cudaSuccess ||  // both state copies
+        cudaMemsetAsync(h->d_step, 0, 2 * 256, h->stream) != cudaSuccess ||
+        launch_setup(su, h->stream) != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return bail(TEUK_ERR_CUDA);
+
+    StepParams &p = h->sp;
+    p.nr = nr; p.nth = nth; p.dt = h->dt; p.q = 0.25 * h->dt; p.half_dt = 0.5 * h->dt;
+    p.pred = PredPlanes{su.pa, su.pb, su.KAp, su.KCp, su.P1, su.P2, su.Q1, su.Q2};
+    p.corr = CorrPlanes{su.tb, su.KAc, su.KCc, su.R1, su.R2, su.R3, su.R4};
+    p.src = SourceWindow{0, -1, 0, -1, nullptr, nullptr, 0.0, 0};
+    p.ext = Extraction{-1, 1, 1, nullptr};
+    p.step_base = h->d_step;
+    h->variant = nth <= 1024 ? 0 : 1;
+    if (nth <= 1024) {
+        const size_t smem = fused_smem_bytes(nth);
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(fused_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+            return bail(TEUK_ERR_CUDA);
+        choose_launch(h);
+    }
+    if (h->variant == 1) {
+        if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return bail(TEUK_ERR_OOM); }
+        h->piH = h->phiH + Nm;
+    }
+    *out = h;
+    return TEUK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Initial data, source, extraction
+// ---------------------------------------------------------------------------
+
+static int reset_counters(teuk_handle *h)
+{
+    h->cur = 0;
+    h->nstep = 0;
+    h->drained = 0;
+    CU(cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream));
+    return TEUK_OK;
+}
+
+static int finish_initial(teuk_handle *h, bool have_pi)
+{
+    const int nr = h->nr, nth = h->nth;
+    CU(launch_zero_boundary_rows(h->phi[0], h->pi[0], nr, nth, h->stream));
+    if (!have_pi) CU(launch_time_symmetric_pi(h->phi[0], h->pi[0], h->b_node, nr, nth, 1.0 / (2.0 * h->h), h->stream));
+    // the second copy's boundary rows are never written by the step kernels
+    CU(launch_zero_boundary_rows(h->phi[1], h->pi[1], nr, nth, h->stream));
+    return reset_counters(h);
+}
+
+extern "C" int teuk_set_initial(teuk_handle *h, const double *phi, const double *pi)
+{
+    if (!h || !phi) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_initial: NULL argument");
+    const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
+    CU(cudaMemcpyAsync(h->phi[0], phi, bytes, cudaMemcpyHostToDevice, h->stream));
+    if (pi) CU(cudaMemcpyAsync(h->pi[0], pi, bytes, cudaMemcpyHostToDevice, h->stream));
+    int rc = finish_initial(h, pi != nullptr);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    return TEUK_OK;
+}
+
+extern "C" int teuk_set_initial_device(teuk_handle *h, const double *phi, const double *pi)
+{
+    if (!h || !phi) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_initial_device: NULL argument");
+    const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
+    CU(cudaMemcpyAsync(h->phi[0], phi, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    if (pi) CU(cudaMemcpyAsync(h->pi[0], pi, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return finish_initial(h, pi != nullptr);
+}
+
+extern "C" int teuk_set_source(teuk_handle *h, const teuk_orbit *o)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    CU(cudaStreamSynchronize(h->stream));
+    destroy_graphs(h);
+    if (!o) {
+        if (h->d_src) { cudaFree(h->d_src); h->d_src = nullptr; }
+        h->sp.src = SourceWindow{0, -1, 0, -1, nullptr, nullptr, 0.0, 0};
+        return TEUK_OK;
+    }
+    double rp, rm;
+    horizons(h->a, &rp, &rm);
+    if (!(o->r0 > rp) || !std::isfinite(o->r0) || !(o->sigma > 0) || !std::isfinite(o->sigma) ||
+        !std::isfinite(o->amplitude))
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_source: need r0 > r+, sigma > 0");
+    const double rs0 = rstar_of_r(o->r0, h->a);
+    if (!(rs0 > h->rstar_min && rs0 < h->rstar_max))
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_source: r*(r0) outside the grid");
+    const double sig_th = o->sigma / o->r0;
+    const int nr = h->nr, nth = h->nth;
+    auto gauss = [&](double rs, double th) {
+        const double z = (rs - rs0) * (rs - rs0) / (2.0 * o->sigma * o->sigma) +
+                         (th - 0.5 * kPi) * (th - 0.5 * kPi) / (2.0 * sig_th * sig_th);
+        return z > 50.0 ? 0.0 : std::exp(-z);
+    };
+    // rows where the Gaussian can be non-zero: |r* - r*0| <= 10 sigma (exponent <= 50)
+    const double reach = 10.0 * o->sigma;
+    const int lo_n = std::max(0, (int)std::floor((rs0 - reach - h->rstar_min) / h->h) - 1);
+    const int hi_n = std::min(nr - 1, (int)std::ceil((rs0 + reach - h->rstar_min) / h->h) + 1);
+    double norm = 0.0;
+    std::vector<double> gn((size_t)(hi_n - lo_n + 1) * nth), gm((size_t)(hi_n - lo_n + 1) * nth, 0.0);
+    for (int i = lo_n; i <= hi_n; ++i)
+        for (int j = 0; j < nth; ++j) {
+            const double v = gauss(h->rstar_min + i * h->h, (j + 0.5) * h->dth);
+            gn[(size_t)(i - lo_n) * nth + j] = v;
+            norm += v * h->h * h->dth;
+        }
+    if (!(norm > 0)) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_source: Gaussian misses every grid node");
+    const int lo_m = lo_n, hi_m = std::min(nr - 2, hi_n);
+    for (int i = lo_m; i <= hi_m; ++i)
+        for (int j = 0; j < nth; ++j)
+            gm[(size_t)(i - lo_m) * nth + j] = gauss(h->rstar_min + (i + 0.5) * h->h, (j + 0.5) * h->dth);
+    const double cP = 0.5 * h->dt * o->amplitude / norm, cC = h->dt * o->amplitude / norm;
+    for (auto &v : gn) v *= cC;
+    for (auto &v : gm) v *= cP;
+    const size_t nmid = (size_t)(hi_m - lo_m + 1) * nth, nnode = (size_t)(hi_n - lo_n + 1) * nth;
+    std::vector<double> buf(nmid + nnode);
+    std::copy(gm.begin(), gm.begin() + nmid, buf.begin());
+    std::copy(gn.begin(), gn.end(), buf.begin() + nmid);
+    if (h->d_src) { cudaFree(h->d_src); h->d_src = nullptr; }
+    if (cudaMalloc(&h->d_src, buf.size() * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, TEUK_ERR_OOM, "teuk_set_source: out of device memory");
+    }
+    CU(cudaMemcpy(h->d_src, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
+    const double Om = o->prograde ? 1.0 / (o->r0 * std::sqrt(o->r0) + h->a)
+                                  : -1.0 / (o->r0 * std::sqrt(o->r0) - h->a);
+    // interior rows only: the boundary rows 0 and nr-1 are never updated
+    h->sp.src = SourceWindow{lo_m, hi_m, std::max(1, lo_n), std::min(nr - 2, hi_n), h->d_src, h->d_src + nmid,
+                             (double)h->m * Om, 1};
+    // gC is indexed from node_lo: shift the pointer when the window was clipped at row 0
+    h->sp.src.gC = h->d_src + nmid + (size_t)(h->sp.src.node_lo - lo_n) * nth;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_set_extraction(teuk_handle *h, double rstar_ext, int every, long capacity)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    const int i = (int)std::floor((rstar_ext - h->rstar_min) / h->h + 0.5);
+    if (!std::isfinite(rstar_ext) || i < 0 || i >= h->nr || every < 1 || capacity < 1)
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_extraction: radius outside the grid, every < 1 or capacity < 1");
+    CU(cudaStreamSynchronize(h->stream));
+    destroy_graphs(h);
+    if (h->d_ring) { cudaFree(h->d_ring); h->d_ring = nullptr; }
+    if (cudaMalloc(&h->d_ring, (size_t)capacity * h->nth * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, TEUK_ERR_OOM, "teuk_set_extraction: out of device memory");
+    }
+    // boundary rows are constant zero: sample row i is still well defined
+    h->sp.ext = Extraction{i, every, capacity, h->d_ring};
+    h->drained = h->nstep / every;
+    return TEUK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stepping
+// ---------------------------------------------------------------------------
+
+static cudaError_t launch_one(teuk_handle *h, int from, int k, cudaStream_t st)
+{
+    if (h->variant == 0)
+        return launch_step_fused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], k,
+                                 h->rows_per_block, h->nblocks, st);
+    return launch_step_unfused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], h->phiH,
+                               h->piH, k, st);
+}
+
+static int capture_graph(teuk_handle *h, int from)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int b = from;
+    for (int k = 0; k < kChunk && e == cudaSuccess; ++k) {
+        e = launch_one(h, b, k, h->cap_stream);
+        b = 1 - b;
+    }
+    if (e == cudaSuccess) e = launch_advance(h->d_step, kChunk, h->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(h, TEUK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph[h->variant][from], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return fail(h, TEUK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+    return TEUK_OK;
+}
+
+extern "C" int teuk_step(teuk_handle *h, long n)
+{
+    if (!h || n < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_step: n < 0");
+    while (n >= kChunk) {
+        if (!h->graph[h->variant][h->cur]) {
+            int rc = capture_graph(h, h->cur);
+            if (rc) return rc;
+        }
+        CU(cudaGraphLaunch(h->graph[h->variant][h->cur], h->stream));
+        n -= kChunk;
+        h->nstep += kChunk;
+    }
+    if (n > 0) {
+        for (int k = 0; k < n; ++k) {
+            CU(launch_one(h, h->cur, k, h->stream));
+            h->cur = 1 - h->cur;
+        }
+        CU(launch_advance(h->d_step, n, h->stream));
+        h->nstep += n;
+    }
+    return TEUK_OK;
+}
+
+extern "C" long teuk_launches_for(const teuk_handle *h, long n)
+{
+    if (!h || n < 0) return -1;
+    const long per = h->variant == 0 ? 1 : 2;
+    const long full = n / kChunk, rem = n % kChunk;
+    return full * (kChunk * per + 1) + (rem ? rem * per + 1 : 0);
+}
+
+extern "C" int teuk_set_kernel(teuk_handle *h, int variant)
+{
+    if (!h || variant < 0 || variant > 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: variant 0 or 1");
+    if (variant == 0 && h->nth > 1024) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: fused kernel needs nth <= 1024");
+    if (variant == 1 && !h->phiH) {
+        const size_t Nm = (size_t)(h->nr - 1) * h->nth;
+        if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, TEUK_ERR_OOM, "teuk_set_kernel: out of device memory");
+        }
+        h->piH = h->phiH + Nm;
+    }
+    h->variant = variant;
+    return TEUK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Results
+// ---------------------------------------------------------------------------
+
+extern "C" int teuk_extract(teuk_handle *h, double *t_out, double *phi_out, long cap, long *n_out)
+{
+    if (!h || !n_out || cap < 0 || (cap > 0 && (!t_out || !phi_out)))
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_extract: bad argument");
+    *n_out = 0;
+    if (h->sp.ext.i_ext < 0) return fail(h, TEUK_ERR_STATE, "teuk_extract: no extraction set");
+    CU(cudaStreamSynchronize(h->stream));
+    const long long every = h->sp.ext.every, capacity = h->sp.ext.capacity;
+    const long long total = h->nstep / every;
+    int rc = TEUK_OK;
+    if (total - h->drained > capacity) {
+        h->drained = total - capacity;
+        rc = fail(h, TEUK_ERR_OVERFLOW, "teuk_extract: ring buffer overflowed; oldest samples lost");
+    }
+    const long long n = std::min<long long>(cap, total - h->drained);
+    const size_t row = (size_t)h->nth * sizeof(double2);
+    long long done = 0;
+    while (done < n) {
+        const long long s = h->drained + done + 1;  // 1-based sample number
+        const long long slot = (s - 1) % capacity;
+        const long long run = std::min<long long>(n - done, capacity - slot);
+        CU(cudaMemcpy(phi_out + (size_t)done * 2 * h->nth, h->d_ring + (size_t)slot * h->nth, (size_t)run * row,
+                      cudaMemcpyDeviceToHost));
+        for (long long q = 0; q < run; ++q) t_out[done + q] = (double)((s + q) * every) * h->dt;
+        done += run;
+    }
+    h->drained += n;
+    *n_out = (long)n;
+    return rc;
+}
+
+extern "C" int teuk_get_state(teuk_handle *h, double *phi, double *pi)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
+    if (phi) CU(cudaMemcpyAsync(phi, h->phi[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (pi) CU(cudaMemcpyAsync(pi, h->pi[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return TEUK_OK;
+}
+
+extern "C" int teuk_get_state_device(teuk_handle *h, double *phi, double *pi)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
+    if (phi) CU(cudaMemcpyAsync(phi, h->phi[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    if (pi) CU(cudaMemcpyAsync(pi, h->pi[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return TEUK_OK;
+}
+
+extern "C" long teuk_step_count(const teuk_handle *h) { return h ? (long)h->nstep : -1; }
+
+extern "C" int teuk_check_finite(teuk_handle *h, int *finite)
+{
+    if (!h || !finite) return fail(h, TEUK_ERR_BAD_ARG, "teuk_check_finite: NULL argument");
+    unsigned long long cnt = 0;
+    CU(cudaMemsetAsync(h->d_count, 0, sizeof(cnt), h->stream));
+    CU(launch_nonfinite_count(h->phi[h->cur], h->pi[h->cur], (long long)h->nr * h->nth, h->d_count, h->stream));
+    CU(cudaMemcpyAsync(&cnt, h->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    *finite = cnt == 0;
+    return cnt == 0 ? TEUK_OK : fail(h, TEUK_ERR_NONFINITE, "state holds NaN or Inf");
+}
+
+extern "C" const char *teuk_last_error(const teuk_handle *h) { return h ? h->err.c_str() : ""; }
+
+extern "C" const char *teuk_strerror(int code)
+{
+    switch (code) {
+    case TEUK_OK: return "ok";
+    case TEUK_ERR_BAD_ARG: return "bad argument";
+    case TEUK_ERR_OOM: return "out of memory";
+    case TEUK_ERR_CUDA: return "CUDA error";
+    case TEUK_ERR_NONFINITE: return "non-finite state";
+    case TEUK_ERR_STATE: return "invalid call for the handle's state";
+    case TEUK_ERR_OVERFLOW: return "waveform ring buffer overflow";
+    default: return "unknown error";
+    }
+}

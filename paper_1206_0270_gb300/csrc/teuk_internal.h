@@ -1,0 +1,116 @@
+// teuk_internal.h -- device data layout and kernel parameters of libteuk.
+//
+// One time step of the two-step Lax-Wendroff scheme (Eqs. 3-4 of
+// arXiv:1206.0270) is linear in the state with time-independent
+// coefficients, apart from the source phase.  The setup kernel folds every
+// constant of the scheme (dt, h, dtheta, the 1/2 averages, the diagonal of
+// the angular stencil, the pole ghosts) into per-point coefficient planes, so
+// that a step costs 60 FP64 fused multiply-adds per point (FP64 throughput
+// is the scarce resource on GB300; bytes are not).
+//
+// With u_i = (Phi_i, Pi_i) the state at node i, sigma_j = Phi_{i,j} +
+// Phi_{i+1,j}, the predictor (Eq. 3) at the mid-point h = i + 1/2 reads
+//   Phi^h = pa Phi_i + pb Phi_{i+1} + (dt/4)(Pi_i + Pi_{i+1})
+//   Pi^h  = P1 Pi_i + P2 Pi_{i+1} + Q1 Phi_i + Q2 Phi_{i+1}
+//           + KA sigma_{j+1} + KC sigma_{j-1} + gP e^{-i m Omega t_n}
+// and with sigma'_j = Phi^{i+1/2}_j + Phi^{i-1/2}_j the corrector (Eq. 4)
+//   Phi^{n+1} = Phi_i - tb Phi^{i+1/2} + tb Phi^{i-1/2} + (dt/2)(Pi^{i+1/2} + Pi^{i-1/2})
+//   Pi^{n+1}  = Pi_i + R1 Pi^{i+1/2} + R2 Pi^{i-1/2} + R3 Phi^{i+1/2} + R4 Phi^{i-1/2}
+//               + KA' sigma'_{j+1} + KC' sigma'_{j-1} + gC e^{-i m Omega (t_n + dt/2)}
+// where (beta = dt b/(2h), gamma = dt d/(2h), A/B/C the angular stencil
+// weights of L_theta with the ghosts folded into B at j = 0 and j = nth-1):
+//   pa = 1/2 + beta, pb = 1/2 - beta,
+//   P1 = 1/2 - beta - (dt/4) c_t,  P2 = 1/2 + beta - (dt/4) c_t,
+//   Q1 = -gamma - (dt/4)(W - kappa B),  Q2 = gamma - (dt/4)(W - kappa B),
+//   KA = (dt/4) kappa A, KC = (dt/4) kappa C, gP = (dt/2) G      (mid-point values)
+//   tb = 2 beta, R1 = 2 beta - (dt/2) c_t, R2 = -2 beta - (dt/2) c_t,
+//   R3 = 2 gamma - (dt/2)(W - kappa B), R4 = -2 gamma - (dt/2)(W - kappa B),
+//   KA' = (dt/2) kappa A, KC' = (dt/2) kappa C, gC = dt G        (node values)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace teuk {
+
+// Predictor planes: rows hp = 0 .. nr-2 (mid-point r*_{hp+1/2}), nth values each.
+struct PredPlanes {
+    const double *pa, *pb, *KA, *KC;
+    const double2 *P1, *P2, *Q1, *Q2;
+};
+
+// Corrector planes: rows i = 0 .. nr-1 (rows 0 and nr-1 unused).
+struct CorrPlanes {
+    const double *tb, *KA, *KC;
+    const double2 *R1, *R2, *R3, *R4;
+};
+
+// Source restricted to the rows where the Gaussian is non-zero.
+struct SourceWindow {
+    int mid_lo, mid_hi;    // predictor rows [mid_lo, mid_hi] (empty if mid_lo > mid_hi)
+    int node_lo, node_hi;  // corrector rows [node_lo, node_hi]
+    const double *gP;      // [(mid_hi - mid_lo + 1) * nth]  (dt/2) G at mid-points
+    const double *gC;      // [(node_hi - node_lo + 1) * nth] dt G at nodes
+    double m_omega;        // m * Omega
+    int active;
+};
+
+struct Extraction {
+    int i_ext;             // node row, or -1 when off
+    int every;
+    long long capacity;    // samples in the ring
+    double2 *ring;         // [capacity][nth]
+};
+
+struct StepParams {
+    int nr, nth;
+    double dt, q, half_dt; // dt, dt/4, dt/2
+    PredPlanes pred;
+    CorrPlanes corr;
+    SourceWindow src;
+    Extraction ext;
+    const long long *step_base;  // device: steps completed before this chunk
+};
+
+// ---------------------------------------------------------------------------
+// Kernels (teuk_kernels.cu)
+// ---------------------------------------------------------------------------
+
+struct SetupParams {
+    int nr, nth, s, m, parity;
+    double a, h, dth, dt;
+    const double *r_node, *D_node, *r_mid, *D_mid;  // radial tables (Delta as D)
+    const double *sin_th, *cos_th, *cot_th;         // angular tables
+    // outputs
+    double *pa, *pb, *KAp, *KCp;
+    double2 *P1, *P2, *Q1, *Q2;
+    double *tb, *KAc, *KCc;
+    double2 *R1, *R2, *R3, *R4;
+    double *b_node;
+};
+
+cudaError_t launch_setup(const SetupParams &sp, cudaStream_t st);
+
+cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const double2 *Pi,
+                              double2 *PhiO, double2 *PiO, int k, int rows_per_block,
+                              int nblocks, cudaStream_t st);
+
+cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const double2 *Pi,
+                                double2 *PhiO, double2 *PiO, double2 *PhiH, double2 *PiH, int k,
+                                cudaStream_t st);
+
+cudaError_t launch_advance(long long *step_base, long long by, cudaStream_t st);
+
+cudaError_t launch_time_symmetric_pi(const double2 *Phi, double2 *Pi, const double *b_node,
+                                     int nr, int nth, double inv_2h, cudaStream_t st);
+
+cudaError_t launch_zero_boundary_rows(double2 *Phi, double2 *Pi, int nr, int nth, cudaStream_t st);
+
+cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long long npts,
+                                   unsigned long long *count, cudaStream_t st);
+
+int fused_block_threads(int nth);
+size_t fused_smem_bytes(int nth);
+const void *fused_kernel_ptr();
+
+}  // namespace teuk

@@ -1,0 +1,238 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides start from the same seeded inputs (paper_1206_0270_gb300.inputs)
+and take the same number of steps of Eqs. (3)-(4).  The bar is the norm-wise
+relative error ||Phi_gpu - Phi_oracle||_inf / ||Phi_oracle||_inf <= 1e-10 (and
+the same for Pi and for the extracted waveform).  The two sides round
+differently (the kernels fold the scheme's constants into coefficients and
+use FMAs; the oracle evaluates Eqs. (3)-(4) literally without contraction), so
+the difference is a few ulp per step.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1206_0270_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def teuk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1206_0270_gb300 import build
+    build.build()
+    from paper_1206_0270_gb300 import teuk as T
+    return T
+
+
+def rel(a, b):
+    s = max(abs(b).max(), 1e-300)
+    return abs(a - b).max() / s
+
+
+def run_pair(T, nr, nth, rmin, rmax, a, s, m, nsteps, *, init="random", source=None, ext=None,
+             kernel=0, c_theta=0.1, seed=0, chunks=None):
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m, 0.5, c_theta)
+    if init == "random":
+        phi0, pi0 = inputs.random_fields(nr, nth, seed=seed)
+    elif init == "pulse":
+        phi0 = inputs.gaussian_pulse(nr, nth, rmin, rmax, s, m, center=0.5 * (rmin + rmax), width=5.0,
+                                     seed=seed)
+        pi0 = None
+    else:
+        phi0, pi0 = np.zeros((nr, nth), complex), np.zeros((nr, nth), complex)
+    ora = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    ora.set_initial(phi0, pi0)
+    gpu = T.Solver(nr, nth, rmin, rmax, dt, a, s, m, kernel=kernel)
+    gpu.set_initial(phi0, pi0)
+    if source:
+        ora.set_source(**source)
+        gpu.set_source(**source)
+    if ext:
+        ora.set_extraction(ext[0], ext[1])
+        gpu.set_extraction(ext[0], ext[1], capacity=max(1, nsteps // ext[1] + 1))
+    ora.step(nsteps)
+    for c in (chunks or [nsteps]):
+        gpu.step(c)
+    out = dict(ora=ora.state(), gpu=gpu.state())
+    if ext:
+        out["ora_w"] = ora.samples()
+        out["gpu_w"] = gpu.extract()
+    gpu.close()
+    return out
+
+
+def assert_parity(out, tol=TOL):
+    (po, qo), (pg, qg) = out["ora"], out["gpu"]
+    assert np.all(np.isfinite(pg)) and np.all(np.isfinite(qg))
+    assert rel(pg, po) <= tol, rel(pg, po)
+    assert rel(qg, qo) <= tol, rel(qg, qo)
+    if "ora_w" in out:
+        (to, wo), (tg, wg) = out["ora_w"], out["gpu_w"]
+        assert len(tg) == len(to)
+        np.testing.assert_array_equal(tg, to)
+        if len(wo):
+            assert rel(wg, wo) <= tol if abs(wo).max() > 0 else abs(wg).max() == 0
+
+
+SRC = dict(r0=8.0, sigma=0.5, amplitude=1.0, prograde=True)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("a,s,m", [(0.9, -2, 2), (0.0, -2, 2), (0.5, 0, 1), (0.7, 2, -3), (0.3, -2, 0)])
+def test_parity_small_grids(teuk, kernel, a, s, m):
+    out = run_pair(teuk, 150, 24, -20.0, 40.0, a, s, m, 130, source=SRC, ext=(10.0, 7), kernel=kernel,
+                   seed=abs(m) + 3)
+    assert_parity(out)
+
+
+@pytest.mark.parametrize("nr,nth", [(4, 2), (5, 3), (37, 33), (70, 31), (129, 50), (40, 96)])
+def test_parity_ragged_and_tiny(teuk, nr, nth):
+    out = run_pair(teuk, nr, nth, -10.0, 30.0, 0.6, -2, 1, 23, source=dict(r0=4.0, sigma=2.0),
+                   ext=(5.0, 2), c_theta=0.05, seed=nr)
+    assert_parity(out)
+
+
+def test_parity_wide_theta_fused_limit_and_beyond(teuk):
+    # nth = 1024 is the widest fused block; 1030 runs the two-kernel variant.
+    for nth, kern in [(1024, 0), (1030, 1)]:
+        out = run_pair(teuk, 40, nth, -10.0, 30.0, 0.9, -2, 2, 6, source=dict(r0=5.0, sigma=1.0), kernel=kern,
+                       seed=1)
+        assert_parity(out)
+
+
+def test_parity_schwarzschild_pulse_1024x64_2000_steps(teuk):
+    # The Schwarzschild workload in full: a = 0, s = -2, m = 2, 1024 x 64,
+    # r* in [-100, 300], time-symmetric Gaussian pulse (width 5M), 2000 steps,
+    # waveform at r* = 100 every 10 steps.
+    w = inputs.WORKLOADS["schwarzschild_s-2_m2_1024x64"]
+    dt = O.stable_dt(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], w["c_r"],
+                     w["c_theta"])
+    phi0 = inputs.gaussian_pulse(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["s"], w["m"],
+                                 w["pulse"]["center"], w["pulse"]["width"], seed=0)
+    ora = O.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+    gpu = teuk.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+    for x in (ora, gpu):
+        x.set_initial(phi0)
+    ora.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"])
+    gpu.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"], capacity=256)
+    ora.step(w["steps"])
+    gpu.step(w["steps"])
+    assert_parity(dict(ora=ora.state(), gpu=gpu.state(), ora_w=ora.samples(), gpu_w=gpu.extract()))
+
+
+def test_parity_kerr_8192x128_full_grid(teuk):
+    # The Kerr a = 0.9 workload's grid, orbit and source (r0 = 10M, sigma =
+    # 0.05M) in the launch configuration the benchmark times (fused kernel,
+    # graph replay), for 640 steps from random smooth data; waveform sampled at
+    # r* = 20 every 10 steps (r* = 500 is still silent this early).
+    w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
+    src = dict(w["source"])
+    out = run_pair(teuk, w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], 640,
+                   init="random", source=src, ext=(20.0, 10), seed=7)
+    assert_parity(out)
+
+
+def test_graph_and_direct_launches_agree_bitwise(teuk):
+    kw = dict(source=SRC, ext=(10.0, 5), seed=2)
+    a = run_pair(teuk, 120, 40, -20.0, 40.0, 0.8, -2, 2, 200, chunks=[200], **kw)
+    b = run_pair(teuk, 120, 40, -20.0, 40.0, 0.8, -2, 2, 200, chunks=[1] * 3 + [64] + [5] * 20 + [33], **kw)
+    for x, y in zip(a["gpu"], b["gpu"]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a["gpu_w"][1], b["gpu_w"][1])
+
+
+def test_fused_and_two_kernel_variants_agree_bitwise(teuk):
+    kw = dict(source=SRC, ext=(10.0, 5), seed=9)
+    a = run_pair(teuk, 100, 48, -20.0, 40.0, 0.9, -2, 1, 150, kernel=0, **kw)
+    b = run_pair(teuk, 100, 48, -20.0, 40.0, 0.9, -2, 1, 150, kernel=1, **kw)
+    for x, y in zip(a["gpu"], b["gpu"]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_runs_are_deterministic(teuk):
+    kw = dict(source=SRC, seed=4)
+    a = run_pair(teuk, 200, 64, -20.0, 40.0, 0.9, -2, 2, 300, **kw)
+    b = run_pair(teuk, 200, 64, -20.0, 40.0, 0.9, -2, 2, 300, **kw)
+    for x, y in zip(a["gpu"], b["gpu"]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_time_symmetric_initial_data(teuk):
+    out = run_pair(teuk, 300, 16, -50.0, 100.0, 0.9, -2, 2, 0, init="pulse", seed=3)
+    assert_parity(out, tol=1e-14)
+    out = run_pair(teuk, 300, 16, -50.0, 100.0, 0.9, -2, 2, 77, init="pulse", seed=3)
+    assert_parity(out)
+
+
+def test_zero_steps_and_boundary_rows(teuk):
+    nr, nth = 64, 16
+    dt = O.stable_dt(nr, nth, -10.0, 30.0, 0.5, -2, 2)
+    g = teuk.Solver(nr, nth, -10.0, 30.0, dt, 0.5, -2, 2)
+    phi0, pi0 = inputs.random_fields(nr, nth, seed=1)
+    g.set_initial(phi0, pi0)
+    g.step(0)
+    p, q = g.state()
+    assert np.all(p[0] == 0) and np.all(p[-1] == 0) and np.all(q[0] == 0) and np.all(q[-1] == 0)
+    np.testing.assert_array_equal(p[1:-1], phi0[1:-1])
+    g.set_source(r0=5.0, sigma=1.0)
+    g.step(129)
+    p, q = g.state()
+    assert np.all(p[0] == 0) and np.all(p[-1] == 0) and np.all(q[0] == 0) and np.all(q[-1] == 0)
+    assert g.step_count == 129
+    assert g.check_finite()
+
+
+def test_extraction_ring_overflow_and_drain(teuk):
+    nr, nth = 64, 8
+    dt = O.stable_dt(nr, nth, -10.0, 30.0, 0.5, -2, 2)
+    g = teuk.Solver(nr, nth, -10.0, 30.0, dt, 0.5, -2, 2)
+    g.set_initial(*inputs.random_fields(nr, nth, seed=2))
+    g.set_extraction(3.0, every=2, capacity=5)
+    g.step(6)
+    t, w = g.extract()
+    assert len(t) == 3 and np.allclose(t, np.array([2, 4, 6]) * dt)
+    g.step(20)                       # 10 samples into a ring of 5
+    with pytest.raises(teuk.TeukError) as e:
+        g.extract()
+    assert e.value.code == -6
+    g.step(4)
+    t, w = g.extract()
+    assert np.allclose(t, np.array([28, 30]) * dt)
+    # the newest samples match a fresh run's state at those steps
+    ref = teuk.Solver(nr, nth, -10.0, 30.0, dt, 0.5, -2, 2)
+    ref.set_initial(*inputs.random_fields(nr, nth, seed=2))
+    ref.step(30)
+    i = int(np.floor((3.0 + 10.0) / (40.0 / 63) + 0.5))
+    np.testing.assert_array_equal(w[-1], ref.state()[0][i])
+
+
+def test_bad_arguments(teuk):
+    nr, nth = 64, 8
+    g = teuk.Solver(nr, nth, -10.0, 30.0, 0.01, 0.5, -2, 2)
+    with pytest.raises(teuk.TeukError):
+        g.set_source(r0=1.0, sigma=0.5)          # inside the horizon
+    with pytest.raises(teuk.TeukError):
+        g.set_source(r0=500.0, sigma=0.5)        # r*(r0) beyond the grid
+    with pytest.raises(teuk.TeukError):
+        g.set_extraction(100.0, 1)               # outside the grid
+    with pytest.raises(teuk.TeukError) as e:
+        g.extract()                              # no extraction set
+    assert e.value.code == -5
+    with pytest.raises(teuk.TeukError):
+        g.step(-1)
+    with pytest.raises(teuk.TeukError):
+        teuk.Solver(64, 8, -10.0, 30.0, 0.01, 0.5, 1, 2)   # s = 1
+
+
+def test_nonfinite_state_is_reported(teuk):
+    nr, nth = 32, 8
+    g = teuk.Solver(nr, nth, -10.0, 30.0, 0.01, 0.5, -2, 2)
+    phi = np.zeros((nr, nth), complex)
+    phi[5, 3] = np.nan
+    g.set_initial(phi, np.zeros_like(phi))
+    assert not g.check_finite()
