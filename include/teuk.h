@@ -26,7 +26,8 @@
  * leaves the handle usable unless the code is TEUK_ERR_CUDA.
  *
  * Streams: all device work of a handle is issued on the CUDA stream given to
- * teuk_create (NULL = the legacy default stream).  teuk_step is asynchronous;
+ * teuk_create (NULL: the handle creates and owns a non-blocking stream).
+ * teuk_step is asynchronous;
  * calls that return host data synchronise that stream.  A handle must not be
  * used from two threads at once; distinct handles are independent.
  *
@@ -147,6 +148,15 @@ int teuk_check_finite(teuk_handle *h, int *finite);
  * 1 = two-kernel predictor/corrector with a half-step buffer in device
  * memory.  Both compute the same Eqs. (3)-(4). */
 int teuk_set_kernel(teuk_handle *h, int variant);
+
+/* Launch shape of the fused kernel: radial rows per CTA (one CTA per strip
+ * of rows, marching along r*).  0 restores the automatic choice.  Longer
+ * strips recompute fewer predictor rows (one per strip) but leave fewer CTAs
+ * to hide latency.  Results do not depend on the shape. */
+int teuk_set_launch(teuk_handle *h, int rows_per_block);
+
+/* Current fused-kernel launch shape. */
+int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *nblocks);
 
 /* Number of kernel launches one teuk_step(h, n) issues for this handle's
  * configuration (graph replays count their kernel nodes). */

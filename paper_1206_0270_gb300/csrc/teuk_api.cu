@@ -194,17 +194,25 @@ struct Arena {
 };
 }  // namespace
 
-static void choose_launch(teuk_handle *h)
+// Automatic launch shape: about 16 resident warps per SM (enough to hide
+// the load latency behind the FP64 pipe), in as few, long strips as that
+// allows, since every strip recomputes one predictor row.
+static void choose_launch(teuk_handle *h, int rows_per_block)
 {
-    const int threads = fused_block_threads(h->nth);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(), threads,
-                                                      fused_smem_bytes(h->nth)) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
     const int rows = h->nr - 2;
-    const int target = std::max(1, h->num_sms * per_sm);
-    h->rows_per_block = std::max(1, (rows + target - 1) / target);
+    if (rows_per_block <= 0) {
+        const int threads = fused_block_threads(h->nth);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(), threads,
+                                                          fused_smem_bytes(h->nth)) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        const int want = std::max(1, 16 / std::max(1, threads / 32));
+        per_sm = std::min(per_sm, want);
+        const int target = std::max(1, h->num_sms * per_sm);
+        rows_per_block = (rows + target - 1) / target;
+    }
+    h->rows_per_block = std::max(1, std::min(rows_per_block, rows));
     h->nblocks = (rows + h->rows_per_block - 1) / h->rows_per_block;
 }
 
@@ -334,7 +342,7 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
             cudaFuncSetAttribute(fused_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess)
             return bail(TEUK_ERR_CUDA);
-        choose_launch(h);
+        choose_launch(h, 0);
     }
     if (h->variant == 1) {
         if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return bail(TEUK_ERR_OOM); }
@@ -527,6 +535,24 @@ extern "C" int teuk_step(teuk_handle *h, long n)
         CU(launch_advance(h->d_step, n, h->stream));
         h->nstep += n;
     }
+    return TEUK_OK;
+}
+
+extern "C" int teuk_set_launch(teuk_handle *h, int rows_per_block)
+{
+    if (!h || rows_per_block < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_launch: rows_per_block < 0");
+    if (h->nth > 1024) return fail(h, TEUK_ERR_STATE, "teuk_set_launch: fused kernel needs nth <= 1024");
+    CU(cudaStreamSynchronize(h->stream));
+    destroy_graphs(h);
+    choose_launch(h, rows_per_block);
+    return TEUK_OK;
+}
+
+extern "C" int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *nblocks)
+{
+    if (!h || !rows_per_block || !nblocks) return TEUK_ERR_BAD_ARG;
+    *rows_per_block = h->rows_per_block;
+    *nblocks = h->nblocks;
     return TEUK_OK;
 }
 

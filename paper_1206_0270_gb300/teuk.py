@@ -60,6 +60,8 @@ _SIGS = {
     "teuk_check_finite": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "teuk_set_kernel": (C.c_int, [_vp, C.c_int]),
     "teuk_launches_for": (C.c_long, [_vp, C.c_long]),
+    "teuk_set_launch": (C.c_int, [_vp, C.c_int]),
+    "teuk_get_launch": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "teuk_last_error": (C.c_char_p, [_vp]),
     "teuk_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -191,6 +193,14 @@ class Solver:
         if rc not in (TEUK_OK, -4):
             _check(rc, self.h, "teuk_check_finite")
         return bool(f.value)
+
+    def set_launch(self, rows_per_block):
+        _check(teuk_set_launch(self.h, int(rows_per_block)), self.h, "teuk_set_launch")
+
+    def launch_shape(self):
+        r, b = C.c_int(), C.c_int()
+        _check(teuk_get_launch(self.h, C.byref(r), C.byref(b)), self.h, "teuk_get_launch")
+        return r.value, b.value
 
     def launches_for(self, n):
         return teuk_launches_for(self.h, int(n))
