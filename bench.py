@@ -36,8 +36,8 @@ WORKLOAD = "kerr_a0.9_s-2_m2_8192x128_r0_10"
 METRIC = "FP64 grid-pt updates/s"
 UNIT = "grid-pt updates/s"
 # FP64 work of one interior point update in the folded formulation of
-# Eqs. (3)-(4): 4 adds + 4 multiplies + 52 FMAs = 60 FP64 instructions = 112 flops.
-FLOPS_PER_UPDATE = 112
+# Eqs. (3)-(4): 8 adds + 4 multiplies + 44 FMAs = 56 FP64 instructions = 100 flops.
+FLOPS_PER_UPDATE = 100
 # Algorithmic HBM bytes of one point update: read u^n, write u^{n+1} (4 doubles each).
 BYTES_PER_UPDATE_ALG = 64
 # Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
@@ -273,7 +273,7 @@ def run_gpu(args):
                 dtype="f64", data="synthetic",
                 config=dict(workload=WORKLOAD, nr=nr, nth=nth, a=w["a"], s=w["s"], m=w["m"],
                             rstar=[w["rstar_min"], w["rstar_max"]], dt=dt, time_steps_per_step=args.chunk,
-                            kernel="fused radial-marching, CUDA-graph replay",
+                            kernel="split predictor/corrector tiles, CUDA-graph replay",
                             l2="inputs larger than L2 (state 2x33.5 MB + coefficients 193 MB per time step)",
                             parallelism="replicas" if ws > 1 else "single GPU"),
                 roofline=roofline, e2e=e2e, gpu_launches=int(launches),

@@ -92,7 +92,7 @@ int teuk_stable_dt(const teuk_grid *g, double a, int s, int m, double c_r, doubl
 
 /* Create a solver for spin weight s in {-2, 0, 2}, |a| < 1, any integer m.
  * Allocates the state (two copies of Phi and Pi, 64 B per point) and the
- * precomputed scheme coefficients (184 B per point) on the current device,
+ * precomputed scheme coefficients (168 B per point) on the current device,
  * builds the coefficients with a setup kernel, zeroes the state.
  * cuda_stream: a cudaStream_t (or NULL).  On success *out receives the handle. */
 int teuk_create(const teuk_grid *g, double a, int s, int m, void *cuda_stream, teuk_handle **out);
@@ -146,7 +146,10 @@ int teuk_check_finite(teuk_handle *h, int *finite);
 
 /* Select the step kernel: 0 = fused radial-marching kernel (default),
  * 1 = two-kernel predictor/corrector with a half-step buffer in device
- * memory.  Both compute the same Eqs. (3)-(4). */
+ * memory, 2 = the same two kernels over 2D tiles with the angular neighbour
+ * sums shared in shared memory (0 needs nth <= 512, 2 needs nth <= 1024; the
+ * default is the first of 0, 2, 1 that fits).  All compute the
+ * same Eqs. (3)-(4) and give bit-identical results. */
 int teuk_set_kernel(teuk_handle *h, int variant);
 
 /* Launch shape of the fused kernel: radial rows per CTA (one CTA per strip

@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "libteuk.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
-           "-I", INCLUDE, "-I", CSRC]
+           "-I", INCLUDE, "-I", CSRC] + os.environ.get("TEUK_NVCC_EXTRA", "").split()
 
 
 def nvcc() -> str:

@@ -22,6 +22,7 @@ using namespace teuk;
 
 static const double kPi = 3.14159265358979323846;
 static const int kChunk = 64;  // time steps per captured CUDA graph (even: ping-pong returns)
+static const int kFusedMaxNth = 512;  // the fused kernel keeps a row ahead in registers: <= 512 threads
 
 struct teuk_handle {
     int nr = 0, nth = 0, s = 0, m = 0, parity = 1;
@@ -46,7 +47,7 @@ struct teuk_handle {
     long long nstep = 0;
     int variant = 0;
     int rows_per_block = 1, nblocks = 1;
-    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t graph[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     std::string err;
 };
 
@@ -283,13 +284,12 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     Arena ar;
     size_t o_phi[2], o_pi[2];
     for (int b = 0; b < 2; ++b) { o_phi[b] = ar.take<double2>(N); o_pi[b] = ar.take<double2>(N); }
-    const size_t o_pa = ar.take<double>(Nm), o_pb = ar.take<double>(Nm), o_KAp = ar.take<double>(Nm),
-                 o_KCp = ar.take<double>(Nm);
-    const size_t o_P1 = ar.take<double2>(Nm), o_P2 = ar.take<double2>(Nm), o_Q1 = ar.take<double2>(Nm),
-                 o_Q2 = ar.take<double2>(Nm);
-    const size_t o_tb = ar.take<double>(N), o_KAc = ar.take<double>(N), o_KCc = ar.take<double>(N);
-    const size_t o_R1 = ar.take<double2>(N), o_R2 = ar.take<double2>(N), o_R3 = ar.take<double2>(N),
-                 o_R4 = ar.take<double2>(N);
+    const size_t o_pa = ar.take<double>(Nm), o_pb = ar.take<double>(Nm), o_eb = ar.take<double>(Nm),
+                 o_KAp = ar.take<double>(Nm), o_KCp = ar.take<double>(Nm);
+    const size_t o_P1 = ar.take<double2>(Nm), o_Q1 = ar.take<double2>(Nm), o_Q2 = ar.take<double2>(Nm);
+    const size_t o_tb = ar.take<double>(N), o_nt2 = ar.take<double>(N), o_KAc = ar.take<double>(N),
+                 o_KCc = ar.take<double>(N);
+    const size_t o_R1 = ar.take<double2>(N), o_R3 = ar.take<double2>(N), o_R4 = ar.take<double2>(N);
     const size_t o_b = ar.take<double>(N);
     const size_t o_tab = ar.take<double>(tab.size());
     const size_t o_step = ar.take<long long>(1), o_cnt = ar.take<unsigned long long>(1);
@@ -312,13 +312,12 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     su.a = a; su.h = h->h; su.dth = h->dth; su.dt = h->dt;
     su.r_node = d_tab; su.D_node = d_tab + nr; su.r_mid = d_tab + 2 * nr; su.D_mid = su.r_mid + (nr - 1);
     su.sin_th = su.D_mid + (nr - 1); su.cos_th = su.sin_th + nth; su.cot_th = su.cos_th + nth;
-    su.pa = (double *)(A + o_pa); su.pb = (double *)(A + o_pb);
+    su.pa = (double *)(A + o_pa); su.pb = (double *)(A + o_pb); su.eb = (double *)(A + o_eb);
     su.KAp = (double *)(A + o_KAp); su.KCp = (double *)(A + o_KCp);
-    su.P1 = (double2 *)(A + o_P1); su.P2 = (double2 *)(A + o_P2);
-    su.Q1 = (double2 *)(A + o_Q1); su.Q2 = (double2 *)(A + o_Q2);
-    su.tb = (double *)(A + o_tb); su.KAc = (double *)(A + o_KAc); su.KCc = (double *)(A + o_KCc);
-    su.R1 = (double2 *)(A + o_R1); su.R2 = (double2 *)(A + o_R2);
-    su.R3 = (double2 *)(A + o_R3); su.R4 = (double2 *)(A + o_R4);
+    su.P1 = (double2 *)(A + o_P1); su.Q1 = (double2 *)(A + o_Q1); su.Q2 = (double2 *)(A + o_Q2);
+    su.tb = (double *)(A + o_tb); su.nt2 = (double *)(A + o_nt2);
+    su.KAc = (double *)(A + o_KAc); su.KCc = (double *)(A + o_KCc);
+    su.R1 = (double2 *)(A + o_R1); su.R3 = (double2 *)(A + o_R3); su.R4 = (double2 *)(A + o_R4);
     su.b_node = h->b_node;
 
     if (cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
@@ -330,12 +329,12 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
 
     StepParams &p = h->sp;
     p.nr = nr; p.nth = nth; p.dt = h->dt; p.q = 0.25 * h->dt; p.half_dt = 0.5 * h->dt;
-    p.pred = PredPlanes{su.pa, su.pb, su.KAp, su.KCp, su.P1, su.P2, su.Q1, su.Q2};
-    p.corr = CorrPlanes{su.tb, su.KAc, su.KCc, su.R1, su.R2, su.R3, su.R4};
+    p.pred = PredPlanes{su.pa, su.pb, su.eb, su.KAp, su.KCp, su.P1, su.Q1, su.Q2};
+    p.corr = CorrPlanes{su.tb, su.nt2, su.KAc, su.KCc, su.R1, su.R3, su.R4};
     p.src = SourceWindow{0, -1, 0, -1, nullptr, nullptr, 0.0, 0};
     p.ext = Extraction{-1, 1, 1, nullptr};
     p.step_base = h->d_step;
-    h->variant = nth <= 1024 ? 0 : 1;
+    h->variant = nth <= 1024 ? 2 : 1;
     if (nth <= 1024) {
         const size_t smem = fused_smem_bytes(nth);
         if (smem > 48 * 1024 &&
@@ -343,6 +342,12 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
                 cudaSuccess)
             return bail(TEUK_ERR_CUDA);
         choose_launch(h, 0);
+        const size_t ssm = split_smem_bytes(nth);
+        if (ssm > 48 * 1024)
+            for (int w = 0; w < 2; ++w)
+                if (cudaFuncSetAttribute(split_kernel_ptr(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) !=
+                    cudaSuccess)
+                    return bail(TEUK_ERR_CUDA);
     }
     if (h->variant == 1) {
         if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return bail(TEUK_ERR_OOM); }
@@ -489,6 +494,9 @@ static cudaError_t launch_one(teuk_handle *h, int from, int k, cudaStream_t st)
     if (h->variant == 0)
         return launch_step_fused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], k,
                                  h->rows_per_block, h->nblocks, st);
+    if (h->variant == 2)
+        return launch_step_split(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], h->phiH,
+                                 h->piH, k, st);
     return launch_step_unfused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], h->phiH,
                                h->piH, k, st);
 }
@@ -541,7 +549,7 @@ extern "C" int teuk_step(teuk_handle *h, long n)
 extern "C" int teuk_set_launch(teuk_handle *h, int rows_per_block)
 {
     if (!h || rows_per_block < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_launch: rows_per_block < 0");
-    if (h->nth > 1024) return fail(h, TEUK_ERR_STATE, "teuk_set_launch: fused kernel needs nth <= 1024");
+    if (h->nth > kFusedMaxNth) return fail(h, TEUK_ERR_STATE, "teuk_set_launch: fused kernel needs nth <= 512");
     CU(cudaStreamSynchronize(h->stream));
     destroy_graphs(h);
     choose_launch(h, rows_per_block);
@@ -559,16 +567,17 @@ extern "C" int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *n
 extern "C" long teuk_launches_for(const teuk_handle *h, long n)
 {
     if (!h || n < 0) return -1;
-    const long per = h->variant == 0 ? 1 : 2;
+    const long per = h->variant == 0 ? 1 : 2;  // the two-kernel and split variants launch twice per step
     const long full = n / kChunk, rem = n % kChunk;
     return full * (kChunk * per + 1) + (rem ? rem * per + 1 : 0);
 }
 
 extern "C" int teuk_set_kernel(teuk_handle *h, int variant)
 {
-    if (!h || variant < 0 || variant > 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: variant 0 or 1");
-    if (variant == 0 && h->nth > 1024) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: fused kernel needs nth <= 1024");
-    if (variant == 1 && !h->phiH) {
+    if (!h || variant < 0 || variant > 2) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: variant 0, 1 or 2");
+    if ((variant == 0 && h->nth > kFusedMaxNth) || (variant == 2 && h->nth > 1024))
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: fused kernel needs nth <= 512, split nth <= 1024");
+    if (variant != 0 && !h->phiH) {
         const size_t Nm = (size_t)(h->nr - 1) * h->nth;
         if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) {
             cudaGetLastError();

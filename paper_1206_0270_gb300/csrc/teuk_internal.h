@@ -5,25 +5,29 @@
 // coefficients, apart from the source phase.  The setup kernel folds every
 // constant of the scheme (dt, h, dtheta, the 1/2 averages, the diagonal of
 // the angular stencil, the pole ghosts) into per-point coefficient planes, so
-// that a step costs 60 FP64 fused multiply-adds per point (FP64 throughput
-// is the scarce resource on GB300; bytes are not).
+// that a step costs 56 FP64 instructions per point (FP64 throughput is the
+// scarce resource on GB300; bytes are not).
 //
 // With u_i = (Phi_i, Pi_i) the state at node i, sigma_j = Phi_{i,j} +
-// Phi_{i+1,j}, the predictor (Eq. 3) at the mid-point h = i + 1/2 reads
-//   Phi^h = pa Phi_i + pb Phi_{i+1} + (dt/4)(Pi_i + Pi_{i+1})
-//   Pi^h  = P1 Pi_i + P2 Pi_{i+1} + Q1 Phi_i + Q2 Phi_{i+1}
+// Phi_{i+1,j} and tau = Pi_i + Pi_{i+1}, the predictor (Eq. 3) at the
+// mid-point h = i + 1/2 reads
+//   Phi^h = pa Phi_i + pb Phi_{i+1} + (dt/4) tau
+//   Pi^h  = P1 tau + eb Pi_{i+1} + Q1 Phi_i + Q2 Phi_{i+1}
 //           + KA sigma_{j+1} + KC sigma_{j-1} + gP e^{-i m Omega t_n}
-// and with sigma'_j = Phi^{i+1/2}_j + Phi^{i-1/2}_j the corrector (Eq. 4)
-//   Phi^{n+1} = Phi_i - tb Phi^{i+1/2} + tb Phi^{i-1/2} + (dt/2)(Pi^{i+1/2} + Pi^{i-1/2})
-//   Pi^{n+1}  = Pi_i + R1 Pi^{i+1/2} + R2 Pi^{i-1/2} + R3 Phi^{i+1/2} + R4 Phi^{i-1/2}
+// (P1 Pi_i + P2 Pi_{i+1} regrouped, eb = P2 - P1) and with
+// sigma'_j = Phi^{i+1/2}_j + Phi^{i-1/2}_j, tau' = Pi^{i+1/2} + Pi^{i-1/2} the
+// corrector (Eq. 4)
+//   Phi^{n+1} = Phi_i - tb Phi^{i+1/2} + tb Phi^{i-1/2} + (dt/2) tau'
+//   Pi^{n+1}  = Pi_i + R1 tau' + nt2 Pi^{i-1/2} + R3 Phi^{i+1/2} + R4 Phi^{i-1/2}
 //               + KA' sigma'_{j+1} + KC' sigma'_{j-1} + gC e^{-i m Omega (t_n + dt/2)}
+// (R1 Pi^{i+1/2} + R2 Pi^{i-1/2} regrouped, nt2 = R2 - R1)
 // where (beta = dt b/(2h), gamma = dt d/(2h), A/B/C the angular stencil
 // weights of L_theta with the ghosts folded into B at j = 0 and j = nth-1):
 //   pa = 1/2 + beta, pb = 1/2 - beta,
-//   P1 = 1/2 - beta - (dt/4) c_t,  P2 = 1/2 + beta - (dt/4) c_t,
+//   P1 = 1/2 - beta - (dt/4) c_t,  P2 = 1/2 + beta - (dt/4) c_t,  eb = 2 beta,
 //   Q1 = -gamma - (dt/4)(W - kappa B),  Q2 = gamma - (dt/4)(W - kappa B),
 //   KA = (dt/4) kappa A, KC = (dt/4) kappa C, gP = (dt/2) G      (mid-point values)
-//   tb = 2 beta, R1 = 2 beta - (dt/2) c_t, R2 = -2 beta - (dt/2) c_t,
+//   tb = 2 beta, R1 = 2 beta - (dt/2) c_t, R2 = -2 beta - (dt/2) c_t, nt2 = -4 beta,
 //   R3 = 2 gamma - (dt/2)(W - kappa B), R4 = -2 gamma - (dt/2)(W - kappa B),
 //   KA' = (dt/2) kappa A, KC' = (dt/2) kappa C, gC = dt G        (node values)
 #pragma once
@@ -35,14 +39,14 @@ namespace teuk {
 
 // Predictor planes: rows hp = 0 .. nr-2 (mid-point r*_{hp+1/2}), nth values each.
 struct PredPlanes {
-    const double *pa, *pb, *KA, *KC;
-    const double2 *P1, *P2, *Q1, *Q2;
+    const double *pa, *pb, *eb, *KA, *KC;
+    const double2 *P1, *Q1, *Q2;
 };
 
 // Corrector planes: rows i = 0 .. nr-1 (rows 0 and nr-1 unused).
 struct CorrPlanes {
-    const double *tb, *KA, *KC;
-    const double2 *R1, *R2, *R3, *R4;
+    const double *tb, *nt2, *KA, *KC;
+    const double2 *R1, *R3, *R4;
 };
 
 // Source restricted to the rows where the Gaussian is non-zero.
@@ -82,10 +86,10 @@ struct SetupParams {
     const double *r_node, *D_node, *r_mid, *D_mid;  // radial tables (Delta as D)
     const double *sin_th, *cos_th, *cot_th;         // angular tables
     // outputs
-    double *pa, *pb, *KAp, *KCp;
-    double2 *P1, *P2, *Q1, *Q2;
-    double *tb, *KAc, *KCc;
-    double2 *R1, *R2, *R3, *R4;
+    double *pa, *pb, *eb, *KAp, *KCp;
+    double2 *P1, *Q1, *Q2;
+    double *tb, *nt2, *KAc, *KCc;
+    double2 *R1, *R3, *R4;
     double *b_node;
 };
 
@@ -98,6 +102,9 @@ cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const dou
 cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const double2 *Pi,
                                 double2 *PhiO, double2 *PiO, double2 *PhiH, double2 *PiH, int k,
                                 cudaStream_t st);
+
+cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
+                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st);
 
 cudaError_t launch_advance(long long *step_base, long long by, cudaStream_t st);
 
@@ -112,5 +119,8 @@ cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long l
 int fused_block_threads(int nth);
 size_t fused_smem_bytes(int nth);
 const void *fused_kernel_ptr();
+int split_rows_per_block(int nth);
+size_t split_smem_bytes(int nth);
+const void *split_kernel_ptr(int which);
 
 }  // namespace teuk

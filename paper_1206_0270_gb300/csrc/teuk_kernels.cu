@@ -5,7 +5,7 @@
 // point-particle source added to the Pi row and the waveform row copied to a
 // ring buffer.  All constants of the scheme are folded into the coefficient
 // planes built by setup_kernel (the formulas are in teuk_internal.h), so the
-// step costs 60 FP64 FMA-class instructions per point.
+// step costs 56 FP64 instructions per point (8 adds, 4 multiplies, 44 FMAs).
 //
 // The fused kernel assigns one thread per theta index j and lets each CTA
 // march along r* over a contiguous strip of rows: the predictor value at
@@ -21,6 +21,23 @@ namespace teuk {
 // Complex helpers: acc += c * x with FP64 FMAs
 // ---------------------------------------------------------------------------
 
+// FP64 adds and multiplies.  On GB300 DADD and DMUL issue at 1.6/clk/SM
+// against 1.9/clk/SM for DFMA; with TEUK_FMA_FOR_ADD they are issued as
+// fma.rn.f64 (a * 1 + b, a * b + (-0)), which round identically.
+#ifdef TEUK_FMA_FOR_ADD
+__device__ __forceinline__ double fma_ptx(double a, double b, double c)
+{
+    double d;
+    asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(d) : "d"(a), "d"(b), "d"(c));
+    return d;
+}
+__device__ __forceinline__ double dadd(double a, double b) { return fma_ptx(a, 1.0, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return fma_ptx(a, b, -0.0); }
+#else
+__device__ __forceinline__ double dadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double dmul(double a, double b) { return a * b; }
+#endif
+
 __device__ __forceinline__ void cfma(double2 &acc, const double2 c, const double2 x)
 {
     acc.x = fma(c.x, x.x, acc.x);
@@ -32,9 +49,9 @@ __device__ __forceinline__ void cfma(double2 &acc, const double2 c, const double
 __device__ __forceinline__ double2 cmul(const double2 c, const double2 x)
 {
     double2 r;
-    r.x = c.x * x.x;
+    r.x = dmul(c.x, x.x);
     r.x = fma(-c.y, x.y, r.x);
-    r.y = c.x * x.y;
+    r.y = dmul(c.x, x.y);
     r.y = fma(c.y, x.x, r.y);
     return r;
 }
@@ -47,7 +64,7 @@ __device__ __forceinline__ void rfma(double2 &acc, const double c, const double2
 
 __device__ __forceinline__ double2 add2(const double2 a, const double2 b)
 {
-    return make_double2(a.x + b.x, a.y + b.y);
+    return make_double2(dadd(a.x, b.x), dadd(a.y, b.y));
 }
 
 template <typename T>
@@ -90,8 +107,8 @@ __global__ void setup_kernel(SetupParams sp)
         const double q = 0.25 * sp.dt;
         sp.pa[k] = 0.5 + beta;
         sp.pb[k] = 0.5 - beta;
+        sp.eb[k] = 2.0 * beta;
         sp.P1[k] = make_double2(0.5 - beta - q * c.ct_re, -q * c.ct_im);
-        sp.P2[k] = make_double2(0.5 + beta - q * c.ct_re, -q * c.ct_im);
         sp.Q1[k] = make_double2(-g_re - q * wr, -g_im - q * wi);
         sp.Q2[k] = make_double2(g_re - q * wr, g_im - q * wi);
         sp.KAp[k] = q * c.kappa * A;
@@ -99,8 +116,8 @@ __global__ void setup_kernel(SetupParams sp)
     } else {
         const double hd = 0.5 * sp.dt;
         sp.tb[k] = 2.0 * beta;
+        sp.nt2[k] = -4.0 * beta;
         sp.R1[k] = make_double2(2.0 * beta - hd * c.ct_re, -hd * c.ct_im);
-        sp.R2[k] = make_double2(-2.0 * beta - hd * c.ct_re, -hd * c.ct_im);
         sp.R3[k] = make_double2(2.0 * g_re - hd * wr, 2.0 * g_im - hd * wi);
         sp.R4[k] = make_double2(-2.0 * g_re - hd * wr, -2.0 * g_im - hd * wi);
         sp.KAc[k] = hd * c.kappa * A;
@@ -126,47 +143,99 @@ struct HalfStep {
     double2 phi, pi;
 };
 
-// Predictor at the mid-point row hp, theta index with plane offset k.
-// phi0/pi0: u at row hp, phi1/pi1: u at row hp + 1, sup/sdn: sigma at j+1, j-1.
-__device__ __forceinline__ HalfStep predict(const StepParams &p, size_t k, double2 phi0, double2 pi0,
-                                            double2 phi1, double2 pi1, double2 sup, double2 sdn)
+// Scheme coefficients of one predictor point (mid-point row) and one corrector
+// point (node row), held in registers so that a row's loads can be issued
+// one iteration ahead of their use.
+struct PredCoef {
+    double pa, pb, eb, KA, KC;
+    double2 P1, Q1, Q2;
+};
+struct CorrCoef {
+    double tb, nt2, KA, KC;
+    double2 R1, R3, R4;
+};
+
+__device__ __forceinline__ PredCoef load_pred(const StepParams &p, size_t k)
 {
+    PredCoef c;
+    c.pa = ldg(p.pred.pa + k);
+    c.pb = ldg(p.pred.pb + k);
+    c.eb = ldg(p.pred.eb + k);
+    c.KA = ldg(p.pred.KA + k);
+    c.KC = ldg(p.pred.KC + k);
+    c.P1 = ldg(p.pred.P1 + k);
+    c.Q1 = ldg(p.pred.Q1 + k);
+    c.Q2 = ldg(p.pred.Q2 + k);
+    return c;
+}
+
+__device__ __forceinline__ CorrCoef load_corr(const StepParams &p, size_t k)
+{
+    CorrCoef c;
+    c.tb = ldg(p.corr.tb + k);
+    c.nt2 = ldg(p.corr.nt2 + k);
+    c.KA = ldg(p.corr.KA + k);
+    c.KC = ldg(p.corr.KC + k);
+    c.R1 = ldg(p.corr.R1 + k);
+    c.R3 = ldg(p.corr.R3 + k);
+    c.R4 = ldg(p.corr.R4 + k);
+    return c;
+}
+
+// Predictor (Eq. 3) at one mid-point.  phi0/pi0: u at row hp, phi1/pi1: u at
+// row hp + 1, sup/sdn: sigma = Phi_hp + Phi_{hp+1} at j+1, j-1.
+__device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, double2 phi0, double2 pi0,
+                                              double2 phi1, double2 pi1, double2 sup, double2 sdn)
+{
+    // P1 Pi_i + P2 Pi_{i+1} = P1 tau + (P2 - P1) Pi_{i+1}, tau = Pi_i + Pi_{i+1}, P2 - P1 = 2 beta (eb)
     HalfStep o;
-    const double pa = ldg(p.pred.pa + k), pb = ldg(p.pred.pb + k);
-    o.phi = make_double2(pa * phi0.x, pa * phi0.y);
-    rfma(o.phi, pb, phi1);
-    rfma(o.phi, p.q, pi0);
-    rfma(o.phi, p.q, pi1);
-    o.pi = cmul(ldg(p.pred.P1 + k), pi0);
-    cfma(o.pi, ldg(p.pred.P2 + k), pi1);
-    cfma(o.pi, ldg(p.pred.Q1 + k), phi0);
-    cfma(o.pi, ldg(p.pred.Q2 + k), phi1);
-    rfma(o.pi, ldg(p.pred.KA + k), sup);
-    rfma(o.pi, ldg(p.pred.KC + k), sdn);
+    const double2 tau = add2(pi0, pi1);
+    o.phi = make_double2(dmul(c.pa, phi0.x), dmul(c.pa, phi0.y));
+    rfma(o.phi, c.pb, phi1);
+    rfma(o.phi, q, tau);
+    o.pi = cmul(c.P1, tau);
+    rfma(o.pi, c.eb, pi1);
+    cfma(o.pi, c.Q1, phi0);
+    cfma(o.pi, c.Q2, phi1);
+    rfma(o.pi, c.KA, sup);
+    rfma(o.pi, c.KC, sdn);
     return o;
 }
 
-// Corrector at node row i (plane offset k).  hp: half step at i + 1/2, hm: at i - 1/2,
+__device__ __forceinline__ HalfStep predict(const StepParams &p, size_t k, double2 phi0, double2 pi0,
+                                            double2 phi1, double2 pi1, double2 sup, double2 sdn)
+{
+    return predict_c(load_pred(p, k), p.q, phi0, pi0, phi1, pi1, sup, sdn);
+}
+
+// Corrector (Eq. 4) at one node.  hp: half step at i + 1/2, hm: at i - 1/2,
 // sup/sdn: sigma' = Phi^{i+1/2} + Phi^{i-1/2} at j+1, j-1.
+__device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, double2 phi, double2 pi,
+                                          const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn,
+                                          double2 *phi_out, double2 *pi_out)
+{
+    // R1 Pi^{+} + R2 Pi^{-} = R1 tau' + (R2 - R1) Pi^{-}, tau' = Pi^{+} + Pi^{-}, R2 - R1 = -2 tb (nt2)
+    const double2 tau = add2(hp.pi, hm.pi);
+    double2 nphi = phi;
+    rfma(nphi, -c.tb, hp.phi);
+    rfma(nphi, c.tb, hm.phi);
+    rfma(nphi, half_dt, tau);
+    double2 npi = pi;
+    cfma(npi, c.R1, tau);
+    rfma(npi, c.nt2, hm.pi);
+    cfma(npi, c.R3, hp.phi);
+    cfma(npi, c.R4, hm.phi);
+    rfma(npi, c.KA, sup);
+    rfma(npi, c.KC, sdn);
+    *phi_out = nphi;
+    *pi_out = npi;
+}
+
 __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 phi, double2 pi,
                                         const HalfStep &hp, const HalfStep &hm, double2 sup,
                                         double2 sdn, double2 *phi_out, double2 *pi_out)
 {
-    const double tb = ldg(p.corr.tb + k);
-    double2 nphi = phi;
-    rfma(nphi, -tb, hp.phi);
-    rfma(nphi, tb, hm.phi);
-    rfma(nphi, p.half_dt, hp.pi);
-    rfma(nphi, p.half_dt, hm.pi);
-    double2 npi = pi;
-    cfma(npi, ldg(p.corr.R1 + k), hp.pi);
-    cfma(npi, ldg(p.corr.R2 + k), hm.pi);
-    cfma(npi, ldg(p.corr.R3 + k), hp.phi);
-    cfma(npi, ldg(p.corr.R4 + k), hm.phi);
-    rfma(npi, ldg(p.corr.KA + k), sup);
-    rfma(npi, ldg(p.corr.KC + k), sdn);
-    *phi_out = nphi;
-    *pi_out = npi;
+    correct_c(load_corr(p, k), p.half_dt, phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -178,7 +247,7 @@ __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 p
 size_t fused_smem_bytes(int nth) { return sizeof(double2) * 4 * (size_t)(nth + 2); }
 int fused_block_threads(int nth) { return ((nth + 31) / 32) * 32; }
 
-__global__ void __launch_bounds__(1024) lw_step_fused(StepParams p, const double2 *__restrict__ Phi,
+__global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2 *__restrict__ Phi,
                                                       const double2 *__restrict__ Pi,
                                                       double2 *__restrict__ PhiO,
                                                       double2 *__restrict__ PiO, int k, int rpb)
@@ -225,14 +294,29 @@ __global__ void __launch_bounds__(1024) lw_step_fused(StepParams p, const double
     phc = phn;
     pic = pin;
 
+    // Loads for row i are issued one iteration ahead: u_{i+1} and the
+    // predictor/corrector coefficients of row i arrive while row i-1 computes.
+    double2 phn_nx = Phi[(size_t)(i0 + 1) * nth + jj], pin_nx = Pi[(size_t)(i0 + 1) * nth + jj];
+    PredCoef pc_nx = load_pred(p, (size_t)i0 * nth + jj);
+    CorrCoef cc_nx = load_corr(p, (size_t)i0 * nth + jj);
     int buf = 1;
     for (int i = i0; i < i1; ++i) {
-        phn = Phi[(size_t)(i + 1) * nth + jj];
-        pin = Pi[(size_t)(i + 1) * nth + jj];
+        phn = phn_nx;
+        pin = pin_nx;
+        const PredCoef pc = pc_nx;
+        const CorrCoef cc = cc_nx;
+        {
+            const int inx = min(i + 1, i1 - 1);  // clamped: the last prefetch is unused
+            const int unx = min(i + 2, p.nr - 1);
+            phn_nx = Phi[(size_t)unx * nth + jj];
+            pin_nx = Pi[(size_t)unx * nth + jj];
+            pc_nx = load_pred(p, (size_t)inx * nth + jj);
+            cc_nx = load_corr(p, (size_t)inx * nth + jj);
+        }
         double2 *sg = s_sig + buf * W;
         if (act) sg[j + 1] = add2(phc, phn);
         __syncthreads();
-        HalfStep hp = predict(p, (size_t)i * nth + jj, phc, pic, phn, pin, sg[jj + 2], sg[jj]);
+        HalfStep hp = predict_c(pc, p.q, phc, pic, phn, pin, sg[jj + 2], sg[jj]);
         if (src_mid && i >= sw.mid_lo && i <= sw.mid_hi)
             rfma(hp.pi, ldg(sw.gP + (size_t)(i - sw.mid_lo) * nth + jj), s_phase[0]);
 
@@ -241,7 +325,7 @@ __global__ void __launch_bounds__(1024) lw_step_fused(StepParams p, const double
         __syncthreads();
         const size_t kc = (size_t)i * nth + jj;
         double2 nphi, npi;
-        correct(p, kc, phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
+        correct_c(cc, p.half_dt, phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
         if (src_node && i >= sw.node_lo && i <= sw.node_hi)
             rfma(npi, ldg(sw.gC + (size_t)(i - sw.node_lo) * nth + jj), s_phase[1]);
         if (act) {
@@ -344,6 +428,108 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
     lw_predict_kernel<<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
     lw_correct_kernel<<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
                                                                                   PhiO, PiO, k);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Split variant: predictor and corrector as two kernels over 2D tiles of
+// R rows x nth columns (one point per thread); sigma is formed once per point
+// and shared with the angular neighbours through shared memory.
+// ---------------------------------------------------------------------------
+
+int split_rows_per_block(int nth)
+{
+    const int cols = fused_block_threads(nth);
+    return cols >= 256 ? 1 : 256 / cols;
+}
+
+__global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
+                                                         const double2 *__restrict__ Pi,
+                                                         double2 *__restrict__ PhiH,
+                                                         double2 *__restrict__ PiH, int k)
+{
+    extern __shared__ double2 smem[];
+    const int nth = p.nth, W = nth + 2;
+    const int j = threadIdx.x;
+    const bool colok = j < nth;
+    const int jj = colok ? j : nth - 1;
+    const int hp = blockIdx.x * blockDim.y + threadIdx.y;
+    const bool rowok = hp < p.nr - 1;
+    const int hq = rowok ? hp : p.nr - 2;
+    double2 *row = smem + threadIdx.y * W;
+    if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
+    const size_t k0 = (size_t)hq * nth + jj;
+    const PredCoef c = load_pred(p, k0);
+    const double2 phi0 = Phi[k0], pi0 = Pi[k0], phi1 = Phi[k0 + nth], pi1 = Pi[k0 + nth];
+    if (colok) row[j + 1] = add2(phi0, phi1);
+    __syncthreads();
+    HalfStep o = predict_c(c, p.q, phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
+    const SourceWindow &sw = p.src;
+    if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
+        const long long n = *p.step_base + k;
+        rfma(o.pi, ldg(sw.gP + (size_t)(hq - sw.mid_lo) * nth + jj), unit_phase(sw.m_omega * ((double)n * p.dt)));
+    }
+    if (colok && rowok) {
+        PhiH[k0] = o.phi;
+        PiH[k0] = o.pi;
+    }
+}
+
+__global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
+                                                         const double2 *__restrict__ Pi,
+                                                         const double2 *__restrict__ PhiH,
+                                                         const double2 *__restrict__ PiH,
+                                                         double2 *__restrict__ PhiO,
+                                                         double2 *__restrict__ PiO, int k)
+{
+    extern __shared__ double2 smem[];
+    const int nth = p.nth, W = nth + 2;
+    const int j = threadIdx.x;
+    const bool colok = j < nth;
+    const int jj = colok ? j : nth - 1;
+    const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
+    const bool rowok = i <= p.nr - 2;
+    const int iq = rowok ? i : p.nr - 2;
+    double2 *row = smem + threadIdx.y * W;
+    if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
+    const size_t kc = (size_t)iq * nth + jj;
+    const CorrCoef c = load_corr(p, kc);
+    HalfStep hp, hm;
+    hp.phi = PhiH[kc];
+    hp.pi = PiH[kc];
+    hm.phi = PhiH[kc - nth];
+    hm.pi = PiH[kc - nth];
+    const double2 phi = Phi[kc], pi = Pi[kc];
+    if (colok) row[j + 1] = add2(hp.phi, hm.phi);
+    __syncthreads();
+    double2 nphi, npi;
+    correct_c(c, p.half_dt, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
+    const long long n = *p.step_base + k;
+    const SourceWindow &sw = p.src;
+    if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
+        rfma(npi, ldg(sw.gC + (size_t)(iq - sw.node_lo) * nth + jj),
+             unit_phase(sw.m_omega * (((double)n + 0.5) * p.dt)));
+    if (colok && rowok) {
+        PhiO[kc] = nphi;
+        PiO[kc] = npi;
+        if (iq == p.ext.i_ext && ((n + 1) % p.ext.every) == 0) {
+            const long long slot = ((n + 1) / p.ext.every - 1) % p.ext.capacity;
+            p.ext.ring[(size_t)slot * nth + j] = nphi;
+        }
+    }
+}
+
+size_t split_smem_bytes(int nth) { return sizeof(double2) * (size_t)split_rows_per_block(nth) * (nth + 2); }
+const void *split_kernel_ptr(int which) { return which ? (const void *)lw_correct_split : (const void *)lw_predict_split; }
+
+cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
+                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st)
+{
+    const int R = split_rows_per_block(p.nth);
+    const dim3 block(fused_block_threads(p.nth), R);
+    const size_t smem = split_smem_bytes(p.nth);
+    lw_predict_split<<<(p.nr - 1 + R - 1) / R, block, smem, st>>>(p, Phi, Pi, PhiH, PiH, k);
+    lw_correct_split<<<(p.nr - 2 + R - 1) / R, block, smem, st>>>(p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);
     return cudaGetLastError();
 }
 

@@ -82,7 +82,7 @@ def assert_parity(out, tol=TOL):
 SRC = dict(r0=8.0, sigma=0.5, amplitude=1.0, prograde=True)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("a,s,m", [(0.9, -2, 2), (0.0, -2, 2), (0.5, 0, 1), (0.7, 2, -3), (0.3, -2, 0)])
 def test_parity_small_grids(teuk, kernel, a, s, m):
     out = run_pair(teuk, 150, 24, -20.0, 40.0, a, s, m, 130, source=SRC, ext=(10.0, 7), kernel=kernel,
@@ -97,9 +97,10 @@ def test_parity_ragged_and_tiny(teuk, nr, nth):
     assert_parity(out)
 
 
-def test_parity_wide_theta_fused_limit_and_beyond(teuk):
-    # nth = 1024 is the widest fused block; 1030 runs the two-kernel variant.
-    for nth, kern in [(1024, 0), (1030, 1)]:
+def test_parity_wide_theta_kernel_limits(teuk):
+    # nth = 512 is the widest fused block, 1024 the widest split tile; 1030
+    # runs the two-kernel variant.
+    for nth, kern in [(512, 0), (513, 2), (1024, 2), (1030, 1)]:
         out = run_pair(teuk, 40, nth, -10.0, 30.0, 0.9, -2, 2, 6, source=dict(r0=5.0, sigma=1.0), kernel=kern,
                        seed=1)
         assert_parity(out)
@@ -146,12 +147,36 @@ def test_graph_and_direct_launches_agree_bitwise(teuk):
     np.testing.assert_array_equal(a["gpu_w"][1], b["gpu_w"][1])
 
 
-def test_fused_and_two_kernel_variants_agree_bitwise(teuk):
+def test_kernel_variants_agree_bitwise(teuk):
     kw = dict(source=SRC, ext=(10.0, 5), seed=9)
     a = run_pair(teuk, 100, 48, -20.0, 40.0, 0.9, -2, 1, 150, kernel=0, **kw)
-    b = run_pair(teuk, 100, 48, -20.0, 40.0, 0.9, -2, 1, 150, kernel=1, **kw)
-    for x, y in zip(a["gpu"], b["gpu"]):
-        np.testing.assert_array_equal(x, y)
+    for kern in (1, 2):
+        b = run_pair(teuk, 100, 48, -20.0, 40.0, 0.9, -2, 1, 150, kernel=kern, **kw)
+        for x, y in zip(a["gpu"], b["gpu"]):
+            np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(a["gpu_w"][1], b["gpu_w"][1])
+
+
+def test_launch_shapes_agree_bitwise(teuk):
+    # the fused kernel's strip length changes which rows are recomputed, not results
+    nr, nth = 300, 40
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, 0.9, -2, 2)
+    u = inputs.random_fields(nr, nth, seed=12)
+    ref = None
+    for rpb in [1, 3, 16, 298]:
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
+        g.set_initial(*u)
+        g.set_source(**SRC)
+        g.set_launch(rpb)
+        assert g.launch_shape()[0] == rpb
+        g.step(70)
+        st = g.state()
+        if ref is None:
+            ref = st
+        else:
+            np.testing.assert_array_equal(st[0], ref[0])
+            np.testing.assert_array_equal(st[1], ref[1])
+        g.close()
 
 
 def test_runs_are_deterministic(teuk):
