@@ -329,6 +329,7 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
 
     StepParams &p = h->sp;
     p.nr = nr; p.nth = nth; p.dt = h->dt; p.q = 0.25 * h->dt; p.half_dt = 0.5 * h->dt;
+    p.one = 1.0; p.nzero = -0.0;
     p.pred = PredPlanes{su.pa, su.pb, su.eb, su.KAp, su.KCp, su.P1, su.Q1, su.Q2};
     p.corr = CorrPlanes{su.tb, su.nt2, su.KAc, su.KCc, su.R1, su.R3, su.R4};
     p.src = SourceWindow{0, -1, 0, -1, nullptr, nullptr, 0.0, 0};
@@ -349,7 +350,7 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
                     cudaSuccess)
                     return bail(TEUK_ERR_CUDA);
     }
-    if (h->variant == 1) {
+    if (h->variant != 0) {  // the two-kernel variants keep the half step in device memory
         if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return bail(TEUK_ERR_OOM); }
         h->piH = h->phiH + Nm;
     }
@@ -491,6 +492,10 @@ extern "C" int teuk_set_extraction(teuk_handle *h, double rstar_ext, int every, 
 
 static cudaError_t launch_one(teuk_handle *h, int from, int k, cudaStream_t st)
 {
+    // never launch a variant without its buffers
+    if (!h->phi[from] || !h->pi[from] || !h->phi[1 - from] || !h->pi[1 - from] ||
+        (h->variant != 0 && (!h->phiH || !h->piH)))
+        return cudaErrorInvalidValue;
     if (h->variant == 0)
         return launch_step_fused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], k,
                                  h->rows_per_block, h->nblocks, st);

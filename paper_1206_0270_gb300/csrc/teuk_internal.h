@@ -69,6 +69,7 @@ struct Extraction {
 struct StepParams {
     int nr, nth;
     double dt, q, half_dt; // dt, dt/4, dt/2
+    double one, nzero;     // 1 and -0: operands that turn FP64 adds and multiplies into FMAs
     PredPlanes pred;
     CorrPlanes corr;
     SourceWindow src;

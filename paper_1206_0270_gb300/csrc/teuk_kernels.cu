@@ -5,7 +5,8 @@
 // point-particle source added to the Pi row and the waveform row copied to a
 // ring buffer.  All constants of the scheme are folded into the coefficient
 // planes built by setup_kernel (the formulas are in teuk_internal.h), so the
-// step costs 56 FP64 instructions per point (8 adds, 4 multiplies, 44 FMAs).
+// step costs 56 FP64 instructions per point (8 adds and 4 multiplies, issued
+// as FMAs, and 44 FMAs).
 //
 // The fused kernel assigns one thread per theta index j and lets each CTA
 // march along r* over a contiguous strip of rows: the predictor value at
@@ -21,22 +22,21 @@ namespace teuk {
 // Complex helpers: acc += c * x with FP64 FMAs
 // ---------------------------------------------------------------------------
 
-// FP64 adds and multiplies.  On GB300 DADD and DMUL issue at 1.6/clk/SM
-// against 1.9/clk/SM for DFMA; with TEUK_FMA_FOR_ADD they are issued as
-// fma.rn.f64 (a * 1 + b, a * b + (-0)), which round identically.
-#ifdef TEUK_FMA_FOR_ADD
-__device__ __forceinline__ double fma_ptx(double a, double b, double c)
+// FP64 adds and multiplies are issued as fma.rn.f64: a + b = fma(a, 1, b) and
+// a * b = fma(a, b, -0) round identically, and on GB300 DFMA issues at
+// 1.9/clk/SM against 1.6/clk/SM for DADD and DMUL.  The constants 1 and -0
+// come from kernel parameters (Ops) so that the compiler cannot turn the FMA
+// back into an add or a multiply.
+struct Ops {
+    double one, nzero;
+};
+
+__device__ __forceinline__ double fma_rn(double a, double b, double c)
 {
     double d;
     asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(d) : "d"(a), "d"(b), "d"(c));
     return d;
 }
-__device__ __forceinline__ double dadd(double a, double b) { return fma_ptx(a, 1.0, b); }
-__device__ __forceinline__ double dmul(double a, double b) { return fma_ptx(a, b, -0.0); }
-#else
-__device__ __forceinline__ double dadd(double a, double b) { return a + b; }
-__device__ __forceinline__ double dmul(double a, double b) { return a * b; }
-#endif
 
 __device__ __forceinline__ void cfma(double2 &acc, const double2 c, const double2 x)
 {
@@ -46,12 +46,12 @@ __device__ __forceinline__ void cfma(double2 &acc, const double2 c, const double
     acc.y = fma(c.y, x.x, acc.y);
 }
 
-__device__ __forceinline__ double2 cmul(const double2 c, const double2 x)
+__device__ __forceinline__ double2 cmul(const double2 c, const double2 x, const Ops o)
 {
     double2 r;
-    r.x = dmul(c.x, x.x);
+    r.x = fma_rn(c.x, x.x, o.nzero);
     r.x = fma(-c.y, x.y, r.x);
-    r.y = dmul(c.x, x.y);
+    r.y = fma_rn(c.x, x.y, o.nzero);
     r.y = fma(c.y, x.x, r.y);
     return r;
 }
@@ -62,9 +62,9 @@ __device__ __forceinline__ void rfma(double2 &acc, const double c, const double2
     acc.y = fma(c, x.y, acc.y);
 }
 
-__device__ __forceinline__ double2 add2(const double2 a, const double2 b)
+__device__ __forceinline__ double2 add2(const double2 a, const double2 b, const Ops o)
 {
-    return make_double2(dadd(a.x, b.x), dadd(a.y, b.y));
+    return make_double2(fma_rn(a.x, o.one, b.x), fma_rn(a.y, o.one, b.y));
 }
 
 template <typename T>
@@ -184,16 +184,16 @@ __device__ __forceinline__ CorrCoef load_corr(const StepParams &p, size_t k)
 
 // Predictor (Eq. 3) at one mid-point.  phi0/pi0: u at row hp, phi1/pi1: u at
 // row hp + 1, sup/sdn: sigma = Phi_hp + Phi_{hp+1} at j+1, j-1.
-__device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, double2 phi0, double2 pi0,
-                                              double2 phi1, double2 pi1, double2 sup, double2 sdn)
+__device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, const Ops ops, double2 phi0,
+                                              double2 pi0, double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
     // P1 Pi_i + P2 Pi_{i+1} = P1 tau + (P2 - P1) Pi_{i+1}, tau = Pi_i + Pi_{i+1}, P2 - P1 = 2 beta (eb)
     HalfStep o;
-    const double2 tau = add2(pi0, pi1);
-    o.phi = make_double2(dmul(c.pa, phi0.x), dmul(c.pa, phi0.y));
+    const double2 tau = add2(pi0, pi1, ops);
+    o.phi = make_double2(fma_rn(c.pa, phi0.x, ops.nzero), fma_rn(c.pa, phi0.y, ops.nzero));
     rfma(o.phi, c.pb, phi1);
     rfma(o.phi, q, tau);
-    o.pi = cmul(c.P1, tau);
+    o.pi = cmul(c.P1, tau, ops);
     rfma(o.pi, c.eb, pi1);
     cfma(o.pi, c.Q1, phi0);
     cfma(o.pi, c.Q2, phi1);
@@ -202,20 +202,22 @@ __device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, doubl
     return o;
 }
 
+__device__ __forceinline__ Ops ops_of(const StepParams &p) { return Ops{p.one, p.nzero}; }
+
 __device__ __forceinline__ HalfStep predict(const StepParams &p, size_t k, double2 phi0, double2 pi0,
                                             double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
-    return predict_c(load_pred(p, k), p.q, phi0, pi0, phi1, pi1, sup, sdn);
+    return predict_c(load_pred(p, k), p.q, ops_of(p), phi0, pi0, phi1, pi1, sup, sdn);
 }
 
 // Corrector (Eq. 4) at one node.  hp: half step at i + 1/2, hm: at i - 1/2,
 // sup/sdn: sigma' = Phi^{i+1/2} + Phi^{i-1/2} at j+1, j-1.
-__device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, double2 phi, double2 pi,
-                                          const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn,
-                                          double2 *phi_out, double2 *pi_out)
+__device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, const Ops ops, double2 phi,
+                                          double2 pi, const HalfStep &hp, const HalfStep &hm, double2 sup,
+                                          double2 sdn, double2 *phi_out, double2 *pi_out)
 {
     // R1 Pi^{+} + R2 Pi^{-} = R1 tau' + (R2 - R1) Pi^{-}, tau' = Pi^{+} + Pi^{-}, R2 - R1 = -2 tb (nt2)
-    const double2 tau = add2(hp.pi, hm.pi);
+    const double2 tau = add2(hp.pi, hm.pi, ops);
     double2 nphi = phi;
     rfma(nphi, -c.tb, hp.phi);
     rfma(nphi, c.tb, hm.phi);
@@ -235,7 +237,7 @@ __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 p
                                         const HalfStep &hp, const HalfStep &hm, double2 sup,
                                         double2 sdn, double2 *phi_out, double2 *pi_out)
 {
-    correct_c(load_corr(p, k), p.half_dt, phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
+    correct_c(load_corr(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2
     // prologue: predictor at i0 - 1/2 from rows i0 - 1 and i0
     double2 phc = Phi[(size_t)(i0 - 1) * nth + jj], pic = Pi[(size_t)(i0 - 1) * nth + jj];
     double2 phn = Phi[(size_t)i0 * nth + jj], pin = Pi[(size_t)i0 * nth + jj];
-    if (act) s_sig[j + 1] = add2(phc, phn);
+    if (act) s_sig[j + 1] = add2(phc, phn, ops_of(p));
     __syncthreads();
     HalfStep hm = predict(p, (size_t)(i0 - 1) * nth + jj, phc, pic, phn, pin, s_sig[jj + 2], s_sig[jj]);
     if (src_mid && i0 - 1 >= sw.mid_lo && i0 - 1 <= sw.mid_hi)
@@ -314,18 +316,18 @@ __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2
             cc_nx = load_corr(p, (size_t)inx * nth + jj);
         }
         double2 *sg = s_sig + buf * W;
-        if (act) sg[j + 1] = add2(phc, phn);
+        if (act) sg[j + 1] = add2(phc, phn, ops_of(p));
         __syncthreads();
-        HalfStep hp = predict_c(pc, p.q, phc, pic, phn, pin, sg[jj + 2], sg[jj]);
+        HalfStep hp = predict_c(pc, p.q, ops_of(p), phc, pic, phn, pin, sg[jj + 2], sg[jj]);
         if (src_mid && i >= sw.mid_lo && i <= sw.mid_hi)
             rfma(hp.pi, ldg(sw.gP + (size_t)(i - sw.mid_lo) * nth + jj), s_phase[0]);
 
         double2 *sh = s_sgh + buf * W;
-        if (act) sh[j + 1] = add2(hp.phi, hm.phi);
+        if (act) sh[j + 1] = add2(hp.phi, hm.phi, ops_of(p));
         __syncthreads();
         const size_t kc = (size_t)i * nth + jj;
         double2 nphi, npi;
-        correct_c(cc, p.half_dt, phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
+        correct_c(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
         if (src_node && i >= sw.node_lo && i <= sw.node_hi)
             rfma(npi, ldg(sw.gC + (size_t)(i - sw.node_lo) * nth + jj), s_phase[1]);
         if (act) {
@@ -372,8 +374,8 @@ __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
     const double2 phi0 = Phi[k0], pi0 = Pi[k0], phi1 = Phi[k1], pi1 = Pi[k1];
     const int ju = j + 1 < nth ? j + 1 : j, jd = j > 0 ? j - 1 : j;  // edge weights are zero
     const size_t r0 = (size_t)hp * nth, r1 = r0 + nth;
-    const double2 sup = add2(Phi[r0 + ju], Phi[r1 + ju]);
-    const double2 sdn = add2(Phi[r0 + jd], Phi[r1 + jd]);
+    const double2 sup = add2(Phi[r0 + ju], Phi[r1 + ju], ops_of(p));
+    const double2 sdn = add2(Phi[r0 + jd], Phi[r1 + jd], ops_of(p));
     HalfStep o = predict(p, k0, phi0, pi0, phi1, pi1, sup, sdn);
     const SourceWindow &sw = p.src;
     if (sw.active && hp >= sw.mid_lo && hp <= sw.mid_hi) {
@@ -402,8 +404,8 @@ __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
     hm.phi = PhiH[km];
     hm.pi = PiH[km];
     const int ju = j + 1 < nth ? j + 1 : j, jd = j > 0 ? j - 1 : j;
-    const double2 sup = add2(PhiH[kp - j + ju], PhiH[km - j + ju]);
-    const double2 sdn = add2(PhiH[kp - j + jd], PhiH[km - j + jd]);
+    const double2 sup = add2(PhiH[kp - j + ju], PhiH[km - j + ju], ops_of(p));
+    const double2 sdn = add2(PhiH[kp - j + jd], PhiH[km - j + jd], ops_of(p));
     double2 nphi, npi;
     correct(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, &nphi, &npi);
     const long long n = *p.step_base + k;
@@ -461,9 +463,9 @@ __global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const dou
     const size_t k0 = (size_t)hq * nth + jj;
     const PredCoef c = load_pred(p, k0);
     const double2 phi0 = Phi[k0], pi0 = Pi[k0], phi1 = Phi[k0 + nth], pi1 = Pi[k0 + nth];
-    if (colok) row[j + 1] = add2(phi0, phi1);
+    if (colok) row[j + 1] = add2(phi0, phi1, ops_of(p));
     __syncthreads();
-    HalfStep o = predict_c(c, p.q, phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
+    HalfStep o = predict_c(c, p.q, ops_of(p), phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
     const SourceWindow &sw = p.src;
     if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
         const long long n = *p.step_base + k;
@@ -500,10 +502,10 @@ __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const dou
     hm.phi = PhiH[kc - nth];
     hm.pi = PiH[kc - nth];
     const double2 phi = Phi[kc], pi = Pi[kc];
-    if (colok) row[j + 1] = add2(hp.phi, hm.phi);
+    if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops_of(p));
     __syncthreads();
     double2 nphi, npi;
-    correct_c(c, p.half_dt, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
+    correct_c(c, p.half_dt, ops_of(p), phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
     const long long n = *p.step_base + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)

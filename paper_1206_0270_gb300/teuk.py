@@ -110,7 +110,7 @@ def stable_dt(nr, nth, rstar_min, rstar_max, a, s, m, c_r=0.5, c_theta=0.1):
 class Solver:
     """One (a, s, m) evolution; fields are numpy complex128 arrays (nr, nth)."""
 
-    def __init__(self, nr, nth, rstar_min, rstar_max, dt, a, s, m, stream=None, kernel=0):
+    def __init__(self, nr, nth, rstar_min, rstar_max, dt, a, s, m, stream=None, kernel=None):
         self.nr, self.nth = int(nr), int(nth)
         self.grid = teuk_grid(self.nr, self.nth, float(rstar_min), float(rstar_max), float(dt))
         self.dt = float(dt)
@@ -118,7 +118,7 @@ class Solver:
         _check(teuk_create(C.byref(self.grid), float(a), int(s), int(m), _stream_handle(stream),
                            C.byref(h)), what="teuk_create")
         self.h = h
-        if kernel:
+        if kernel is not None:
             self.set_kernel(kernel)
 
     def close(self):

@@ -35,7 +35,7 @@ def rel(a, b):
 
 
 def run_pair(T, nr, nth, rmin, rmax, a, s, m, nsteps, *, init="random", source=None, ext=None,
-             kernel=0, c_theta=0.1, seed=0, chunks=None):
+             kernel=None, c_theta=0.1, seed=0, chunks=None):
     dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m, 0.5, c_theta)
     if init == "random":
         phi0, pi0 = inputs.random_fields(nr, nth, seed=seed)
@@ -128,7 +128,7 @@ def test_parity_schwarzschild_pulse_1024x64_2000_steps(teuk):
 
 def test_parity_kerr_8192x128_full_grid(teuk):
     # The Kerr a = 0.9 workload's grid, orbit and source (r0 = 10M, sigma =
-    # 0.05M) in the launch configuration the benchmark times (fused kernel,
+    # 0.05M) in the launch configuration the benchmark times (default kernel,
     # graph replay), for 640 steps from random smooth data; waveform sampled at
     # r* = 20 every 10 steps (r* = 500 is still silent this early).
     w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
@@ -164,7 +164,7 @@ def test_launch_shapes_agree_bitwise(teuk):
     u = inputs.random_fields(nr, nth, seed=12)
     ref = None
     for rpb in [1, 3, 16, 298]:
-        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2, kernel=0)
         g.set_initial(*u)
         g.set_source(**SRC)
         g.set_launch(rpb)
