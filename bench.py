@@ -42,6 +42,22 @@ FLOPS_PER_UPDATE = 100
 BYTES_PER_UPDATE_ALG = 64
 # Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
 FP64_PEAK_FLOPS = 1.25e12
+# DRAM bytes (read + write) of one time step (predictor + corrector launches) from one
+# ncu capture (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and
+# launch sources whose SHA-256 is recorded here; reported as null otherwise.
+NCU_TRAFFIC = dict(bytes_per_step=310.7e6,
+                   sources_sha256="cf22408a76281ee8bbae348124194205e2fff767d6addf9592e3cca9953c2137")
+TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu", "paper_1206_0270_gb300/csrc/teuk_internal.h",
+                   "paper_1206_0270_gb300/csrc/teuk_api.cu"]
+
+
+def sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def dist_env():
@@ -223,8 +239,10 @@ def run_gpu(args):
     per_launch_s = (total_ms / 1e3) / (args.steps * args.chunk)
     upd_per_launch = (nr - 2) * nth
     achieved = FLOPS_PER_UPDATE * upd_per_launch / per_launch_s
+    traffic = NCU_TRAFFIC["bytes_per_step"] if NCU_TRAFFIC["sources_sha256"] == sources_sha256() else None
     roofline = dict(bound="alu", achieved=achieved / 1e12, peak=FP64_PEAK_FLOPS / 1e12, unit="TFLOP/s",
-                    frac=achieved / FP64_PEAK_FLOPS, traffic=None,
+                    frac=achieved / FP64_PEAK_FLOPS, traffic=traffic,
+                    unit_of_launch="one time step: lw_predict_split + lw_correct_split",
                     peak_source="nominal FP64 (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz)",
                     hbm_alg_gbs=BYTES_PER_UPDATE_ALG * upd_per_launch / per_launch_s / 1e9)
 
