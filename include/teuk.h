@@ -165,6 +165,33 @@ int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *nblocks);
  * configuration (graph replays count their kernel nodes). */
 long teuk_launches_for(const teuk_handle *h, long n);
 
+/* One time step that allocates no device memory.  The paper has no
+ * counterpart: this entry point serves callers that cannot allocate while
+ * they step -- code running while a stream is being captured into a CUDA
+ * graph (cudaMalloc is not permitted there), real-time loops that must not
+ * block in the allocator, and processes whose device memory is owned by
+ * another framework's pool.
+ *
+ * Advances the DEVICE state (phi_in, pi_in) by one time step (Eqs. 3-4, split
+ * kernels) into the DEVICE buffers (phi_out, pi_out), all interleaved complex
+ * [nr][nth] and owned by the caller; outputs must not alias inputs.  Uses the
+ * handle's coefficients and source (phase at t = step_index * dt), issues its
+ * work on the handle's stream and returns without waiting.  No waveform is
+ * sampled; the output boundary rows are set to zero.  The handle's own state,
+ * step counter and ring buffer are neither read nor changed.
+ *
+ * The half step is kept in a static device array of 32 MiB inside libteuk:
+ * every GPU that loads the library holds it until the process exits, and it
+ * limits the grid to (nr - 1) * nth <= 1,048,576 (larger grids and nth > 1024
+ * return TEUK_ERR_BAD_ARG).  All calls share that array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (different streams or
+ * handles running at once) race: issue them one after another on one stream.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The handle's device must be the current device. */
+int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in, double *phi_out,
+                      double *pi_out, long step_index);
+
 /* Message of the last failed call on this handle ("" if none). */
 const char *teuk_last_error(const teuk_handle *h);
 

@@ -594,6 +594,69 @@ extern "C" int teuk_set_kernel(teuk_handle *h, int variant)
     return TEUK_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// One time step without any device allocation
+// ---------------------------------------------------------------------------
+//
+// For callers that cannot allocate device memory while they step: code that
+// runs while a stream is being captured into a CUDA graph (cudaMalloc is not
+// allowed there), real-time loops that must not block in the allocator, and
+// hosts whose device memory is owned by another framework's pool.  The half
+// step lives in the static array below instead of a per-handle buffer.  The
+// array (32 MiB) is part of the library image: every GPU that loads libteuk
+// holds it until the process exits.
+
+static const long long kNoAllocMaxMid = 1LL << 20;  // mid-point values: (nr - 1) * nth <= 1,048,576
+// Layout: Phi^{1/2} [kNoAllocMaxMid] double2, Pi^{1/2} [kNoAllocMaxMid] double2, then
+// the step counter read by the kernels (one 256-byte slot).
+static const size_t kNoAllocScratchBytes = 2 * (size_t)kNoAllocMaxMid * sizeof(double2) + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Host-side device addresses of g_noalloc_scratch, one per device, looked up
+// on the first call made with that device current.
+static void *g_noalloc_ptr[128];
+
+extern "C" int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in, double *phi_out,
+                                 double *pi_out, long step_index)
+{
+    if (!h || !phi_in || !pi_in || !phi_out || !pi_out || step_index < 0)
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: NULL buffer or negative step index");
+    if (h->nth > 1024)
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: needs nth <= 1024");
+    const long long mids = (long long)(h->nr - 1) * h->nth;
+    if (mids > kNoAllocMaxMid)
+        return fail(h, TEUK_ERR_BAD_ARG,
+                    "teuk_step_noalloc: (nr - 1) * nth = " + std::to_string(mids) +
+                        " exceeds the static scratch of 1048576 mid-point values (32 MiB)");
+    if (phi_in == phi_out || pi_in == pi_out || (const double *)phi_out == pi_in || (const double *)pi_out == phi_in)
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: output buffers must not alias the inputs");
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != h->device || dev < 0 || dev >= 128)
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: the handle's device must be the current device");
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        CU(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    char *base = (char *)g_noalloc_ptr[dev];
+    double2 *phiH = (double2 *)base;
+    double2 *piH = phiH + kNoAllocMaxMid;
+    long long *step = (long long *)(base + 2 * (size_t)kNoAllocMaxMid * sizeof(double2));
+
+    StepParams p = h->sp;
+    p.ext.i_ext = -1;  // no waveform sampling: the caller owns the output state
+    p.step_base = step;
+    // the step counter is written on the stream before the kernels read it; the
+    // half step is fully rewritten by the predictor before the corrector reads it
+    CU(launch_set_counter(step, step_index, h->stream));
+    CU(launch_step_split(p, (const double2 *)phi_in, (const double2 *)pi_in, (double2 *)phi_out,
+                         (double2 *)pi_out, phiH, piH, 0, h->stream));
+    CU(launch_zero_boundary_rows((double2 *)phi_out, (double2 *)pi_out, h->nr, h->nth, h->stream));
+    return TEUK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Results
 // ---------------------------------------------------------------------------

@@ -109,6 +109,8 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
 
 cudaError_t launch_advance(long long *step_base, long long by, cudaStream_t st);
 
+cudaError_t launch_set_counter(long long *counter, long long value, cudaStream_t st);
+
 cudaError_t launch_time_symmetric_pi(const double2 *Phi, double2 *Pi, const double *b_node,
                                      int nr, int nth, double inv_2h, cudaStream_t st);
 

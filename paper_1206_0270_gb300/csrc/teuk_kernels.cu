@@ -541,6 +541,14 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
 
 __global__ void advance_kernel(long long *step_base, long long by) { *step_base += by; }
 
+__global__ void set_counter_kernel(long long *counter, long long value) { *counter = value; }
+
+cudaError_t launch_set_counter(long long *counter, long long value, cudaStream_t st)
+{
+    set_counter_kernel<<<1, 1, 0, st>>>(counter, value);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_advance(long long *step_base, long long by, cudaStream_t st)
 {
     advance_kernel<<<1, 1, 0, st>>>(step_base, by);

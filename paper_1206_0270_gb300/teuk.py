@@ -62,6 +62,7 @@ _SIGS = {
     "teuk_launches_for": (C.c_long, [_vp, C.c_long]),
     "teuk_set_launch": (C.c_int, [_vp, C.c_int]),
     "teuk_get_launch": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "teuk_step_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_long]),
     "teuk_last_error": (C.c_char_p, [_vp]),
     "teuk_strerror": (C.c_char_p, [C.c_int]),
 }
