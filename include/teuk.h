@@ -158,6 +158,16 @@ int teuk_set_kernel(teuk_handle *h, int variant);
  * to hide latency.  Results do not depend on the shape. */
 int teuk_set_launch(teuk_handle *h, int rows_per_block);
 
+/* Tuning options (teuk_set_option).  Results do not depend on them.
+ *   TEUK_OPT_PDL: 1 (default) launches the split kernels with programmatic
+ *     dependent launch, so a kernel loads its constant coefficients while its
+ *     predecessor drains; 0 launches them in plain stream order.
+ *   TEUK_OPT_GRAPH_CHUNK: time steps per captured CUDA graph, even, 2..4096
+ *     (default 64). */
+#define TEUK_OPT_PDL 1
+#define TEUK_OPT_GRAPH_CHUNK 2
+int teuk_set_option(teuk_handle *h, int option, long value);
+
 /* Current fused-kernel launch shape. */
 int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *nblocks);
 

@@ -21,7 +21,6 @@
 using namespace teuk;
 
 static const double kPi = 3.14159265358979323846;
-static const int kChunk = 64;  // time steps per captured CUDA graph (even: ping-pong returns)
 static const int kFusedMaxNth = 512;  // the fused kernel keeps a row ahead in registers: <= 512 threads
 
 struct teuk_handle {
@@ -47,6 +46,8 @@ struct teuk_handle {
     long long nstep = 0;
     int variant = 0;
     int rows_per_block = 1, nblocks = 1;
+    int pdl = 1;      // programmatic dependent launch of the split kernels
+    int chunk = 64;   // time steps per captured graph (even)
     cudaGraphExec_t graph[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     std::string err;
 };
@@ -501,7 +502,7 @@ static cudaError_t launch_one(teuk_handle *h, int from, int k, cudaStream_t st)
                                  h->rows_per_block, h->nblocks, st);
     if (h->variant == 2)
         return launch_step_split(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], h->phiH,
-                                 h->piH, k, st);
+                                 h->piH, k, st, h->pdl != 0);
     return launch_step_unfused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], h->phiH,
                                h->piH, k, st);
 }
@@ -512,11 +513,11 @@ static int capture_graph(teuk_handle *h, int from)
     CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     int b = from;
-    for (int k = 0; k < kChunk && e == cudaSuccess; ++k) {
+    for (int k = 0; k < h->chunk && e == cudaSuccess; ++k) {
         e = launch_one(h, b, k, h->cap_stream);
         b = 1 - b;
     }
-    if (e == cudaSuccess) e = launch_advance(h->d_step, kChunk, h->cap_stream);
+    if (e == cudaSuccess) e = launch_advance(h->d_step, h->chunk, h->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -531,14 +532,14 @@ static int capture_graph(teuk_handle *h, int from)
 extern "C" int teuk_step(teuk_handle *h, long n)
 {
     if (!h || n < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_step: n < 0");
-    while (n >= kChunk) {
+    while (n >= h->chunk) {
         if (!h->graph[h->variant][h->cur]) {
             int rc = capture_graph(h, h->cur);
             if (rc) return rc;
         }
         CU(cudaGraphLaunch(h->graph[h->variant][h->cur], h->stream));
-        n -= kChunk;
-        h->nstep += kChunk;
+        n -= h->chunk;
+        h->nstep += h->chunk;
     }
     if (n > 0) {
         for (int k = 0; k < n; ++k) {
@@ -561,6 +562,28 @@ extern "C" int teuk_set_launch(teuk_handle *h, int rows_per_block)
     return TEUK_OK;
 }
 
+extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    switch (option) {
+    case TEUK_OPT_PDL:
+        if (value != 0 && value != 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: PDL is 0 or 1");
+        CU(cudaStreamSynchronize(h->stream));
+        destroy_graphs(h);
+        h->pdl = (int)value;
+        return TEUK_OK;
+    case TEUK_OPT_GRAPH_CHUNK:
+        if (value < 2 || value > 4096 || value % 2)
+            return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: graph chunk must be even, 2..4096");
+        CU(cudaStreamSynchronize(h->stream));
+        destroy_graphs(h);
+        h->chunk = (int)value;
+        return TEUK_OK;
+    default:
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: unknown option");
+    }
+}
+
 extern "C" int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *nblocks)
 {
     if (!h || !rows_per_block || !nblocks) return TEUK_ERR_BAD_ARG;
@@ -573,8 +596,8 @@ extern "C" long teuk_launches_for(const teuk_handle *h, long n)
 {
     if (!h || n < 0) return -1;
     const long per = h->variant == 0 ? 1 : 2;  // the two-kernel and split variants launch twice per step
-    const long full = n / kChunk, rem = n % kChunk;
-    return full * (kChunk * per + 1) + (rem ? rem * per + 1 : 0);
+    const long full = n / h->chunk, rem = n % h->chunk;
+    return full * (h->chunk * per + 1) + (rem ? rem * per + 1 : 0);
 }
 
 extern "C" int teuk_set_kernel(teuk_handle *h, int variant)
@@ -652,7 +675,7 @@ extern "C" int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const dou
     // half step is fully rewritten by the predictor before the corrector reads it
     CU(launch_set_counter(step, step_index, h->stream));
     CU(launch_step_split(p, (const double2 *)phi_in, (const double2 *)pi_in, (double2 *)phi_out,
-                         (double2 *)pi_out, phiH, piH, 0, h->stream));
+                         (double2 *)pi_out, phiH, piH, 0, h->stream, false));
     CU(launch_zero_boundary_rows((double2 *)phi_out, (double2 *)pi_out, h->nr, h->nth, h->stream));
     return TEUK_OK;
 }

@@ -105,7 +105,7 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
                                 cudaStream_t st);
 
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
-                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st);
+                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl);
 
 cudaError_t launch_advance(long long *step_base, long long by, cudaStream_t st);
 

@@ -70,6 +70,14 @@ __device__ __forceinline__ double2 add2(const double2 a, const double2 b, const 
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor drains.  Everything it reads
+// that an earlier kernel writes (state, half step, step counter) is read after
+// grid_dependency_wait(); only the constant coefficient planes are loaded
+// before.  Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // e^{-i phase}
 __device__ __forceinline__ double2 unit_phase(double ph)
 {
@@ -462,7 +470,9 @@ __global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const dou
     if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
     const size_t k0 = (size_t)hq * nth + jj;
     const PredCoef c = load_pred(p, k0);
+    grid_dependency_wait();
     const double2 phi0 = Phi[k0], pi0 = Pi[k0], phi1 = Phi[k0 + nth], pi1 = Pi[k0 + nth];
+    allow_dependents();
     if (colok) row[j + 1] = add2(phi0, phi1, ops_of(p));
     __syncthreads();
     HalfStep o = predict_c(c, p.q, ops_of(p), phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
@@ -496,12 +506,14 @@ __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const dou
     if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
     const size_t kc = (size_t)iq * nth + jj;
     const CorrCoef c = load_corr(p, kc);
+    grid_dependency_wait();
     HalfStep hp, hm;
     hp.phi = PhiH[kc];
     hp.pi = PiH[kc];
     hm.phi = PhiH[kc - nth];
     hm.pi = PiH[kc - nth];
     const double2 phi = Phi[kc], pi = Pi[kc];
+    allow_dependents();
     if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops_of(p));
     __syncthreads();
     double2 nphi, npi;
@@ -525,13 +537,25 @@ size_t split_smem_bytes(int nth) { return sizeof(double2) * (size_t)split_rows_p
 const void *split_kernel_ptr(int which) { return which ? (const void *)lw_correct_split : (const void *)lw_predict_split; }
 
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
-                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st)
+                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl)
 {
     const int R = split_rows_per_block(p.nth);
-    const dim3 block(fused_block_threads(p.nth), R);
-    const size_t smem = split_smem_bytes(p.nth);
-    lw_predict_split<<<(p.nr - 1 + R - 1) / R, block, smem, st>>>(p, Phi, Pi, PhiH, PiH, k);
-    lw_correct_split<<<(p.nr - 2 + R - 1) / R, block, smem, st>>>(p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(fused_block_threads(p.nth), R);
+    cfg.dynamicSmemBytes = split_smem_bytes(p.nth);
+    cfg.stream = st;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cfg.gridDim = dim3((p.nr - 1 + R - 1) / R);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, lw_predict_split, p, Phi, Pi, PhiH, PiH, k);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3((p.nr - 2 + R - 1) / R);
+    e = cudaLaunchKernelEx(&cfg, lw_correct_split, p, Phi, Pi, (const double2 *)PhiH, (const double2 *)PiH,
+                           PhiO, PiO, k);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

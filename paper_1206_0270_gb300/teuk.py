@@ -27,6 +27,8 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 TEUK_OK = 0
+TEUK_OPT_PDL = 1
+TEUK_OPT_GRAPH_CHUNK = 2
 ERRORS = {-1: "TEUK_ERR_BAD_ARG", -2: "TEUK_ERR_OOM", -3: "TEUK_ERR_CUDA", -4: "TEUK_ERR_NONFINITE",
           -5: "TEUK_ERR_STATE", -6: "TEUK_ERR_OVERFLOW"}
 
@@ -63,6 +65,7 @@ _SIGS = {
     "teuk_set_launch": (C.c_int, [_vp, C.c_int]),
     "teuk_get_launch": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "teuk_step_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_long]),
+    "teuk_set_option": (C.c_int, [_vp, C.c_int, C.c_long]),
     "teuk_last_error": (C.c_char_p, [_vp]),
     "teuk_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -194,6 +197,9 @@ class Solver:
         if rc not in (TEUK_OK, -4):
             _check(rc, self.h, "teuk_check_finite")
         return bool(f.value)
+
+    def set_option(self, option, value):
+        _check(teuk_set_option(self.h, int(option), int(value)), self.h, "teuk_set_option")
 
     def set_launch(self, rows_per_block):
         _check(teuk_set_launch(self.h, int(rows_per_block)), self.h, "teuk_set_launch")

@@ -179,6 +179,34 @@ def test_launch_shapes_agree_bitwise(teuk):
         g.close()
 
 
+def test_tuning_options_agree_bitwise(teuk):
+    # programmatic dependent launch and the graph chunk change scheduling only
+    nr, nth = 260, 48
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, 0.9, -2, 2)
+    u = inputs.random_fields(nr, nth, seed=13)
+    ref = None
+    for pdl, chunk in [(1, 64), (0, 64), (1, 2), (1, 128), (0, 6)]:
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
+        g.set_option(teuk.TEUK_OPT_PDL, pdl)
+        g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, chunk)
+        g.set_initial(*u)
+        g.set_source(**SRC)
+        g.set_extraction(10.0, 3, capacity=200)
+        g.step(131)
+        g.step(200)
+        st = g.state() + (g.extract()[1],)
+        assert g.launches_for(131) > 0
+        if ref is None:
+            ref = st
+        else:
+            for x, y in zip(st, ref):
+                np.testing.assert_array_equal(x, y)
+        g.close()
+    with pytest.raises(teuk.TeukError):
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
+        g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, 3)
+
+
 def test_runs_are_deterministic(teuk):
     kw = dict(source=SRC, seed=4)
     a = run_pair(teuk, 200, 64, -20.0, 40.0, 0.9, -2, 2, 300, **kw)
