@@ -74,7 +74,16 @@ __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 // serialisation may start while its predecessor drains.  Everything it reads
 // that an earlier kernel writes (state, half step, step counter) is read after
 // grid_dependency_wait(); only the constant coefficient planes are loaded
-// before.  Without the launch attribute both instructions are no-ops.
+// before.  A predecessor signals with allow_dependents() only after its last
+// store, since a dependent is guaranteed to see only the writes made before
+// that signal.  Without the launch attribute both instructions are no-ops.
+// Loads of data that other kernels write (state, half step, step counter) in
+// kernels launched with programmatic dependent launch: cached in L2 only.
+// Under PDL the kernel boundary no longer guarantees that the read-only
+// (L1/texture) path holds no line from before the predecessor's writes.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -471,20 +480,20 @@ __global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const dou
     const size_t k0 = (size_t)hq * nth + jj;
     const PredCoef c = load_pred(p, k0);
     grid_dependency_wait();
-    const double2 phi0 = Phi[k0], pi0 = Pi[k0], phi1 = Phi[k0 + nth], pi1 = Pi[k0 + nth];
-    allow_dependents();
+    const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth), pi1 = ldcg(Pi + k0 + nth);
     if (colok) row[j + 1] = add2(phi0, phi1, ops_of(p));
     __syncthreads();
     HalfStep o = predict_c(c, p.q, ops_of(p), phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
     const SourceWindow &sw = p.src;
     if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
-        const long long n = *p.step_base + k;
+        const long long n = ldcg(p.step_base) + k;
         rfma(o.pi, ldg(sw.gP + (size_t)(hq - sw.mid_lo) * nth + jj), unit_phase(sw.m_omega * ((double)n * p.dt)));
     }
     if (colok && rowok) {
         PhiH[k0] = o.phi;
         PiH[k0] = o.pi;
     }
+    allow_dependents();  // after the last store: the dependent sees only writes made before it
 }
 
 __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
@@ -508,17 +517,16 @@ __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const dou
     const CorrCoef c = load_corr(p, kc);
     grid_dependency_wait();
     HalfStep hp, hm;
-    hp.phi = PhiH[kc];
-    hp.pi = PiH[kc];
-    hm.phi = PhiH[kc - nth];
-    hm.pi = PiH[kc - nth];
-    const double2 phi = Phi[kc], pi = Pi[kc];
-    allow_dependents();
+    hp.phi = ldcg(PhiH + kc);
+    hp.pi = ldcg(PiH + kc);
+    hm.phi = ldcg(PhiH + kc - nth);
+    hm.pi = ldcg(PiH + kc - nth);
+    const double2 phi = ldcg(Phi + kc), pi = ldcg(Pi + kc);
     if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops_of(p));
     __syncthreads();
     double2 nphi, npi;
     correct_c(c, p.half_dt, ops_of(p), phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
-    const long long n = *p.step_base + k;
+    const long long n = ldcg(p.step_base) + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
         rfma(npi, ldg(sw.gC + (size_t)(iq - sw.node_lo) * nth + jj),
@@ -531,6 +539,7 @@ __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const dou
             p.ext.ring[(size_t)slot * nth + j] = nphi;
         }
     }
+    allow_dependents();  // after the last store
 }
 
 size_t split_smem_bytes(int nth) { return sizeof(double2) * (size_t)split_rows_per_block(nth) * (nth + 2); }

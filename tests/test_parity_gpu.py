@@ -207,6 +207,28 @@ def test_tuning_options_agree_bitwise(teuk):
         g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, 3)
 
 
+@pytest.mark.parametrize("nr,nth", [(40, 513), (20, 1024), (10, 96), (6, 32), (300, 128)])
+def test_pdl_small_grids_match_plain_launches(teuk, nr, nth):
+    # Few CTAs per kernel leave stale lines in the read-only cache if a kernel
+    # launched with programmatic dependent launch read its predecessor's output
+    # through it; repeat to expose such a race.
+    dt = O.stable_dt(nr, nth, -10.0, 30.0, 0.9, -2, 2, 0.5, 0.05)
+    u = inputs.random_fields(nr, nth, seed=nr + nth)
+    out = []
+    for pdl in (0, 1, 1, 1):
+        g = teuk.Solver(nr, nth, -10.0, 30.0, dt, 0.9, -2, 2)
+        g.set_option(teuk.TEUK_OPT_PDL, pdl)
+        g.set_initial(*u)
+        g.set_source(r0=5.0, sigma=1.0)
+        for c in (1, 2, 64, 3, 128, 5):
+            g.step(c)
+        out.append(g.state())
+        g.close()
+    for st in out[1:]:
+        np.testing.assert_array_equal(st[0], out[0][0])
+        np.testing.assert_array_equal(st[1], out[0][1])
+
+
 def test_runs_are_deterministic(teuk):
     kw = dict(source=SRC, seed=4)
     a = run_pair(teuk, 200, 64, -20.0, 40.0, 0.9, -2, 2, 300, **kw)
