@@ -45,8 +45,8 @@ FP64_PEAK_FLOPS = 1.25e12
 # DRAM bytes (read + write) of one time step (predictor + corrector launches) from one
 # ncu capture (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and
 # launch sources whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(bytes_per_step=310.7e6,
-                   sources_sha256="cf22408a76281ee8bbae348124194205e2fff767d6addf9592e3cca9953c2137")
+NCU_TRAFFIC = dict(bytes_per_step=310.6e6,
+                   sources_sha256="8110f0257b45419ac7635394c0cb7abf5996ea462055ff064337367bfcb263f4")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu", "paper_1206_0270_gb300/csrc/teuk_internal.h",
                    "paper_1206_0270_gb300/csrc/teuk_api.cu"]
 
