@@ -310,6 +310,95 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Batched workloads: waveforms/s batched vs one job at a time
+# ---------------------------------------------------------------------------
+
+def batch_jobs(kind, scale):
+    """Job list (dicts) of a batched workload, step counts scaled by `scale`."""
+    from paper_1206_0270_gb300 import inputs
+    jobs = []
+    if kind == "batch_modes":
+        w = inputs.MODE_BATCH
+        for m, nth in w["modes"]:
+            jobs.append(dict(a=w["a"], s=w["s"], m=m, nr=w["nr"], nth=nth, r0=w["r0"], sigma=w["sigma"],
+                             steps=max(2, int(round(w["steps"] * scale)))))
+    else:
+        for j in inputs.template_bank(256):
+            j = dict(j)
+            j["sigma"] = 0.05
+            j["steps"] = max(2, int(round(j["steps"] * scale)))
+            jobs.append(j)
+    return jobs
+
+
+def run_batch_workload(args):
+    import torch
+    from paper_1206_0270_gb300 import build
+    build.build()
+    from paper_1206_0270_gb300 import teuk as T
+    rmin, rmax, ext = -100.0, 600.0, dict(rstar=500.0, every=10)
+    jobs = batch_jobs(args.workload, args.steps_scale)
+    stream = torch.cuda.Stream()
+    dts = {}
+    for j in jobs:
+        key = (j["nr"], j["nth"], j["a"], j["s"], j["m"])
+        if key not in dts:
+            dts[key] = T.stable_dt(j["nr"], j["nth"], rmin, rmax, j["a"], j["s"], j["m"])
+        j["dt"] = dts[key]
+
+    def make_all():
+        out = []
+        for j in jobs:
+            dt = j["dt"]
+            g = T.Solver(j["nr"], j["nth"], rmin, rmax, dt, j["a"], j["s"], j["m"], stream=stream)
+            g.set_source(r0=j["r0"], sigma=j["sigma"])
+            g.set_extraction(ext["rstar"], ext["every"], capacity=j["steps"] // ext["every"] + 1)
+            out.append(g)
+        torch.cuda.synchronize()
+        return out
+
+    upd = sum((j["nr"] - 2) * j["nth"] * j["steps"] for j in jobs)
+    # one at a time: each job's own graph-replayed steps, jobs in sequence
+    solvers = make_all()
+    t0 = time.perf_counter()
+    for g, j in zip(solvers, jobs):
+        g.step(j["steps"])
+        g.extract()
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    launches_single = sum(g.launches_for(j["steps"]) for g, j in zip(solvers, jobs))
+    for g in solvers:
+        g.close()
+    # batched: every job in one batch, CTA size autotuned on the jobs themselves
+    solvers = make_all()
+    B = T.Batch(stream=stream)
+    for g, j in zip(solvers, jobs):
+        B.add(g, j["steps"])
+    t0 = time.perf_counter()
+    best = B.autotune()
+    B.step(10 ** 9)
+    B.sync()
+    for g in solvers:
+        g.extract()
+    t_batch = time.perf_counter() - t0
+    B.close()
+    for g in solvers:
+        g.close()
+    n = len(jobs)
+    line = dict(metric="batched waveforms/s", value=n / t_batch, unit="waveforms/s", n_gpus=1,
+                steps=1, warmup=0, ms_per_step=1e3 * t_batch, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, jobs=n, steps_scale=args.steps_scale,
+                            point_updates=upd, block_threads=best),
+                one_by_one=dict(value=n / t_single, unit="waveforms/s", seconds=t_single,
+                                gpu_launches=int(launches_single)),
+                batched=dict(seconds=t_batch, grid_pt_updates_per_s=upd / t_batch),
+                speedup=t_single / t_batch)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,7 +409,14 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=10, help="oracle time steps per reference step")
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batch_modes", "template_bank"],
+                    help="single: the Kerr 8192x128 step (default); batch_modes / template_bank: batched "
+                         "waveforms/s against one job at a time")
+    ap.add_argument("--steps-scale", type=float, default=0.2,
+                    help="batched workloads: fraction of each job's step count that is run")
     args = ap.parse_args()
+    if args.workload != "single":
+        return run_batch_workload(args)
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     if args.impl == "reference":

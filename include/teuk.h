@@ -166,6 +166,7 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  *     (default 64). */
 #define TEUK_OPT_PDL 1
 #define TEUK_OPT_GRAPH_CHUNK 2
+#define TEUK_OPT_BLOCK_THREADS 3  /* batches only: CTA threads, 0 = automatic */
 int teuk_set_option(teuk_handle *h, int option, long value);
 
 /* Current fused-kernel launch shape. */
@@ -201,6 +202,66 @@ long teuk_launches_for(const teuk_handle *h, long n);
  * The handle's device must be the current device. */
 int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in, double *phi_out,
                       double *pi_out, long step_index);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent evolutions stepped together.
+ *
+ * A template bank is many independent (a, r0, m) evolutions of uneven grid
+ * size and length (the paper's motivation for fast waveform generation; its
+ * temporal segments are independent evolutions too).  A batch groups
+ * existing handles on one device and advances all of its jobs by one time
+ * step with one predictor launch and one corrector launch, each CTA working on
+ * one tile of one job; the arithmetic per point is that of teuk_step (results
+ * are bit-identical to stepping each handle alone).  Jobs advance in slices of
+ * min(graph chunk, smallest remaining step count) steps; a job that has taken
+ * its steps leaves at the next slice boundary.  Full slices replay a CUDA
+ * graph captured for the current set of jobs.
+ *
+ * Rules: a handle in a batch is driven by the batch only; call
+ * teuk_batch_sync() before reading a job's results through its handle
+ * (teuk_extract, teuk_get_state) and do not destroy a handle before removing
+ * it.  Jobs need nth <= 1024.  A batch allocates its job table (and a job's
+ * half-step buffer if the handle has none).
+ * ------------------------------------------------------------------------ */
+typedef struct teuk_batch teuk_batch;
+
+/* Create an empty batch on the current device; work is issued on
+ * cuda_stream (NULL: the batch creates and owns a non-blocking stream). */
+int teuk_batch_create(void *cuda_stream, teuk_batch **out);
+
+/* Add a handle that still has `steps` time steps to take; *job_id receives
+ * its index in the batch.  Synchronises the handle's stream. */
+int teuk_batch_add(teuk_batch *b, teuk_handle *h, long steps, int *job_id);
+
+/* Remove a job (its handle stays valid).  Synchronises the batch stream. */
+int teuk_batch_remove(teuk_batch *b, int job_id);
+
+/* Advance the jobs by up to max_steps time steps of batch time (each job at
+ * most its remaining count), asynchronously; *steps_done (may be NULL)
+ * receives the batch time advanced. */
+int teuk_batch_step(teuk_batch *b, long max_steps, long *steps_done);
+
+/* Steps job_id still has to take (0 once done or removed). */
+int teuk_batch_remaining(const teuk_batch *b, int job_id, long *remaining);
+
+/* Wait for the batch's queued work. */
+int teuk_batch_sync(teuk_batch *b);
+
+/* TEUK_OPT_PDL, TEUK_OPT_GRAPH_CHUNK or TEUK_OPT_BLOCK_THREADS. */
+int teuk_batch_set_option(teuk_batch *b, int option, long value);
+
+/* Time each candidate CTA size (256, 512, 1024 threads; at least the widest
+ * job's row) on the batch's own jobs -- the timed steps count as progress --
+ * and keep the fastest; *best_block receives it.  Synchronises. */
+int teuk_batch_autotune(teuk_batch *b, int *best_block);
+
+/* Kernel launches that teuk_batch_step(b, n) issues when no job finishes. */
+long teuk_batch_launches_for(const teuk_batch *b, long n);
+
+/* Message of the last failed batch call ("" if none). */
+const char *teuk_batch_last_error(const teuk_batch *b);
+
+int teuk_batch_destroy(teuk_batch *b);
 
 /* Message of the last failed call on this handle ("" if none). */
 const char *teuk_last_error(const teuk_handle *h);

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "teuk.h"
+#include "teuk_handle.h"
 #include "teuk_internal.h"
 #include "teuk_physics.h"
 
@@ -22,35 +23,6 @@ using namespace teuk;
 
 static const double kPi = 3.14159265358979323846;
 static const int kFusedMaxNth = 512;  // the fused kernel keeps a row ahead in registers: <= 512 threads
-
-struct teuk_handle {
-    int nr = 0, nth = 0, s = 0, m = 0, parity = 1;
-    double a = 0, rstar_min = 0, rstar_max = 0, h = 0, dth = 0, dt = 0;
-    int device = 0, num_sms = 0;
-    cudaStream_t stream = nullptr, cap_stream = nullptr;
-    bool own_stream = false;
-
-    char *arena = nullptr;         // state, planes, tables, counters
-    double2 *phi[2] = {nullptr, nullptr}, *pi[2] = {nullptr, nullptr};
-    double2 *phiH = nullptr, *piH = nullptr;  // half-step buffer of the two-kernel variant
-    double *b_node = nullptr;
-    long long *d_step = nullptr;
-    unsigned long long *d_count = nullptr;
-    StepParams sp{};
-
-    double *d_src = nullptr;       // source windows (gP then gC)
-    double2 *d_ring = nullptr;
-    long long drained = 0;
-
-    int cur = 0;
-    long long nstep = 0;
-    int variant = 0;
-    int rows_per_block = 1, nblocks = 1;
-    int pdl = 1;      // programmatic dependent launch of the split kernels
-    int chunk = 64;   // time steps per captured graph (even)
-    cudaGraphExec_t graph[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
-    std::string err;
-};
 
 // ---------------------------------------------------------------------------
 // Helpers

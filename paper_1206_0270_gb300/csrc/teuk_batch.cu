@@ -1,0 +1,395 @@
+// teuk_batch.cu -- batched stepping of many independent solver handles.
+//
+// A template bank is thousands of independent (a, r0, m) evolutions of
+// uneven grid size and length.  A batch advances all of its active jobs by
+// one time step with a single predictor launch and a single corrector launch
+// (lw_predict_batch / lw_correct_batch): CTA b finds its job by a binary
+// search over the jobs' tile offsets and works on one tile of that job.  Jobs
+// advance in slices; a slice is min(chunk, smallest remaining step count)
+// steps, so a job that reaches its step count leaves at a slice boundary.
+// Full slices replay a CUDA graph captured for the current set of jobs.  The
+// CTA size is chosen by timing the candidates on the jobs themselves
+// (teuk_batch_autotune), so tuning advances the jobs instead of wasting work.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "teuk.h"
+#include "teuk_handle.h"
+#include "teuk_internal.h"
+
+using namespace teuk;
+
+struct teuk_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    bool own_stream = false;
+    struct Job {
+        teuk_handle *h = nullptr;
+        long long remaining = 0;
+        bool member = false;  // still in the batch (not removed)
+    };
+    std::vector<Job> jobs;
+
+    // device tables of the active set (rebuilt when it changes)
+    JobDesc *d_jobs = nullptr;
+    int *d_off = nullptr;  // pred offsets [cap_jobs + 1], then corr offsets [cap_jobs + 1]
+    int cap_jobs = 0;
+    std::vector<int> active;  // job ids in table order
+    std::vector<JobDesc> host_desc;
+    int pred_tiles = 0, corr_tiles = 0;
+    size_t smem = 0;
+    int block = 0;          // CTA threads in use
+    int block_request = 0;  // 0 = automatic
+    bool layout_dirty = true;
+    cudaGraphExec_t graph = nullptr;
+    int pdl = 1, chunk = 64;
+    std::string err;
+};
+
+static int bfail(teuk_batch *b, int code, const std::string &msg)
+{
+    if (b) b->err = msg;
+    return code;
+}
+
+#define BCU(call)                                                                                \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return bfail(b, TEUK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static int colpad_of(int nth) { return ((nth + 31) / 32) * 32; }
+
+static void drop_graph(teuk_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+extern "C" int teuk_batch_create(void *cuda_stream, teuk_batch **out)
+{
+    if (!out) return TEUK_ERR_BAD_ARG;
+    *out = nullptr;
+    teuk_batch *b = new (std::nothrow) teuk_batch();
+    if (!b) return TEUK_ERR_OOM;
+    if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return TEUK_ERR_CUDA; }
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return TEUK_ERR_CUDA; }
+        b->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return TEUK_ERR_CUDA;
+    }
+    *out = b;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_destroy(teuk_batch *b)
+{
+    if (!b) return TEUK_ERR_BAD_ARG;
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_off) cudaFree(b->d_off);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_add(teuk_batch *b, teuk_handle *h, long steps, int *job_id)
+{
+    if (!b || !h || steps < 0 || !job_id) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: bad argument");
+    *job_id = -1;
+    if (h->device != b->device) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: handle on another device");
+    if (h->nth > 1024) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: batched tiles need nth <= 1024");
+    for (const auto &j : b->jobs)
+        if (j.member && j.h == h) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: handle already in the batch");
+    BCU(cudaStreamSynchronize(h->stream));  // the handle's own queued work comes first
+    if (!h->phiH) {
+        const size_t Nm = (size_t)(h->nr - 1) * h->nth;
+        if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, TEUK_ERR_OOM, "teuk_batch_add: out of device memory for the half step");
+        }
+        h->piH = h->phiH + Nm;
+    }
+    teuk_batch::Job j;
+    j.h = h;
+    j.remaining = steps;
+    j.member = true;
+    b->jobs.push_back(j);
+    *job_id = (int)b->jobs.size() - 1;
+    b->layout_dirty = true;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_remove(teuk_batch *b, int job_id)
+{
+    if (!b || job_id < 0 || job_id >= (int)b->jobs.size() || !b->jobs[job_id].member)
+        return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_remove: unknown job");
+    BCU(cudaStreamSynchronize(b->stream));
+    b->jobs[job_id].member = false;
+    b->jobs[job_id].remaining = 0;
+    b->layout_dirty = true;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_remaining(const teuk_batch *b, int job_id, long *remaining)
+{
+    if (!b || !remaining || job_id < 0 || job_id >= (int)b->jobs.size()) return TEUK_ERR_BAD_ARG;
+    *remaining = b->jobs[job_id].member ? (long)b->jobs[job_id].remaining : 0;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_sync(teuk_batch *b)
+{
+    if (!b) return TEUK_ERR_BAD_ARG;
+    BCU(cudaStreamSynchronize(b->stream));
+    return TEUK_OK;
+}
+
+// CTA size: at least 256 threads, at least the widest job's padded row.
+static int pick_block(const teuk_batch *b)
+{
+    int widest = 32;
+    for (int id : b->active) widest = std::max(widest, colpad_of(b->jobs[id].h->nth));
+    int blk = std::max(256, widest);
+    if (b->block_request >= widest) blk = b->block_request;
+    return std::min(blk, 1024);
+}
+
+// Rebuild the job table and tile offsets for the jobs with steps left.
+static int rebuild(teuk_batch *b)
+{
+    b->active.clear();
+    for (int id = 0; id < (int)b->jobs.size(); ++id)
+        if (b->jobs[id].member && b->jobs[id].remaining > 0) b->active.push_back(id);
+    drop_graph(b);
+    const int nj = (int)b->active.size();
+    if (nj == 0) {
+        b->layout_dirty = false;
+        return TEUK_OK;
+    }
+    b->block = pick_block(b);
+    if (nj > b->cap_jobs) {
+        BCU(cudaStreamSynchronize(b->stream));  // queued slices still read the old table
+        if (b->d_jobs) { cudaFree(b->d_jobs); b->d_jobs = nullptr; }
+        if (b->d_off) { cudaFree(b->d_off); b->d_off = nullptr; }
+        const int cap = std::max(nj, 2 * b->cap_jobs);
+        if (cudaMalloc(&b->d_jobs, (size_t)cap * sizeof(JobDesc)) != cudaSuccess ||
+            cudaMalloc(&b->d_off, 2 * (size_t)(cap + 1) * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            b->cap_jobs = 0;
+            return bfail(b, TEUK_ERR_OOM, "batch: out of device memory for the job table");
+        }
+        b->cap_jobs = cap;
+    }
+    b->host_desc.assign(nj, JobDesc{});
+    std::vector<int> off(2 * (size_t)(b->cap_jobs + 1), 0);
+    int *poff = off.data(), *coff = off.data() + (b->cap_jobs + 1);
+    size_t smem = 0;
+    for (int q = 0; q < nj; ++q) {
+        teuk_handle *h = b->jobs[b->active[q]].h;
+        JobDesc &d = b->host_desc[q];
+        d.p = h->sp;
+        d.phi[0] = h->phi[0]; d.phi[1] = h->phi[1];
+        d.pi[0] = h->pi[0]; d.pi[1] = h->pi[1];
+        d.phiH = h->phiH; d.piH = h->piH;
+        d.cur = h->cur;
+        d.colpad = colpad_of(h->nth);
+        d.rows = std::max(1, b->block / d.colpad);
+        const int pt = (h->nr - 1 + d.rows - 1) / d.rows, ct = (h->nr - 2 + d.rows - 1) / d.rows;
+        poff[q + 1] = poff[q] + pt;
+        coff[q + 1] = coff[q] + ct;
+        smem = std::max(smem, batch_smem_bytes(b->block, d.rows, h->nth));
+    }
+    b->pred_tiles = poff[nj];
+    b->corr_tiles = coff[nj];
+    b->smem = smem;
+    if (smem > 48 * 1024)
+        for (int w = 0; w < 2; ++w)
+            BCU(cudaFuncSetAttribute(batch_kernel_ptr(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCU(cudaMemcpyAsync(b->d_jobs, b->host_desc.data(), nj * sizeof(JobDesc), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    b->layout_dirty = false;
+    return TEUK_OK;
+}
+
+// After an odd number of steps the jobs' current buffers flipped: refresh the table.
+static int refresh_cur(teuk_batch *b)
+{
+    for (int q = 0; q < (int)b->active.size(); ++q) b->host_desc[q].cur = b->jobs[b->active[q]].h->cur;
+    BCU(cudaMemcpyAsync(b->d_jobs, b->host_desc.data(), b->active.size() * sizeof(JobDesc), cudaMemcpyHostToDevice,
+                        b->stream));
+    return TEUK_OK;
+}
+
+// The first predictor of every call follows the table upload or the counter
+// update, not a step kernel, so it is launched in plain stream order; the
+// other step kernels use programmatic dependent launch when enabled.
+static cudaError_t launch_batch_steps(teuk_batch *b, int k0, int n, cudaStream_t st)
+{
+    const int nj = (int)b->active.size();
+    for (int k = k0; k < k0 + n; ++k) {
+        cudaError_t e = launch_step_batch(b->d_jobs, b->d_off, b->d_off + (b->cap_jobs + 1), nj, b->pred_tiles,
+                                          b->corr_tiles, b->block, b->smem, 1.0, -0.0, k, st,
+                                          b->pdl != 0 && k > k0, b->pdl != 0);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_advance_batch(b->d_jobs, nj, n, st);
+}
+
+static int capture(teuk_batch *b)
+{
+    cudaGraph_t g = nullptr;
+    BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_batch_steps(b, 0, b->chunk, b->cap);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, TEUK_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e ? e : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return bfail(b, TEUK_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e3));
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_step(teuk_batch *b, long max_steps, long *steps_done)
+{
+    if (!b || max_steps < 0) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_step: bad argument");
+    long done = 0;
+    while (done < max_steps) {
+        if (b->layout_dirty) {
+            int rc = rebuild(b);
+            if (rc) return rc;
+        }
+        if (b->active.empty()) break;
+        long long L = std::min<long long>(b->chunk, max_steps - done);
+        for (int id : b->active) L = std::min(L, b->jobs[id].remaining);
+        if (L == b->chunk) {
+            if (!b->graph) {
+                int rc = capture(b);
+                if (rc) return rc;
+            }
+            BCU(cudaGraphLaunch(b->graph, b->stream));
+        } else {
+            BCU(launch_batch_steps(b, 0, (int)L, b->stream));
+        }
+        bool finished = false;
+        for (int id : b->active) {
+            auto &j = b->jobs[id];
+            j.h->nstep += L;
+            j.h->cur ^= (int)(L & 1);
+            j.remaining -= L;
+            finished |= j.remaining == 0;
+        }
+        if (finished) {
+            b->layout_dirty = true;  // finished jobs leave at this slice boundary
+        } else if (L & 1) {
+            int rc = refresh_cur(b);
+            if (rc) return rc;
+        }
+        done += (long)L;
+    }
+    if (steps_done) *steps_done = done;
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_set_option(teuk_batch *b, int option, long value)
+{
+    if (!b) return TEUK_ERR_BAD_ARG;
+    BCU(cudaStreamSynchronize(b->stream));
+    switch (option) {
+    case TEUK_OPT_PDL:
+        if (value != 0 && value != 1) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: PDL is 0 or 1");
+        b->pdl = (int)value;
+        break;
+    case TEUK_OPT_GRAPH_CHUNK:
+        if (value < 2 || value > 4096 || value % 2)
+            return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: graph chunk must be even, 2..4096");
+        b->chunk = (int)value;
+        break;
+    case TEUK_OPT_BLOCK_THREADS:
+        if (value != 0 && (value < 32 || value > 1024 || value % 32))
+            return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: block threads 0 or a multiple of 32 <= 1024");
+        b->block_request = (int)value;
+        b->layout_dirty = true;
+        break;
+    default:
+        return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: unknown option");
+    }
+    drop_graph(b);
+    return TEUK_OK;
+}
+
+extern "C" int teuk_batch_autotune(teuk_batch *b, int *best_block)
+{
+    if (!b) return TEUK_ERR_BAD_ARG;
+    if (b->layout_dirty) {
+        int rc = rebuild(b);
+        if (rc) return rc;
+    }
+    if (b->active.empty()) return bfail(b, TEUK_ERR_STATE, "teuk_batch_autotune: no job has steps left");
+    int widest = 32;
+    for (int id : b->active) widest = std::max(widest, colpad_of(b->jobs[id].h->nth));
+    const int cands[] = {256, 512, 1024};
+    cudaEvent_t e0, e1;
+    BCU(cudaEventCreate(&e0));
+    BCU(cudaEventCreate(&e1));
+    int best = 0;
+    double best_rate = -1.0;
+    const int saved = b->block_request;
+    for (int c : cands) {
+        if (c < widest) continue;
+        long long pts = 0, minrem = 1LL << 62;
+        for (int id : b->active) minrem = std::min(minrem, b->jobs[id].remaining);
+        if (minrem < 2) break;
+        b->block_request = c;
+        b->layout_dirty = true;
+        int rc = rebuild(b);
+        if (rc) return rc;
+        for (int id : b->active) pts += (long long)(b->jobs[id].h->nr - 2) * b->jobs[id].h->nth;
+        const long n = (long)std::min<long long>(minrem, 2 * b->chunk) & ~1L;
+        BCU(launch_batch_steps(b, 0, 2, b->stream));  // warm-up, counted as progress
+        BCU(cudaEventRecord(e0, b->stream));
+        BCU(launch_batch_steps(b, 0, (int)n - 2, b->stream));
+        BCU(cudaEventRecord(e1, b->stream));
+        BCU(cudaEventSynchronize(e1));
+        float ms = 0;
+        BCU(cudaEventElapsedTime(&ms, e0, e1));
+        for (int id : b->active) {
+            b->jobs[id].h->nstep += n;
+            b->jobs[id].remaining -= n;
+        }
+        const double rate = (double)pts * (n - 2) / (ms > 0 ? ms : 1e-3);
+        if (rate > best_rate) { best_rate = rate; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->block_request = best ? best : saved;
+    b->layout_dirty = true;
+    if (best_block) *best_block = best;
+    return TEUK_OK;
+}
+
+extern "C" long teuk_batch_launches_for(const teuk_batch *b, long n)
+{
+    // each step is two launches, each slice adds one counter update
+    if (!b || n < 0) return -1;
+    const long slices = (n + b->chunk - 1) / b->chunk;
+    return 2 * n + slices;
+}
+
+extern "C" const char *teuk_batch_last_error(const teuk_batch *b) { return b ? b->err.c_str() : ""; }

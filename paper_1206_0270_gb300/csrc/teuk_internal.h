@@ -77,6 +77,21 @@ struct StepParams {
     const long long *step_base;  // device: steps completed before this chunk
 };
 
+// One job of a batch: its step parameters and buffers.  A batch advances all
+// of its jobs by one time step with one predictor and one corrector launch;
+// CTA b works on tile b - tile_off[job] of the job with the largest
+// tile_off[job] <= b.  A tile is `rows` consecutive rows of nth values, one
+// thread per value (colpad = nth rounded up to a warp).
+struct JobDesc {
+    StepParams p;
+    double2 *phi[2], *pi[2];  // state, ping-pong
+    double2 *phiH, *piH;      // half step
+    int cur;                  // buffer holding the state at the start of the slice
+    int rows;                 // rows per tile
+    int colpad;
+    int pad_;
+};
+
 // ---------------------------------------------------------------------------
 // Kernels (teuk_kernels.cu)
 // ---------------------------------------------------------------------------
@@ -118,6 +133,15 @@ cudaError_t launch_zero_boundary_rows(double2 *Phi, double2 *Pi, int nr, int nth
 
 cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long long npts,
                                    unsigned long long *count, cudaStream_t st);
+
+cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const int *corr_off, int njobs,
+                              int pred_tiles, int corr_tiles, int block, size_t smem, double one, double nzero,
+                              int k, cudaStream_t st, bool pdl_pred, bool pdl_corr);
+
+cudaError_t launch_advance_batch(const JobDesc *jobs, int njobs, long long by, cudaStream_t st);
+
+size_t batch_smem_bytes(int block, int rows, int nth);
+const void *batch_kernel_ptr(int which);
 
 int fused_block_threads(int nth);
 size_t fused_smem_bytes(int nth);

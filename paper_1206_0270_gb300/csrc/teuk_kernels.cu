@@ -569,6 +569,177 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
 }
 
 // ---------------------------------------------------------------------------
+// Batched split kernels: one launch covers the tiles of every job of a batch
+// ---------------------------------------------------------------------------
+
+// Dynamic shared memory of a batch CTA: the job descriptor, then `rows` rows
+// of nth + 2 sums.
+size_t batch_smem_bytes(int block, int rows, int nth)
+{
+    (void)block;
+    return ((sizeof(JobDesc) + 15) / 16) * 16 + sizeof(double2) * (size_t)rows * (nth + 2);
+}
+
+// Largest j < njobs with off[j] <= b (off is increasing, off[0] = 0).
+__device__ __forceinline__ int find_job(const int *off, int njobs, int b)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ldcg(off + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Copy the CTA's job descriptor to shared memory (through L2: the host
+// rewrites the table between slices) and return the tile index.
+__device__ __forceinline__ int batch_prologue(const JobDesc *jobs, const int *off, int njobs, JobDesc *sj)
+{
+    __shared__ int s_job;
+    if (threadIdx.x == 0) s_job = find_job(off, njobs, blockIdx.x);
+    __syncthreads();
+    const int jb = s_job;
+    const unsigned long long *src = (const unsigned long long *)(jobs + jb);
+    unsigned long long *dst = (unsigned long long *)sj;
+    for (int w = threadIdx.x; w < (int)(sizeof(JobDesc) / 8); w += blockDim.x) dst[w] = ldcg(src + w);
+    __syncthreads();
+    return blockIdx.x - ldcg(off + jb);
+}
+
+__global__ void __launch_bounds__(1024) lw_predict_batch(const JobDesc *__restrict__ jobs,
+                                                         const int *__restrict__ off, int njobs, int k, Ops ops)
+{
+    extern __shared__ double2 smem[];
+    JobDesc &J = *(JobDesc *)smem;
+    double2 *rows = smem + (sizeof(JobDesc) + 15) / 16;
+    const int tile = batch_prologue(jobs, off, njobs, &J);
+    const StepParams &p = J.p;
+    const int nth = p.nth, W = nth + 2, colpad = J.colpad, R = J.rows;
+    const int ty = threadIdx.x / colpad, j = threadIdx.x - ty * colpad;
+    const bool slot = ty < R;                 // threads past R rows only join the barrier
+    const int tyc = slot ? ty : R - 1;
+    const bool colok = slot && j < nth;
+    const int jj = j < nth ? j : nth - 1;
+    const int hp = tile * R + tyc;
+    const bool rowok = slot && hp < p.nr - 1;
+    const int hq = min(hp, p.nr - 2);
+    double2 *row = rows + tyc * W;
+    if (slot && j < 2) row[j == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
+    const size_t k0 = (size_t)hq * nth + jj;
+    const PredCoef c = load_pred(p, k0);
+    grid_dependency_wait();
+    const int from = J.cur ^ (k & 1);
+    const double2 *Phi = J.phi[from], *Pi = J.pi[from];
+    const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth), pi1 = ldcg(Pi + k0 + nth);
+    if (colok) row[j + 1] = add2(phi0, phi1, ops);
+    __syncthreads();
+    HalfStep o = predict_c(c, p.q, ops, phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
+    const SourceWindow &sw = p.src;
+    if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
+        const long long n = ldcg(p.step_base) + k;
+        rfma(o.pi, ldg(sw.gP + (size_t)(hq - sw.mid_lo) * nth + jj), unit_phase(sw.m_omega * ((double)n * p.dt)));
+    }
+    if (colok && rowok) {
+        J.phiH[k0] = o.phi;
+        J.piH[k0] = o.pi;
+    }
+    allow_dependents();
+}
+
+__global__ void __launch_bounds__(1024) lw_correct_batch(const JobDesc *__restrict__ jobs,
+                                                         const int *__restrict__ off, int njobs, int k, Ops ops)
+{
+    extern __shared__ double2 smem[];
+    JobDesc &J = *(JobDesc *)smem;
+    double2 *rows = smem + (sizeof(JobDesc) + 15) / 16;
+    const int tile = batch_prologue(jobs, off, njobs, &J);
+    const StepParams &p = J.p;
+    const int nth = p.nth, W = nth + 2, colpad = J.colpad, R = J.rows;
+    const int ty = threadIdx.x / colpad, j = threadIdx.x - ty * colpad;
+    const bool slot = ty < R;
+    const int tyc = slot ? ty : R - 1;
+    const bool colok = slot && j < nth;
+    const int jj = j < nth ? j : nth - 1;
+    const int i = 1 + tile * R + tyc;
+    const bool rowok = slot && i <= p.nr - 2;
+    const int iq = min(i, p.nr - 2);
+    double2 *row = rows + tyc * W;
+    if (slot && j < 2) row[j == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
+    const size_t kc = (size_t)iq * nth + jj;
+    const CorrCoef c = load_corr(p, kc);
+    grid_dependency_wait();
+    const int from = J.cur ^ (k & 1);
+    const double2 *Phi = J.phi[from], *Pi = J.pi[from];
+    double2 *PhiO = J.phi[1 - from], *PiO = J.pi[1 - from];
+    HalfStep hp, hm;
+    hp.phi = ldcg(J.phiH + kc);
+    hp.pi = ldcg(J.piH + kc);
+    hm.phi = ldcg(J.phiH + kc - nth);
+    hm.pi = ldcg(J.piH + kc - nth);
+    const double2 phi = ldcg(Phi + kc), pi = ldcg(Pi + kc);
+    if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops);
+    __syncthreads();
+    double2 nphi, npi;
+    correct_c(c, p.half_dt, ops, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
+    const long long n = ldcg(p.step_base) + k;
+    const SourceWindow &sw = p.src;
+    if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
+        rfma(npi, ldg(sw.gC + (size_t)(iq - sw.node_lo) * nth + jj),
+             unit_phase(sw.m_omega * (((double)n + 0.5) * p.dt)));
+    if (colok && rowok) {
+        PhiO[kc] = nphi;
+        PiO[kc] = npi;
+        if (iq == p.ext.i_ext && ((n + 1) % p.ext.every) == 0) {
+            const long long slot_k = ((n + 1) / p.ext.every - 1) % p.ext.capacity;
+            p.ext.ring[(size_t)slot_k * nth + j] = nphi;
+        }
+    }
+    allow_dependents();
+}
+
+const void *batch_kernel_ptr(int which) { return which ? (const void *)lw_correct_batch : (const void *)lw_predict_batch; }
+
+cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const int *corr_off, int njobs,
+                              int pred_tiles, int corr_tiles, int block, size_t smem, double one, double nzero,
+                              int k, cudaStream_t st, bool pdl_pred, bool pdl_corr)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = pdl_pred ? attr : nullptr;
+    cfg.numAttrs = pdl_pred ? 1 : 0;
+    const Ops ops{one, nzero};
+    cfg.gridDim = dim3(pred_tiles);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, lw_predict_batch, jobs, pred_off, njobs, k, ops);
+    if (e != cudaSuccess) return e;
+    cfg.attrs = pdl_corr ? attr : nullptr;
+    cfg.numAttrs = pdl_corr ? 1 : 0;
+    cfg.gridDim = dim3(corr_tiles);
+    e = cudaLaunchKernelEx(&cfg, lw_correct_batch, jobs, corr_off, njobs, k, ops);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+__global__ void advance_batch_kernel(const JobDesc *jobs, int njobs, long long by)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < njobs) {
+        long long *step = (long long *)ldcg((const unsigned long long *)&jobs[j].p.step_base);
+        *step += by;
+    }
+}
+
+cudaError_t launch_advance_batch(const JobDesc *jobs, int njobs, long long by, cudaStream_t st)
+{
+    advance_batch_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(jobs, njobs, by);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Small kernels
 // ---------------------------------------------------------------------------
 

@@ -39,6 +39,14 @@ WORKLOADS = {
 }
 
 
+# Batched workloads.  One Kerr a = 0.7M orbit at r0 = 8M, modes m = 1..8 with
+# theta resolution growing with m, 4096 r* points each, 5e4 steps.
+MODE_BATCH = dict(
+    a=0.7, s=-2, r0=8.0, sigma=0.05, nr=4096, rstar_min=-100.0, rstar_max=600.0, steps=50000,
+    modes=[(1, 32), (2, 32), (3, 64), (4, 64), (5, 128), (6, 128), (7, 256), (8, 256)],
+    extraction=dict(rstar=500.0, every=10), c_r=0.5, c_theta=0.1)
+
+
 def rstar_grid(nr: int, rstar_min: float, rstar_max: float) -> np.ndarray:
     h = (rstar_max - rstar_min) / (nr - 1)
     return rstar_min + h * np.arange(nr)

@@ -29,6 +29,7 @@ _lib = C.CDLL(LIB_PATH)
 TEUK_OK = 0
 TEUK_OPT_PDL = 1
 TEUK_OPT_GRAPH_CHUNK = 2
+TEUK_OPT_BLOCK_THREADS = 3
 ERRORS = {-1: "TEUK_ERR_BAD_ARG", -2: "TEUK_ERR_OOM", -3: "TEUK_ERR_CUDA", -4: "TEUK_ERR_NONFINITE",
           -5: "TEUK_ERR_STATE", -6: "TEUK_ERR_OVERFLOW"}
 
@@ -66,6 +67,17 @@ _SIGS = {
     "teuk_get_launch": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "teuk_step_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_long]),
     "teuk_set_option": (C.c_int, [_vp, C.c_int, C.c_long]),
+    "teuk_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
+    "teuk_batch_add": (C.c_int, [_vp, _vp, C.c_long, C.POINTER(C.c_int)]),
+    "teuk_batch_remove": (C.c_int, [_vp, C.c_int]),
+    "teuk_batch_step": (C.c_int, [_vp, C.c_long, C.POINTER(C.c_long)]),
+    "teuk_batch_remaining": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_long)]),
+    "teuk_batch_sync": (C.c_int, [_vp]),
+    "teuk_batch_set_option": (C.c_int, [_vp, C.c_int, C.c_long]),
+    "teuk_batch_autotune": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "teuk_batch_launches_for": (C.c_long, [_vp, C.c_long]),
+    "teuk_batch_last_error": (C.c_char_p, [_vp]),
+    "teuk_batch_destroy": (C.c_int, [_vp]),
     "teuk_last_error": (C.c_char_p, [_vp]),
     "teuk_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -211,3 +223,61 @@ class Solver:
 
     def launches_for(self, n):
         return teuk_launches_for(self.h, int(n))
+
+
+def _bcheck(rc, b, what):
+    if rc != TEUK_OK:
+        raise TeukError(rc, "%s: %s" % (what, teuk_batch_last_error(b).decode()))
+    return rc
+
+
+class Batch:
+    """Many handles stepped together (teuk_batch_*).  Jobs are Solver objects."""
+
+    def __init__(self, stream=None):
+        b = _vp()
+        _check(teuk_batch_create(_stream_handle(stream), C.byref(b)), what="teuk_batch_create")
+        self.b = b
+        self.solvers = {}
+
+    def close(self):
+        if getattr(self, "b", None):
+            teuk_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        self.close()
+
+    def add(self, solver, steps):
+        jid = C.c_int()
+        _bcheck(teuk_batch_add(self.b, solver.h, int(steps), C.byref(jid)), self.b, "teuk_batch_add")
+        self.solvers[jid.value] = solver
+        return jid.value
+
+    def remove(self, job_id):
+        _bcheck(teuk_batch_remove(self.b, int(job_id)), self.b, "teuk_batch_remove")
+        self.solvers.pop(job_id, None)
+
+    def step(self, max_steps):
+        done = C.c_long()
+        _bcheck(teuk_batch_step(self.b, int(max_steps), C.byref(done)), self.b, "teuk_batch_step")
+        return done.value
+
+    def remaining(self, job_id):
+        r = C.c_long()
+        _bcheck(teuk_batch_remaining(self.b, int(job_id), C.byref(r)), self.b, "teuk_batch_remaining")
+        return r.value
+
+    def sync(self):
+        _bcheck(teuk_batch_sync(self.b), self.b, "teuk_batch_sync")
+
+    def set_option(self, option, value):
+        _bcheck(teuk_batch_set_option(self.b, int(option), int(value)), self.b, "teuk_batch_set_option")
+
+    def autotune(self):
+        best = C.c_int()
+        _bcheck(teuk_batch_autotune(self.b, C.byref(best)), self.b, "teuk_batch_autotune")
+        return best.value
+
+    def launches_for(self, n):
+        return teuk_batch_launches_for(self.b, int(n))

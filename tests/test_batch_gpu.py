@@ -1,0 +1,152 @@
+"""Batched stepping (teuk_batch_*): many independent evolutions advanced by
+shared launches give the same bits as stepping each handle alone, and match
+the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1206_0270_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+# uneven grids, spins, modes, sources and step counts
+JOBS = [
+    dict(nr=300, nth=64, a=0.9, s=-2, m=2, steps=131, src=dict(r0=8.0, sigma=0.5), ext=(10.0, 7)),
+    dict(nr=120, nth=32, a=0.0, s=-2, m=2, steps=64, src=None, ext=(5.0, 4)),
+    dict(nr=77, nth=96, a=0.5, s=0, m=1, steps=200, src=dict(r0=6.0, sigma=1.0), ext=None),
+    dict(nr=40, nth=256, a=0.7, s=2, m=-3, steps=37, src=dict(r0=5.0, sigma=1.0), ext=(0.0, 5)),
+    dict(nr=64, nth=20, a=0.3, s=-2, m=0, steps=0, src=None, ext=None),
+    dict(nr=500, nth=128, a=0.95, s=-2, m=4, steps=129, src=dict(r0=12.0, sigma=0.3), ext=(30.0, 10)),
+]
+RMIN, RMAX = -20.0, 40.0
+
+
+@pytest.fixture(scope="module")
+def teuk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1206_0270_gb300 import build
+    build.build()
+    from paper_1206_0270_gb300 import teuk as T
+    return T
+
+
+def make(T, j, seed):
+    dt = O.stable_dt(j["nr"], j["nth"], RMIN, RMAX, j["a"], j["s"], j["m"])
+    g = T.Solver(j["nr"], j["nth"], RMIN, RMAX, dt, j["a"], j["s"], j["m"])
+    g.set_initial(*inputs.random_fields(j["nr"], j["nth"], seed=seed))
+    if j["src"]:
+        g.set_source(**j["src"])
+    if j["ext"]:
+        g.set_extraction(j["ext"][0], j["ext"][1], capacity=64)
+    return g, dt
+
+
+def collect(g, j):
+    out = list(g.state())
+    if j["ext"]:
+        out.append(g.extract()[1])
+    return out
+
+
+def run_alone(T):
+    res = []
+    for q, j in enumerate(JOBS):
+        g, _ = make(T, j, q)
+        g.step(j["steps"])
+        res.append(collect(g, j))
+        g.close()
+    return res
+
+
+@pytest.mark.parametrize("pdl,chunk,block", [(1, 64, 0), (0, 64, 0), (1, 8, 512), (1, 2, 1024)])
+def test_batch_equals_individual_runs(teuk, pdl, chunk, block):
+    alone = run_alone(teuk)
+    B = teuk.Batch()
+    B.set_option(teuk.TEUK_OPT_PDL, pdl)
+    B.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, chunk)
+    B.set_option(teuk.TEUK_OPT_BLOCK_THREADS, block)
+    solvers = []
+    for q, j in enumerate(JOBS):
+        g, _ = make(teuk, j, q)
+        solvers.append(g)
+        B.add(g, j["steps"])
+    done = B.step(10 ** 6)
+    assert done == max(j["steps"] for j in JOBS)
+    B.sync()
+    for q, (g, j) in enumerate(zip(solvers, JOBS)):
+        assert B.remaining(q) == 0
+        assert g.step_count == j["steps"]
+        for x, y in zip(collect(g, j), alone[q]):
+            np.testing.assert_array_equal(x, y)
+    B.close()
+
+
+def test_batch_in_slices_remove_and_autotune(teuk):
+    alone = run_alone(teuk)
+    B = teuk.Batch()
+    solvers = []
+    for q, j in enumerate(JOBS):
+        g, _ = make(teuk, j, q)
+        solvers.append(g)
+        B.add(g, j["steps"])
+    best = B.autotune()          # timed steps count as progress
+    assert best in (256, 512, 1024)
+    B.step(5)
+    B.step(33)
+    B.sync()
+    # take job 1 out, finish it alone, the others in the batch
+    r1 = B.remaining(1)
+    B.remove(1)
+    solvers[1].step(r1)
+    while B.step(17):
+        pass
+    B.sync()
+    for q, (g, j) in enumerate(zip(solvers, JOBS)):
+        assert g.step_count == j["steps"]
+        for x, y in zip(collect(g, j), alone[q]):
+            np.testing.assert_array_equal(x, y)
+    B.close()
+
+
+def test_batch_matches_oracle(teuk):
+    j = JOBS[0]
+    g, dt = make(teuk, j, 0)
+    other, _ = make(teuk, JOBS[3], 3)
+    B = teuk.Batch()
+    B.add(g, j["steps"])
+    B.add(other, JOBS[3]["steps"])
+    B.step(j["steps"])
+    B.sync()
+    ora = O.Solver(j["nr"], j["nth"], RMIN, RMAX, dt, j["a"], j["s"], j["m"])
+    ora.set_initial(*inputs.random_fields(j["nr"], j["nth"], seed=0))
+    ora.set_source(**j["src"])
+    ora.set_extraction(*j["ext"])
+    ora.step(j["steps"])
+    po, qo = ora.state()
+    pg, qg = g.state()
+    assert abs(pg - po).max() / abs(po).max() <= 1e-10
+    assert abs(qg - qo).max() / abs(qo).max() <= 1e-10
+    to, wo = ora.samples()
+    tg, wg = g.extract()
+    np.testing.assert_array_equal(tg, to)
+    assert abs(wg - wo).max() / abs(wo).max() <= 1e-10
+    B.close()
+
+
+def test_batch_bad_arguments(teuk):
+    B = teuk.Batch()
+    g = teuk.Solver(40, 2048, RMIN, RMAX, 1e-3, 0.5, -2, 2)
+    with pytest.raises(teuk.TeukError):
+        B.add(g, 10)              # nth > 1024
+    h = teuk.Solver(40, 32, RMIN, RMAX, 1e-3, 0.5, -2, 2)
+    B.add(h, 10)
+    with pytest.raises(teuk.TeukError):
+        B.add(h, 10)              # twice
+    with pytest.raises(teuk.TeukError):
+        B.remove(7)
+    with pytest.raises(teuk.TeukError):
+        B.set_option(teuk.TEUK_OPT_BLOCK_THREADS, 100)
+    assert B.step(0) == 0
+    B.close()
