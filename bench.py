@@ -326,7 +326,8 @@ def batch_jobs(kind, scale):
     else:
         for j in inputs.template_bank(256):
             j = dict(j)
-            j["sigma"] = 0.05
+            # the bank fixes no source width: two radial cells, at least 0.05M
+            j["sigma"] = max(0.05, 2.0 * 700.0 / (j["nr"] - 1))
             j["steps"] = max(2, int(round(j["steps"] * scale)))
             jobs.append(j)
     return jobs
