@@ -400,6 +400,67 @@ def run_batch_workload(args):
     return 0
 
 
+def run_serving(args):
+    """Poisson stream of requests through the continuous-batching service:
+    p50/p99 latency and waveforms/s, beside the same stream served one job at
+    a time in arrival order."""
+    import torch
+    from paper_1206_0270_gb300 import build
+    build.build()
+    from paper_1206_0270_gb300 import inputs, serve as S
+    from paper_1206_0270_gb300 import teuk as T
+    raw = inputs.serving_requests(args.requests, args.rate)
+
+    def request(d):
+        sigma = max(0.05, 2.0 * 700.0 / (d["nr"] - 1))
+        return S.Request(a=d["a"], s=d["s"], m=d["m"], nr=d["nr"], nth=d["nth"], steps=d["steps"], r0=d["r0"],
+                         sigma=sigma, arrival=d["arrival"])
+    reqs = [request(d) for d in raw]
+    upd = sum((r.nr - 2) * r.nth * r.steps for r in reqs)
+    budget = int(args.memory_gb * 2 ** 30)
+    # continuous batching
+    svc = S.WaveformService(memory_budget=budget, slice_steps=args.slice)
+    for r in reqs:
+        svc.submit(r)
+    torch.cuda.synchronize()
+    t0 = svc.now()
+    res = svc.run()
+    wall = svc.now() - t0
+    st = S.latency_stats(res)
+    svc.close()
+    # one job at a time, arrival order (same kernels, no batching)
+    t_start = time.perf_counter()
+    lat1, clock = [], 0.0
+    for r in reqs:
+        now = time.perf_counter() - t_start
+        if now < r.arrival:
+            time.sleep(r.arrival - now)
+        dt = T.stable_dt(r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m, r.c_r, r.c_theta)
+        g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, dt, r.a, r.s, r.m)
+        g.set_source(r0=r.r0, sigma=r.sigma)
+        g.set_extraction(r.rstar_ext, r.every, capacity=r.steps // r.every + 1)
+        g.step(r.steps)
+        g.extract()
+        g.close()
+        lat1.append(time.perf_counter() - t_start - r.arrival)
+    wall1 = time.perf_counter() - t_start
+    lat1 = np.array(lat1)
+    n = len(reqs)
+    line = dict(metric="served waveforms/s", value=n / wall, unit="waveforms/s", n_gpus=1, steps=1, warmup=0,
+                ms_per_step=1e3 * wall, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic",
+                config=dict(workload="serving", requests=n, rate_per_s=args.rate, slice_steps=args.slice,
+                            memory_budget_gb=args.memory_gb, point_updates=upd,
+                            grids="2048x64..32768x512", steps="logU[1e3, 1e4]"),
+                latency_s=dict(p50=st["p50"], p99=st["p99"], mean=st["mean"]),
+                grid_pt_updates_per_s=upd / wall,
+                one_by_one=dict(value=n / wall1, unit="waveforms/s",
+                                latency_s=dict(p50=float(np.percentile(lat1, 50)),
+                                               p99=float(np.percentile(lat1, 99)), mean=float(lat1.mean()))))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,12 +471,19 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=10, help="oracle time steps per reference step")
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch_modes", "template_bank"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch_modes", "template_bank", "serving"],
                     help="single: the Kerr 8192x128 step (default); batch_modes / template_bank: batched "
                          "waveforms/s against one job at a time")
     ap.add_argument("--steps-scale", type=float, default=0.2,
                     help="batched workloads: fraction of each job's step count that is run")
+    ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=4.0, help="serving: Poisson arrival rate (1/s)")
+    ap.add_argument("--slice", type=int, default=640, help="serving: time steps per batch slice")
+    ap.add_argument("--memory-gb", type=float, default=200.0, help="serving: device memory budget (GiB)")
     args = ap.parse_args()
+    if args.workload == "serving":
+        return run_serving(args)
     if args.workload != "single":
         return run_batch_workload(args)
     if args.warmup < 3 and args.impl == "gpu":

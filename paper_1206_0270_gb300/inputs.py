@@ -116,3 +116,23 @@ def template_bank(n_jobs: int, seed: int = 20120603):
             nr=int(rng.choice([2048, 4096, 8192, 16384])), nth=int(rng.choice([64, 128, 256])),
             steps=int(round(10 ** rng.uniform(4.0, 5.0)))))
     return jobs
+
+
+def serving_requests(n: int, rate: float, seed: int = 20120604, step_range=(1e3, 1e4),
+                     grids=((2048, 64), (4096, 64), (4096, 128), (8192, 128), (16384, 256), (32768, 512)),
+                     grid_weights=(0.25, 0.25, 0.2, 0.2, 0.08, 0.02)):
+    """A Poisson stream of waveform requests: arrival gaps ~ Exp(rate), a ~
+    U[0, 0.95], r0 ~ U[6, 20] M, m ~ U{1..4}, s = -2, grid drawn from `grids`
+    with `grid_weights`, steps ~ logU[step_range]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    w = np.asarray(grid_weights, float)
+    w = w / w.sum()
+    for _ in range(n):
+        t += rng.exponential(1.0 / rate)
+        nr, nth = grids[rng.choice(len(grids), p=w)]
+        out.append(dict(arrival=t, a=float(rng.uniform(0.0, 0.95)), r0=float(rng.uniform(6.0, 20.0)),
+                        m=int(rng.integers(1, 5)), s=-2, nr=int(nr), nth=int(nth),
+                        steps=int(round(10 ** rng.uniform(np.log10(step_range[0]), np.log10(step_range[1]))))))
+    return out

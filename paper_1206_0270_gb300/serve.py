@@ -1,0 +1,212 @@
+"""Continuous-batching waveform service on one GPU.
+
+Requests (one (a, s, m) evolution each) queue up; the service admits them
+while their device footprint fits in a memory budget, keeps every admitted
+job's state resident on the device, advances all admitted jobs together in
+slices of time steps (one teuk_batch: shared predictor/corrector launches),
+streams each job's waveform samples to the host after every slice, and
+retires finished jobs so that their memory and slot admit the next requests.
+Requests that arrive while others are running join at the next slice
+boundary.  Results do not depend on the mix: a job's arithmetic is the same
+alone and in any batch (bit-identical).
+
+All device work runs in libteuk (teuk_create / teuk_batch_* / teuk_extract);
+this module only schedules.
+"""
+from __future__ import annotations
+
+import dataclasses
+import heapq
+import time
+from typing import Callable, Optional
+
+import numpy as np
+
+from . import teuk as T
+
+
+@dataclasses.dataclass
+class Request:
+    """One waveform job.  Grid r* in [rstar_min, rstar_max], nr x nth points;
+    a circular equatorial orbit at r0 with Gaussian width sigma; waveform at
+    rstar_ext every `every` steps."""
+    a: float
+    s: int
+    m: int
+    nr: int
+    nth: int
+    steps: int
+    r0: float = 10.0
+    sigma: float = 0.05
+    rstar_min: float = -100.0
+    rstar_max: float = 600.0
+    rstar_ext: float = 500.0
+    every: int = 10
+    c_r: float = 0.5
+    c_theta: float = 0.1
+    dt: Optional[float] = None  # None: teuk_stable_dt with c_r, c_theta
+    arrival: float = 0.0        # seconds (service clock) at which it may be admitted
+
+
+def footprint_bytes(req: Request, slice_steps: int) -> int:
+    """Device memory of one admitted job: two state copies (64 B/point),
+    coefficient planes (168 B/point), b at nodes (8 B/point), half step
+    (32 B/point), waveform ring for one slice, source window (small)."""
+    pts = req.nr * req.nth
+    ring = (slice_steps // req.every + 2) * req.nth * 16
+    return pts * (64 + 168 + 8 + 32) + ring + (1 << 20)
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    request: Request
+    t: np.ndarray            # sample times (M)
+    phi: np.ndarray          # [samples, nth] complex waveform
+    submitted: float         # service-clock seconds
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.submitted
+
+
+class WaveformService:
+    """Continuous batching over teuk_batch with admission by device memory."""
+
+    def __init__(self, memory_budget: int, slice_steps: int = 640, max_jobs: int = 4096,
+                 stream=None, clock: Callable[[], float] = time.perf_counter):
+        if slice_steps < 2 or slice_steps % 2:
+            raise ValueError("slice_steps must be even and >= 2")
+        self.budget = int(memory_budget)
+        self.slice = int(slice_steps)
+        self.max_jobs = int(max_jobs)
+        self.stream = stream
+        self._clock = clock
+        self._t0 = clock()
+        self.batch = T.Batch(stream=stream)
+        self.batch.set_option(T.TEUK_OPT_GRAPH_CHUNK, 64 if self.slice % 64 == 0 else 2)
+        self._queue: list = []      # heap of (arrival, rid)
+        self._requests: dict = {}
+        self._submitted: dict = {}
+        self._running: dict = {}    # rid -> dict(solver, job, admitted, t, phi)
+        self._used = 0
+        self._next = 0
+        self.results: dict = {}
+        self._dt_cache: dict = {}
+        self.slices = 0
+
+    # -- clock -------------------------------------------------------------
+    def now(self) -> float:
+        return self._clock() - self._t0
+
+    # -- requests ------------------------------------------------------------
+    def submit(self, req: Request) -> int:
+        if footprint_bytes(req, self.slice) > self.budget:
+            raise ValueError("request needs more device memory than the whole budget")
+        rid = self._next
+        self._next += 1
+        self._requests[rid] = req
+        self._submitted[rid] = max(req.arrival, 0.0)
+        heapq.heappush(self._queue, (req.arrival, rid))
+        return rid
+
+    def pending(self) -> int:
+        return len(self._queue)
+
+    def running(self) -> int:
+        return len(self._running)
+
+    def memory_in_use(self) -> int:
+        return self._used
+
+    def _dt(self, r: Request) -> float:
+        if r.dt is not None:
+            return float(r.dt)
+        key = (r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m, r.c_r, r.c_theta)
+        if key not in self._dt_cache:
+            self._dt_cache[key] = T.stable_dt(r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m,
+                                              r.c_r, r.c_theta)
+        return self._dt_cache[key]
+
+    def _admit(self):
+        now = self.now()
+        while self._queue and self._queue[0][0] <= now and len(self._running) < self.max_jobs:
+            arrival, rid = self._queue[0]
+            r = self._requests[rid]
+            need = footprint_bytes(r, self.slice)
+            if self._used + need > self.budget:
+                break                      # first-come first-served: wait for memory to free up
+            heapq.heappop(self._queue)
+            # each handle sets up on its own stream, concurrently with the running slice
+            g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, self._dt(r), r.a, r.s, r.m)
+            g.set_source(r0=r.r0, sigma=r.sigma)
+            g.set_extraction(r.rstar_ext, r.every, capacity=self.slice // r.every + 2)
+            job = self.batch.add(g, r.steps)
+            self._used += need
+            self._running[rid] = dict(solver=g, job=job, admitted=self.now(), t=[], phi=[], need=need)
+
+    def _drain(self):
+        """Stream every running job's new samples; retire finished jobs."""
+        self.batch.sync()
+        done = []
+        for rid, st in self._running.items():
+            t, w = st["solver"].extract(cap=self.slice // self._requests[rid].every + 2)
+            if len(t):
+                st["t"].append(t)
+                st["phi"].append(w)
+            if self.batch.remaining(st["job"]) == 0:
+                done.append(rid)
+        fin = self.now()
+        for rid in done:
+            st = self._running.pop(rid)
+            self.batch.remove(st["job"])
+            st["solver"].close()
+            self._used -= st["need"]
+            r = self._requests[rid]
+            nth = r.nth
+            t = np.concatenate(st["t"]) if st["t"] else np.zeros(0)
+            phi = np.concatenate(st["phi"]) if st["phi"] else np.zeros((0, nth), complex)
+            self.results[rid] = Result(rid, r, t, phi, self._submitted[rid], st["admitted"], fin)
+
+    def step(self) -> bool:
+        """One service iteration: launch a slice for the admitted jobs, admit
+        arrivals (their set-up overlaps the slice), then stream samples and
+        retire finished jobs.  New jobs join the batch at the next slice.
+        Returns False when nothing is queued or running."""
+        had_jobs = bool(self._running)
+        if had_jobs:
+            self.batch.step(self.slice)
+            self.slices += 1
+        self._admit()
+        if had_jobs:
+            self._drain()
+        elif not self._running:
+            if not self._queue:
+                return False
+            wait = self._queue[0][0] - self.now()   # idle until the next arrival
+            if wait > 0:
+                time.sleep(min(wait, 0.01))
+        return True
+
+    def run(self, until_empty: bool = True, max_seconds: float = float("inf")):
+        t_end = self.now() + max_seconds
+        while self.now() < t_end:
+            if not self.step() and until_empty:
+                break
+        return self.results
+
+    def close(self):
+        for st in self._running.values():
+            st["solver"].close()
+        self._running.clear()
+        self.batch.close()
+
+
+def latency_stats(results) -> dict:
+    lat = np.array([r.latency for r in results.values()])
+    if lat.size == 0:
+        return dict(p50=None, p99=None, mean=None, n=0)
+    return dict(p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)),
+                mean=float(lat.mean()), n=int(lat.size))

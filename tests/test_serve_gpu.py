@@ -1,0 +1,81 @@
+"""Continuous-batching service: admission by device memory, jobs joining and
+leaving between slices, streamed waveforms; each result is the same alone and
+in the mix."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def serve():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1206_0270_gb300 import build
+    build.build()
+    from paper_1206_0270_gb300 import serve as S
+    return S
+
+
+def reqs(S):
+    R = S.Request
+    return [
+        R(a=0.9, s=-2, m=2, nr=600, nth=64, steps=900, r0=10.0, sigma=1.0, rstar_ext=40.0, every=10),
+        R(a=0.3, s=-2, m=1, nr=300, nth=32, steps=320, r0=8.0, sigma=2.0, rstar_ext=30.0, every=8, arrival=0.0),
+        R(a=0.7, s=0, m=3, nr=1000, nth=128, steps=1500, r0=12.0, sigma=1.0, rstar_ext=50.0, every=5),
+        R(a=0.0, s=-2, m=2, nr=200, nth=16, steps=2, r0=6.0, sigma=3.0, rstar_ext=20.0, every=1),
+        R(a=0.5, s=2, m=-1, nr=400, nth=48, steps=700, r0=9.0, sigma=1.5, rstar_ext=30.0, every=7),
+    ]
+
+
+def run_alone(S, r):
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=64)
+    rid = svc.submit(r)
+    res = svc.run()
+    svc.close()
+    return res[rid]
+
+
+def test_results_same_alone_and_in_the_mix(serve):
+    S = serve
+    rs = reqs(S)
+    alone = [run_alone(S, r) for r in rs]
+    # the mix: a budget that fits about two jobs at a time, staggered arrivals
+    budget = 2 * S.footprint_bytes(rs[2], 64)
+    svc = S.WaveformService(memory_budget=budget, slice_steps=64)
+    ids = []
+    for k, r in enumerate(rs):
+        r2 = S.Request(**{**r.__dict__, "arrival": 0.002 * k})
+        ids.append(svc.submit(r2))
+    peak = 0
+    while svc.step():
+        peak = max(peak, svc.memory_in_use())
+        assert svc.memory_in_use() <= budget
+    assert peak > S.footprint_bytes(rs[2], 64)   # jobs really overlapped on the device
+    assert svc.slices > 0
+    for rid, a in zip(ids, alone):
+        r = svc.results[rid]
+        assert len(r.t) == r.request.steps // r.request.every
+        np.testing.assert_array_equal(r.t, a.t)
+        np.testing.assert_array_equal(r.phi, a.phi)
+        assert r.finished >= r.admitted >= r.submitted - 1e-9
+    st = S.latency_stats(svc.results)
+    assert st["n"] == len(rs) and st["p99"] >= st["p50"] > 0
+    svc.close()
+
+
+def test_admission_respects_budget_and_rejects_oversize(serve):
+    S = serve
+    r = S.Request(a=0.5, s=-2, m=2, nr=400, nth=64, steps=200, sigma=1.0, rstar_ext=30.0)
+    one = S.footprint_bytes(r, 64)
+    svc = S.WaveformService(memory_budget=int(1.5 * one), slice_steps=64)
+    for _ in range(3):
+        svc.submit(r)
+    svc.step()
+    assert svc.running() == 1 and svc.pending() == 2    # only one fits
+    svc.run()
+    assert len(svc.results) == 3 and svc.memory_in_use() == 0
+    with pytest.raises(ValueError):
+        svc.submit(S.Request(a=0.5, s=-2, m=2, nr=40000, nth=512, steps=10))
+    svc.close()
