@@ -67,6 +67,24 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, device) -> float:
+    """Max of x over the ranks of the default process group (x itself when
+    there is no group).  NCCL needs device="cuda"; gloo works with "cpu"."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, slowest_seconds: float) -> float:
+    """Replicas: every rank processes units_per_rank; the job takes as long as
+    the slowest rank."""
+    return world * units_per_rank / slowest_seconds
+
+
 def workload():
     from paper_1206_0270_gb300 import inputs
     return dict(inputs.WORKLOADS[WORKLOAD])
@@ -226,14 +244,12 @@ def run_gpu(args):
         torch.cuda.synchronize()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = reduce_max(total_ms, "cuda")
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     assert S.check_finite(), "state became non-finite"
     launches = args.steps * S.launches_for(args.chunk)
-    value = ws * upd_per_step * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(ws, upd_per_step * args.steps, total_ms / 1e3)
 
     # ---- dominant kernel: average launch duration over the timed region --------------
     per_launch_s = (total_ms / 1e3) / (args.steps * args.chunk)
@@ -273,12 +289,8 @@ def run_gpu(args):
     nsamp = 0
     for _ in range(args.steps):
         nsamp = e2e_step()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = dict(value=ws * upd_per_step * args.steps / e2e_s, unit=UNIT,
+    e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
+    e2e = dict(value=whole_job_rate(ws, upd_per_step * args.steps, e2e_s), unit=UNIT,
                h2d_bytes_per_step=2 * nr * nth * 16, d2h_bytes_per_step=nsamp * (nth * 16 + 8))
     E.close()
 

@@ -131,6 +131,14 @@ int teuk_step(teuk_handle *h, long n);
  * the previous call (the newest `capacity` samples are returned). */
 int teuk_extract(teuk_handle *h, double *t_out, double *phi_out, long cap, long *n_out);
 
+/* Restore a checkpoint: the state from HOST arrays phi, pi (layout as in
+ * teuk_set_initial) taken after `step` time steps.  The step count is set to
+ * `step`, so the source phase and the waveform sampling continue where the
+ * checkpointed run stood (samples already taken are not replayed); resuming
+ * gives bit-identical results to an uninterrupted run.  The radial boundary
+ * rows are forced to zero.  Synchronises. */
+int teuk_set_state(teuk_handle *h, const double *phi, const double *pi, long step);
+
 /* Copy the current state to HOST arrays (either may be NULL).  Synchronises. */
 int teuk_get_state(teuk_handle *h, double *phi, double *pi);
 

@@ -366,6 +366,22 @@ extern "C" int teuk_set_initial(teuk_handle *h, const double *phi, const double 
     return TEUK_OK;
 }
 
+extern "C" int teuk_set_state(teuk_handle *h, const double *phi, const double *pi, long step)
+{
+    if (!h || !phi || !pi || step < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_state: NULL array or step < 0");
+    const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
+    CU(cudaMemcpyAsync(h->phi[0], phi, bytes, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->pi[0], pi, bytes, cudaMemcpyHostToDevice, h->stream));
+    CU(launch_zero_boundary_rows(h->phi[0], h->pi[0], h->nr, h->nth, h->stream));
+    CU(launch_zero_boundary_rows(h->phi[1], h->pi[1], h->nr, h->nth, h->stream));
+    CU(launch_set_counter(h->d_step, step, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    h->nstep = step;
+    h->drained = h->sp.ext.i_ext >= 0 ? step / h->sp.ext.every : 0;
+    return TEUK_OK;
+}
+
 extern "C" int teuk_set_initial_device(teuk_handle *h, const double *phi, const double *pi)
 {
     if (!h || !phi) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_initial_device: NULL argument");

@@ -53,6 +53,7 @@ _SIGS = {
     "teuk_destroy": (C.c_int, [_vp]),
     "teuk_set_initial": (C.c_int, [_vp, _dp, _dp]),
     "teuk_set_initial_device": (C.c_int, [_vp, _vp, _vp]),
+    "teuk_set_state": (C.c_int, [_vp, _dp, _dp, C.c_long]),
     "teuk_set_source": (C.c_int, [_vp, C.POINTER(teuk_orbit)]),
     "teuk_set_extraction": (C.c_int, [_vp, C.c_double, C.c_int, C.c_long]),
     "teuk_step": (C.c_int, [_vp, C.c_long]),
@@ -163,6 +164,13 @@ class Solver:
         _check(teuk_set_initial(self.h, _ptr(phi.view(np.float64)),
                                 None if pi is None else _ptr(pi.view(np.float64))), self.h,
                "teuk_set_initial")
+
+    def set_state(self, phi, pi, step):
+        phi = np.ascontiguousarray(phi, dtype=np.complex128)
+        pi = np.ascontiguousarray(pi, dtype=np.complex128)
+        assert phi.shape == pi.shape == (self.nr, self.nth)
+        _check(teuk_set_state(self.h, _ptr(phi.view(np.float64)), _ptr(pi.view(np.float64)), int(step)),
+               self.h, "teuk_set_state")
 
     def set_initial_device(self, phi_ptr, pi_ptr=None):
         _check(teuk_set_initial_device(self.h, phi_ptr, pi_ptr), self.h, "teuk_set_initial_device")

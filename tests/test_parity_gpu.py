@@ -229,6 +229,38 @@ def test_pdl_small_grids_match_plain_launches(teuk, nr, nth):
         np.testing.assert_array_equal(st[1], out[0][1])
 
 
+def test_checkpoint_resume_is_bit_identical(teuk):
+    nr, nth = 400, 64
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, 0.9, -2, 2)
+    u = inputs.random_fields(nr, nth, seed=21)
+
+    def fresh():
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
+        g.set_source(**SRC)
+        g.set_extraction(10.0, 7, capacity=100)
+        return g
+    a = fresh()
+    a.set_initial(*u)
+    a.step(300)
+    ref = a.state()
+    t_ref, w_ref = a.extract()
+    b = fresh()
+    b.set_initial(*u)
+    b.step(130)
+    t1, w1 = b.extract()
+    ck = b.state()
+    b.close()
+    c = fresh()
+    c.set_state(ck[0], ck[1], 130)
+    assert c.step_count == 130
+    c.step(170)
+    t2, w2 = c.extract()
+    for x, y in zip(c.state(), ref):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(np.concatenate([t1, t2]), t_ref)
+    np.testing.assert_array_equal(np.concatenate([w1, w2]), w_ref)
+
+
 def test_runs_are_deterministic(teuk):
     kw = dict(source=SRC, seed=4)
     a = run_pair(teuk, 200, 64, -20.0, 40.0, 0.9, -2, 2, 300, **kw)
