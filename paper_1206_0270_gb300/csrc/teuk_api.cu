@@ -177,7 +177,7 @@ static void choose_launch(teuk_handle *h, int rows_per_block)
     if (rows_per_block <= 0) {
         const int threads = fused_block_threads(h->nth);
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(), threads,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(h->sp.real_coef), threads,
                                                           fused_smem_bytes(h->nth)) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
@@ -282,6 +282,8 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
 
     SetupParams su{};
     su.nr = nr; su.nth = nth; su.s = s; su.m = m; su.parity = h->parity;
+    // a = 0, or s = m = 0: every coefficient is real
+    su.real_coef = (a == 0.0 || (s == 0 && m == 0)) ? 1 : 0;
     su.a = a; su.h = h->h; su.dth = h->dth; su.dt = h->dt;
     su.r_node = d_tab; su.D_node = d_tab + nr; su.r_mid = d_tab + 2 * nr; su.D_mid = su.r_mid + (nr - 1);
     su.sin_th = su.D_mid + (nr - 1); su.cos_th = su.sin_th + nth; su.cot_th = su.cos_th + nth;
@@ -303,6 +305,8 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     StepParams &p = h->sp;
     p.nr = nr; p.nth = nth; p.dt = h->dt; p.q = 0.25 * h->dt; p.half_dt = 0.5 * h->dt;
     p.one = 1.0; p.nzero = -0.0;
+    p.real_coef = su.real_coef;
+    h->su = su;
     p.pred = PredPlanes{su.pa, su.pb, su.eb, su.KAp, su.KCp, su.P1, su.Q1, su.Q2};
     p.corr = CorrPlanes{su.tb, su.nt2, su.KAc, su.KCc, su.R1, su.R3, su.R4};
     p.src = SourceWindow{0, -1, 0, -1, nullptr, nullptr, 0.0, 0};
@@ -311,16 +315,17 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     h->variant = nth <= 1024 ? 2 : 1;
     if (nth <= 1024) {
         const size_t smem = fused_smem_bytes(nth);
-        if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(fused_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-            return bail(TEUK_ERR_CUDA);
+        if (smem > 48 * 1024)
+            for (int rl = 0; rl < 2; ++rl)
+                if (cudaFuncSetAttribute(fused_kernel_ptr(rl), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                    cudaSuccess)
+                    return bail(TEUK_ERR_CUDA);
         choose_launch(h, 0);
         const size_t ssm = split_smem_bytes(nth);
         if (ssm > 48 * 1024)
-            for (int w = 0; w < 2; ++w)
-                if (cudaFuncSetAttribute(split_kernel_ptr(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) !=
-                    cudaSuccess)
+            for (int w = 0; w < 4; ++w)
+                if (cudaFuncSetAttribute(split_kernel_ptr(w & 1, w >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ssm) != cudaSuccess)
                     return bail(TEUK_ERR_CUDA);
     }
     if (h->variant != 0) {  // the two-kernel variants keep the half step in device memory
@@ -567,6 +572,18 @@ extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
         destroy_graphs(h);
         h->chunk = (int)value;
         return TEUK_OK;
+    case TEUK_OPT_REAL_PATH: {
+        if (value != 0 && value != 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: real path is 0 or 1");
+        const int real = (value == 1 && (h->a == 0.0 || (h->s == 0 && h->m == 0))) ? 1 : 0;
+        if (real == h->sp.real_coef) return TEUK_OK;
+        CU(cudaStreamSynchronize(h->stream));
+        destroy_graphs(h);
+        h->su.real_coef = real;
+        CU(launch_setup(h->su, h->stream));  // rewrite the planes in the other layout
+        CU(cudaStreamSynchronize(h->stream));
+        h->sp.real_coef = real;
+        return TEUK_OK;
+    }
     default:
         return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: unknown option");
     }

@@ -21,6 +21,7 @@ struct teuk_handle {
     long long *d_step = nullptr;
     unsigned long long *d_count = nullptr;
     teuk::StepParams sp{};
+    teuk::SetupParams su{};  // kept to rebuild the coefficient planes
 
     double *d_src = nullptr;       // source windows (gP then gC)
     double2 *d_ring = nullptr;

@@ -70,6 +70,7 @@ struct StepParams {
     int nr, nth;
     double dt, q, half_dt; // dt, dt/4, dt/2
     double one, nzero;     // 1 and -0: operands that turn FP64 adds and multiplies into FMAs
+    int real_coef;         // 1: P1, Q1, Q2, R1, R3, R4 are packed real planes (no imaginary parts)
     PredPlanes pred;
     CorrPlanes corr;
     SourceWindow src;
@@ -98,6 +99,7 @@ struct JobDesc {
 
 struct SetupParams {
     int nr, nth, s, m, parity;
+    int real_coef;  // write P1, Q1, Q2, R1, R3, R4 as packed real planes
     double a, h, dth, dt;
     const double *r_node, *D_node, *r_mid, *D_mid;  // radial tables (Delta as D)
     const double *sin_th, *cos_th, *cot_th;         // angular tables
@@ -145,9 +147,9 @@ const void *batch_kernel_ptr(int which);
 
 int fused_block_threads(int nth);
 size_t fused_smem_bytes(int nth);
-const void *fused_kernel_ptr();
+const void *fused_kernel_ptr(int real);
 int split_rows_per_block(int nth);
 size_t split_smem_bytes(int nth);
-const void *split_kernel_ptr(int which);
+const void *split_kernel_ptr(int which, int real);
 
 }  // namespace teuk

@@ -125,18 +125,36 @@ __global__ void setup_kernel(SetupParams sp)
         sp.pa[k] = 0.5 + beta;
         sp.pb[k] = 0.5 - beta;
         sp.eb[k] = 2.0 * beta;
-        sp.P1[k] = make_double2(0.5 - beta - q * c.ct_re, -q * c.ct_im);
-        sp.Q1[k] = make_double2(-g_re - q * wr, -g_im - q * wi);
-        sp.Q2[k] = make_double2(g_re - q * wr, g_im - q * wi);
+        const double2 P1 = make_double2(0.5 - beta - q * c.ct_re, -q * c.ct_im);
+        const double2 Q1 = make_double2(-g_re - q * wr, -g_im - q * wi);
+        const double2 Q2 = make_double2(g_re - q * wr, g_im - q * wi);
+        if (sp.real_coef) {
+            ((double *)sp.P1)[k] = P1.x;
+            ((double *)sp.Q1)[k] = Q1.x;
+            ((double *)sp.Q2)[k] = Q2.x;
+        } else {
+            sp.P1[k] = P1;
+            sp.Q1[k] = Q1;
+            sp.Q2[k] = Q2;
+        }
         sp.KAp[k] = q * c.kappa * A;
         sp.KCp[k] = q * c.kappa * C;
     } else {
         const double hd = 0.5 * sp.dt;
         sp.tb[k] = 2.0 * beta;
         sp.nt2[k] = -4.0 * beta;
-        sp.R1[k] = make_double2(2.0 * beta - hd * c.ct_re, -hd * c.ct_im);
-        sp.R3[k] = make_double2(2.0 * g_re - hd * wr, 2.0 * g_im - hd * wi);
-        sp.R4[k] = make_double2(-2.0 * g_re - hd * wr, -2.0 * g_im - hd * wi);
+        const double2 R1 = make_double2(2.0 * beta - hd * c.ct_re, -hd * c.ct_im);
+        const double2 R3 = make_double2(2.0 * g_re - hd * wr, 2.0 * g_im - hd * wi);
+        const double2 R4 = make_double2(-2.0 * g_re - hd * wr, -2.0 * g_im - hd * wi);
+        if (sp.real_coef) {
+            ((double *)sp.R1)[k] = R1.x;
+            ((double *)sp.R3)[k] = R3.x;
+            ((double *)sp.R4)[k] = R4.x;
+        } else {
+            sp.R1[k] = R1;
+            sp.R3[k] = R3;
+            sp.R4[k] = R4;
+        }
         sp.KAc[k] = hd * c.kappa * A;
         sp.KCc[k] = hd * c.kappa * C;
         sp.b_node[k] = c.b;
@@ -172,6 +190,16 @@ struct CorrCoef {
     double2 R1, R3, R4;
 };
 
+// REAL: P1, Q1, Q2 (and R1, R3, R4) are stored as packed real planes (the
+// coefficients of a = 0, or of s = m = 0, have no imaginary part).
+template <bool REAL>
+__device__ __forceinline__ double2 ld_coef(const double2 *plane, size_t k)
+{
+    if (REAL) return make_double2(ldg((const double *)plane + k), 0.0);
+    return ldg(plane + k);
+}
+
+template <bool REAL>
 __device__ __forceinline__ PredCoef load_pred(const StepParams &p, size_t k)
 {
     PredCoef c;
@@ -180,12 +208,13 @@ __device__ __forceinline__ PredCoef load_pred(const StepParams &p, size_t k)
     c.eb = ldg(p.pred.eb + k);
     c.KA = ldg(p.pred.KA + k);
     c.KC = ldg(p.pred.KC + k);
-    c.P1 = ldg(p.pred.P1 + k);
-    c.Q1 = ldg(p.pred.Q1 + k);
-    c.Q2 = ldg(p.pred.Q2 + k);
+    c.P1 = ld_coef<REAL>(p.pred.P1, k);
+    c.Q1 = ld_coef<REAL>(p.pred.Q1, k);
+    c.Q2 = ld_coef<REAL>(p.pred.Q2, k);
     return c;
 }
 
+template <bool REAL>
 __device__ __forceinline__ CorrCoef load_corr(const StepParams &p, size_t k)
 {
     CorrCoef c;
@@ -193,14 +222,29 @@ __device__ __forceinline__ CorrCoef load_corr(const StepParams &p, size_t k)
     c.nt2 = ldg(p.corr.nt2 + k);
     c.KA = ldg(p.corr.KA + k);
     c.KC = ldg(p.corr.KC + k);
-    c.R1 = ldg(p.corr.R1 + k);
-    c.R3 = ldg(p.corr.R3 + k);
-    c.R4 = ldg(p.corr.R4 + k);
+    c.R1 = ld_coef<REAL>(p.corr.R1, k);
+    c.R3 = ld_coef<REAL>(p.corr.R3, k);
+    c.R4 = ld_coef<REAL>(p.corr.R4, k);
     return c;
+}
+
+// acc += c x for a complex coefficient (4 FMAs), or a real one (2 FMAs)
+template <bool REAL>
+__device__ __forceinline__ void kfma(double2 &acc, const double2 c, const double2 x)
+{
+    if (REAL) rfma(acc, c.x, x); else cfma(acc, c, x);
+}
+
+template <bool REAL>
+__device__ __forceinline__ double2 kmul(const double2 c, const double2 x, const Ops o)
+{
+    if (REAL) return make_double2(fma_rn(c.x, x.x, o.nzero), fma_rn(c.x, x.y, o.nzero));
+    return cmul(c, x, o);
 }
 
 // Predictor (Eq. 3) at one mid-point.  phi0/pi0: u at row hp, phi1/pi1: u at
 // row hp + 1, sup/sdn: sigma = Phi_hp + Phi_{hp+1} at j+1, j-1.
+template <bool REAL>
 __device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, const Ops ops, double2 phi0,
                                               double2 pi0, double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
@@ -210,10 +254,10 @@ __device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, const
     o.phi = make_double2(fma_rn(c.pa, phi0.x, ops.nzero), fma_rn(c.pa, phi0.y, ops.nzero));
     rfma(o.phi, c.pb, phi1);
     rfma(o.phi, q, tau);
-    o.pi = cmul(c.P1, tau, ops);
+    o.pi = kmul<REAL>(c.P1, tau, ops);
     rfma(o.pi, c.eb, pi1);
-    cfma(o.pi, c.Q1, phi0);
-    cfma(o.pi, c.Q2, phi1);
+    kfma<REAL>(o.pi, c.Q1, phi0);
+    kfma<REAL>(o.pi, c.Q2, phi1);
     rfma(o.pi, c.KA, sup);
     rfma(o.pi, c.KC, sdn);
     return o;
@@ -221,14 +265,16 @@ __device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, const
 
 __device__ __forceinline__ Ops ops_of(const StepParams &p) { return Ops{p.one, p.nzero}; }
 
+template <bool REAL>
 __device__ __forceinline__ HalfStep predict(const StepParams &p, size_t k, double2 phi0, double2 pi0,
                                             double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
-    return predict_c(load_pred(p, k), p.q, ops_of(p), phi0, pi0, phi1, pi1, sup, sdn);
+    return predict_c<REAL>(load_pred<REAL>(p, k), p.q, ops_of(p), phi0, pi0, phi1, pi1, sup, sdn);
 }
 
 // Corrector (Eq. 4) at one node.  hp: half step at i + 1/2, hm: at i - 1/2,
 // sup/sdn: sigma' = Phi^{i+1/2} + Phi^{i-1/2} at j+1, j-1.
+template <bool REAL>
 __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, const Ops ops, double2 phi,
                                           double2 pi, const HalfStep &hp, const HalfStep &hm, double2 sup,
                                           double2 sdn, double2 *phi_out, double2 *pi_out)
@@ -240,21 +286,22 @@ __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, con
     rfma(nphi, c.tb, hm.phi);
     rfma(nphi, half_dt, tau);
     double2 npi = pi;
-    cfma(npi, c.R1, tau);
+    kfma<REAL>(npi, c.R1, tau);
     rfma(npi, c.nt2, hm.pi);
-    cfma(npi, c.R3, hp.phi);
-    cfma(npi, c.R4, hm.phi);
+    kfma<REAL>(npi, c.R3, hp.phi);
+    kfma<REAL>(npi, c.R4, hm.phi);
     rfma(npi, c.KA, sup);
     rfma(npi, c.KC, sdn);
     *phi_out = nphi;
     *pi_out = npi;
 }
 
+template <bool REAL>
 __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 phi, double2 pi,
                                         const HalfStep &hp, const HalfStep &hm, double2 sup,
                                         double2 sdn, double2 *phi_out, double2 *pi_out)
 {
-    correct_c(load_corr(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
+    correct_c<REAL>(load_corr<REAL>(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -266,6 +313,7 @@ __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 p
 size_t fused_smem_bytes(int nth) { return sizeof(double2) * 4 * (size_t)(nth + 2); }
 int fused_block_threads(int nth) { return ((nth + 31) / 32) * 32; }
 
+template <bool REAL>
 __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2 *__restrict__ Phi,
                                                       const double2 *__restrict__ Pi,
                                                       double2 *__restrict__ PhiO,
@@ -307,7 +355,7 @@ __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2
     double2 phn = Phi[(size_t)i0 * nth + jj], pin = Pi[(size_t)i0 * nth + jj];
     if (act) s_sig[j + 1] = add2(phc, phn, ops_of(p));
     __syncthreads();
-    HalfStep hm = predict(p, (size_t)(i0 - 1) * nth + jj, phc, pic, phn, pin, s_sig[jj + 2], s_sig[jj]);
+    HalfStep hm = predict<REAL>(p, (size_t)(i0 - 1) * nth + jj, phc, pic, phn, pin, s_sig[jj + 2], s_sig[jj]);
     if (src_mid && i0 - 1 >= sw.mid_lo && i0 - 1 <= sw.mid_hi)
         rfma(hm.pi, ldg(sw.gP + (size_t)(i0 - 1 - sw.mid_lo) * nth + jj), s_phase[0]);
     phc = phn;
@@ -316,8 +364,8 @@ __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2
     // Loads for row i are issued one iteration ahead: u_{i+1} and the
     // predictor/corrector coefficients of row i arrive while row i-1 computes.
     double2 phn_nx = Phi[(size_t)(i0 + 1) * nth + jj], pin_nx = Pi[(size_t)(i0 + 1) * nth + jj];
-    PredCoef pc_nx = load_pred(p, (size_t)i0 * nth + jj);
-    CorrCoef cc_nx = load_corr(p, (size_t)i0 * nth + jj);
+    PredCoef pc_nx = load_pred<REAL>(p, (size_t)i0 * nth + jj);
+    CorrCoef cc_nx = load_corr<REAL>(p, (size_t)i0 * nth + jj);
     int buf = 1;
     for (int i = i0; i < i1; ++i) {
         phn = phn_nx;
@@ -329,13 +377,13 @@ __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2
             const int unx = min(i + 2, p.nr - 1);
             phn_nx = Phi[(size_t)unx * nth + jj];
             pin_nx = Pi[(size_t)unx * nth + jj];
-            pc_nx = load_pred(p, (size_t)inx * nth + jj);
-            cc_nx = load_corr(p, (size_t)inx * nth + jj);
+            pc_nx = load_pred<REAL>(p, (size_t)inx * nth + jj);
+            cc_nx = load_corr<REAL>(p, (size_t)inx * nth + jj);
         }
         double2 *sg = s_sig + buf * W;
         if (act) sg[j + 1] = add2(phc, phn, ops_of(p));
         __syncthreads();
-        HalfStep hp = predict_c(pc, p.q, ops_of(p), phc, pic, phn, pin, sg[jj + 2], sg[jj]);
+        HalfStep hp = predict_c<REAL>(pc, p.q, ops_of(p), phc, pic, phn, pin, sg[jj + 2], sg[jj]);
         if (src_mid && i >= sw.mid_lo && i <= sw.mid_hi)
             rfma(hp.pi, ldg(sw.gP + (size_t)(i - sw.mid_lo) * nth + jj), s_phase[0]);
 
@@ -344,7 +392,7 @@ __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2
         __syncthreads();
         const size_t kc = (size_t)i * nth + jj;
         double2 nphi, npi;
-        correct_c(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
+        correct_c<REAL>(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
         if (src_node && i >= sw.node_lo && i <= sw.node_hi)
             rfma(npi, ldg(sw.gC + (size_t)(i - sw.node_lo) * nth + jj), s_phase[1]);
         if (act) {
@@ -362,15 +410,17 @@ __global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2
     }
 }
 
-const void *fused_kernel_ptr() { return (const void *)lw_step_fused; }
+const void *fused_kernel_ptr(int real) { return real ? (const void *)lw_step_fused<true> : (const void *)lw_step_fused<false>; }
 
 cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const double2 *Pi,
                               double2 *PhiO, double2 *PiO, int k, int rows_per_block, int nblocks,
                               cudaStream_t st)
 {
     const int threads = fused_block_threads(p.nth);
-    lw_step_fused<<<nblocks, threads, fused_smem_bytes(p.nth), st>>>(p, Phi, Pi, PhiO, PiO, k,
-                                                                     rows_per_block);
+    if (p.real_coef)
+        lw_step_fused<true><<<nblocks, threads, fused_smem_bytes(p.nth), st>>>(p, Phi, Pi, PhiO, PiO, k, rows_per_block);
+    else
+        lw_step_fused<false><<<nblocks, threads, fused_smem_bytes(p.nth), st>>>(p, Phi, Pi, PhiO, PiO, k, rows_per_block);
     return cudaGetLastError();
 }
 
@@ -378,6 +428,7 @@ cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const dou
 // Two-kernel variant: predictor writes the half-step fields to device memory
 // ---------------------------------------------------------------------------
 
+template <bool REAL>
 __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
                                   const double2 *__restrict__ Pi, double2 *__restrict__ PhiH,
                                   double2 *__restrict__ PiH, int k)
@@ -393,7 +444,7 @@ __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
     const size_t r0 = (size_t)hp * nth, r1 = r0 + nth;
     const double2 sup = add2(Phi[r0 + ju], Phi[r1 + ju], ops_of(p));
     const double2 sdn = add2(Phi[r0 + jd], Phi[r1 + jd], ops_of(p));
-    HalfStep o = predict(p, k0, phi0, pi0, phi1, pi1, sup, sdn);
+    HalfStep o = predict<REAL>(p, k0, phi0, pi0, phi1, pi1, sup, sdn);
     const SourceWindow &sw = p.src;
     if (sw.active && hp >= sw.mid_lo && hp <= sw.mid_hi) {
         const long long n = *p.step_base + k;
@@ -403,6 +454,7 @@ __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
     PiH[k0] = o.pi;
 }
 
+template <bool REAL>
 __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
                                   const double2 *__restrict__ Pi, const double2 *__restrict__ PhiH,
                                   const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
@@ -424,7 +476,7 @@ __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
     const double2 sup = add2(PhiH[kp - j + ju], PhiH[km - j + ju], ops_of(p));
     const double2 sdn = add2(PhiH[kp - j + jd], PhiH[km - j + jd], ops_of(p));
     double2 nphi, npi;
-    correct(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, &nphi, &npi);
+    correct<REAL>(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, &nphi, &npi);
     const long long n = *p.step_base + k;
     const SourceWindow &sw = p.src;
     if (sw.active && i >= sw.node_lo && i <= sw.node_hi)
@@ -444,9 +496,15 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
 {
     const int threads = 256;
     const long long np = (long long)(p.nr - 1) * p.nth, nc = (long long)(p.nr - 2) * p.nth;
-    lw_predict_kernel<<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
-    lw_correct_kernel<<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
+    if (p.real_coef) {
+        lw_predict_kernel<true><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
+        lw_correct_kernel<true><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
                                                                                   PhiO, PiO, k);
+    } else {
+        lw_predict_kernel<false><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
+        lw_correct_kernel<false><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
+                                                                                  PhiO, PiO, k);
+    }
     return cudaGetLastError();
 }
 
@@ -462,6 +520,7 @@ int split_rows_per_block(int nth)
     return cols >= 256 ? 1 : 256 / cols;
 }
 
+template <bool REAL>
 __global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
                                                          const double2 *__restrict__ Pi,
                                                          double2 *__restrict__ PhiH,
@@ -478,12 +537,12 @@ __global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const dou
     double2 *row = smem + threadIdx.y * W;
     if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
     const size_t k0 = (size_t)hq * nth + jj;
-    const PredCoef c = load_pred(p, k0);
+    const PredCoef c = load_pred<REAL>(p, k0);
     grid_dependency_wait();
     const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth), pi1 = ldcg(Pi + k0 + nth);
     if (colok) row[j + 1] = add2(phi0, phi1, ops_of(p));
     __syncthreads();
-    HalfStep o = predict_c(c, p.q, ops_of(p), phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
+    HalfStep o = predict_c<REAL>(c, p.q, ops_of(p), phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
     const SourceWindow &sw = p.src;
     if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
         const long long n = ldcg(p.step_base) + k;
@@ -496,6 +555,7 @@ __global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const dou
     allow_dependents();  // after the last store: the dependent sees only writes made before it
 }
 
+template <bool REAL>
 __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
                                                          const double2 *__restrict__ Pi,
                                                          const double2 *__restrict__ PhiH,
@@ -514,7 +574,7 @@ __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const dou
     double2 *row = smem + threadIdx.y * W;
     if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
     const size_t kc = (size_t)iq * nth + jj;
-    const CorrCoef c = load_corr(p, kc);
+    const CorrCoef c = load_corr<REAL>(p, kc);
     grid_dependency_wait();
     HalfStep hp, hm;
     hp.phi = ldcg(PhiH + kc);
@@ -525,7 +585,7 @@ __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const dou
     if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops_of(p));
     __syncthreads();
     double2 nphi, npi;
-    correct_c(c, p.half_dt, ops_of(p), phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
+    correct_c<REAL>(c, p.half_dt, ops_of(p), phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
     const long long n = ldcg(p.step_base) + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
@@ -543,7 +603,11 @@ __global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const dou
 }
 
 size_t split_smem_bytes(int nth) { return sizeof(double2) * (size_t)split_rows_per_block(nth) * (nth + 2); }
-const void *split_kernel_ptr(int which) { return which ? (const void *)lw_correct_split : (const void *)lw_predict_split; }
+const void *split_kernel_ptr(int which, int real)
+{
+    if (real) return which ? (const void *)lw_correct_split<true> : (const void *)lw_predict_split<true>;
+    return which ? (const void *)lw_correct_split<false> : (const void *)lw_predict_split<false>;
+}
 
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
                               double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl)
@@ -559,11 +623,14 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     cfg.attrs = pdl ? attr : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;
     cfg.gridDim = dim3((p.nr - 1 + R - 1) / R);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, lw_predict_split, p, Phi, Pi, PhiH, PiH, k);
+    cudaError_t e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_predict_split<true>, p, Phi, Pi, PhiH, PiH, k)
+                                : cudaLaunchKernelEx(&cfg, lw_predict_split<false>, p, Phi, Pi, PhiH, PiH, k);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3((p.nr - 2 + R - 1) / R);
-    e = cudaLaunchKernelEx(&cfg, lw_correct_split, p, Phi, Pi, (const double2 *)PhiH, (const double2 *)PiH,
-                           PhiO, PiO, k);
+    e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_correct_split<true>, p, Phi, Pi, (const double2 *)PhiH,
+                                         (const double2 *)PiH, PhiO, PiO, k)
+                    : cudaLaunchKernelEx(&cfg, lw_correct_split<false>, p, Phi, Pi, (const double2 *)PhiH,
+                                         (const double2 *)PiH, PhiO, PiO, k);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -626,14 +693,16 @@ __global__ void __launch_bounds__(1024) lw_predict_batch(const JobDesc *__restri
     double2 *row = rows + tyc * W;
     if (slot && j < 2) row[j == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
     const size_t k0 = (size_t)hq * nth + jj;
-    const PredCoef c = load_pred(p, k0);
+    const bool real = p.real_coef != 0;  // uniform over the CTA
+    const PredCoef c = real ? load_pred<true>(p, k0) : load_pred<false>(p, k0);
     grid_dependency_wait();
     const int from = J.cur ^ (k & 1);
     const double2 *Phi = J.phi[from], *Pi = J.pi[from];
     const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth), pi1 = ldcg(Pi + k0 + nth);
     if (colok) row[j + 1] = add2(phi0, phi1, ops);
     __syncthreads();
-    HalfStep o = predict_c(c, p.q, ops, phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
+    HalfStep o = real ? predict_c<true>(c, p.q, ops, phi0, pi0, phi1, pi1, row[jj + 2], row[jj])
+                      : predict_c<false>(c, p.q, ops, phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
     const SourceWindow &sw = p.src;
     if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
         const long long n = ldcg(p.step_base) + k;
@@ -666,7 +735,8 @@ __global__ void __launch_bounds__(1024) lw_correct_batch(const JobDesc *__restri
     double2 *row = rows + tyc * W;
     if (slot && j < 2) row[j == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
     const size_t kc = (size_t)iq * nth + jj;
-    const CorrCoef c = load_corr(p, kc);
+    const bool real = p.real_coef != 0;
+    const CorrCoef c = real ? load_corr<true>(p, kc) : load_corr<false>(p, kc);
     grid_dependency_wait();
     const int from = J.cur ^ (k & 1);
     const double2 *Phi = J.phi[from], *Pi = J.pi[from];
@@ -680,7 +750,10 @@ __global__ void __launch_bounds__(1024) lw_correct_batch(const JobDesc *__restri
     if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops);
     __syncthreads();
     double2 nphi, npi;
-    correct_c(c, p.half_dt, ops, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
+    if (real)
+        correct_c<true>(c, p.half_dt, ops, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
+    else
+        correct_c<false>(c, p.half_dt, ops, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
     const long long n = ldcg(p.step_base) + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)

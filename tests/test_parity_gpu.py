@@ -261,6 +261,27 @@ def test_checkpoint_resume_is_bit_identical(teuk):
     np.testing.assert_array_equal(np.concatenate([w1, w2]), w_ref)
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("a,s,m", [(0.0, -2, 2), (0.0, 2, 1), (0.6, 0, 0)])
+def test_real_coefficient_path_equals_complex_path(teuk, kernel, a, s, m):
+    # a = 0 (or s = m = 0): real planes and real-by-complex products give the
+    # same numbers as the complex planes
+    nr, nth = 200, 40
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, a, s, m)
+    u = inputs.random_fields(nr, nth, seed=31)
+    out = []
+    for real in (1, 0):
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, a, s, m, kernel=kernel)
+        g.set_option(teuk.TEUK_OPT_REAL_PATH, real)
+        g.set_initial(*u)
+        g.set_source(**SRC)
+        g.step(150)
+        out.append(g.state())
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        np.testing.assert_array_equal(x, y)
+
+
 def test_runs_are_deterministic(teuk):
     kw = dict(source=SRC, seed=4)
     a = run_pair(teuk, 200, 64, -20.0, 40.0, 0.9, -2, 2, 300, **kw)
