@@ -42,6 +42,12 @@ FLOPS_PER_UPDATE = 100
 BYTES_PER_UPDATE_ALG = 64
 # Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
 FP64_PEAK_FLOPS = 1.25e12
+# The same step as FP64 instructions: adds and multiplies are issued as FMAs,
+# so all 56 occupy the FP64 pipe like an FMA.  Measured issue rate of that
+# pipe on GB300 (FMA-chain probe): 1.906 per clock per SM.
+FP64_INSTR_PER_UPDATE = 56
+FP64_FMA_PER_CLK_SM = 1.906
+NUM_SMS = 152
 # DRAM bytes (read + write) of one time step (predictor + corrector launches) from one
 # ncu capture (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and
 # launch sources whose SHA-256 is recorded here; reported as null otherwise.
@@ -311,6 +317,10 @@ def run_gpu(args):
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
+        # FP64 pipe occupancy at the clock seen during the timed region
+        pipe = NUM_SMS * FP64_FMA_PER_CLK_SM * clocks["sm_mhz"] * 1e6
+        roofline["fp64_instr_per_update"] = FP64_INSTR_PER_UPDATE
+        roofline["fp64_pipe_frac"] = FP64_INSTR_PER_UPDATE * upd_per_launch / per_launch_s / pipe
     if ws == 1 and not args.no_cpu_baseline:
         per = args.cpu_sample_steps
         upd, times = oracle_rate(per, 1)
