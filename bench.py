@@ -440,16 +440,18 @@ def run_serving(args):
     reqs = [request(d) for d in raw]
     upd = sum((r.nr - 2) * r.nth * r.steps for r in reqs)
     budget = int(args.memory_gb * 2 ** 30)
-    # continuous batching
-    svc = S.WaveformService(memory_budget=budget, slice_steps=args.slice)
-    for r in reqs:
-        svc.submit(r)
-    torch.cuda.synchronize()
-    t0 = svc.now()
-    res = svc.run()
-    wall = svc.now() - t0
-    st = S.latency_stats(res)
-    svc.close()
+    # continuous batching, both scheduling policies
+    per_policy = {}
+    for policy in ("fill", "share"):
+        svc = S.WaveformService(memory_budget=budget, slice_steps=args.slice, policy=policy)
+        for r in reqs:
+            svc.submit(r)
+        torch.cuda.synchronize()
+        t0 = svc.now()
+        res = svc.run()
+        per_policy[policy] = (svc.now() - t0, S.latency_stats(res))
+        svc.close()
+    wall, st = per_policy["fill"]
     # one job at a time, arrival order (same kernels, no batching)
     t_start = time.perf_counter()
     lat1, clock = [], 0.0
@@ -474,8 +476,12 @@ def run_serving(args):
                 config=dict(workload="serving", requests=n, rate_per_s=args.rate, slice_steps=args.slice,
                             memory_budget_gb=args.memory_gb, point_updates=upd,
                             grids="2048x64..32768x512", steps="logU[1e3, 1e4]"),
+                policy="fill",
                 latency_s=dict(p50=st["p50"], p99=st["p99"], mean=st["mean"]),
                 grid_pt_updates_per_s=upd / wall,
+                share_policy=dict(value=n / per_policy["share"][0], unit="waveforms/s",
+                                  latency_s=dict(p50=per_policy["share"][1]["p50"], p99=per_policy["share"][1]["p99"],
+                                                 mean=per_policy["share"][1]["mean"])),
                 one_by_one=dict(value=n / wall1, unit="waveforms/s",
                                 latency_s=dict(p50=float(np.percentile(lat1, 50)),
                                                p99=float(np.percentile(lat1, 99)), mean=float(lat1.mean()))))

@@ -231,10 +231,11 @@ int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in,
  * its steps leaves at the next slice boundary.  Full slices replay a CUDA
  * graph captured for the current set of jobs.
  *
- * Rules: a handle in a batch is driven by the batch only; call
+ * Rules: a handle in a batch is driven by the batch only -- teuk_step,
+ * teuk_set_* , teuk_step_noalloc and teuk_destroy on it return
+ * TEUK_ERR_STATE until it is removed (or the batch destroyed); call
  * teuk_batch_sync() before reading a job's results through its handle
- * (teuk_extract, teuk_get_state) and do not destroy a handle before removing
- * it.  Jobs need nth <= 1024.  A batch allocates its job table (and a job's
+ * (teuk_extract, teuk_get_state).  Jobs need nth <= 1024.  A batch allocates its job table (and a job's
  * half-step buffer if the handle has none).
  * ------------------------------------------------------------------------ */
 typedef struct teuk_batch teuk_batch;

@@ -193,6 +193,7 @@ static void choose_launch(teuk_handle *h, int rows_per_block)
 extern "C" int teuk_destroy(teuk_handle *h)
 {
     if (!h) return TEUK_ERR_BAD_ARG;
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_destroy: the handle belongs to a batch (remove it first)");
     if (h->stream || h->own_stream) cudaStreamSynchronize(h->stream);
     destroy_graphs(h);
     if (h->d_src) cudaFree(h->d_src);
@@ -362,6 +363,7 @@ static int finish_initial(teuk_handle *h, bool have_pi)
 extern "C" int teuk_set_initial(teuk_handle *h, const double *phi, const double *pi)
 {
     if (!h || !phi) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_initial: NULL argument");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_initial: the handle belongs to a batch (remove it first)");
     const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
     CU(cudaMemcpyAsync(h->phi[0], phi, bytes, cudaMemcpyHostToDevice, h->stream));
     if (pi) CU(cudaMemcpyAsync(h->pi[0], pi, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -374,6 +376,7 @@ extern "C" int teuk_set_initial(teuk_handle *h, const double *phi, const double 
 extern "C" int teuk_set_state(teuk_handle *h, const double *phi, const double *pi, long step)
 {
     if (!h || !phi || !pi || step < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_state: NULL array or step < 0");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_state: the handle belongs to a batch (remove it first)");
     const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
     CU(cudaMemcpyAsync(h->phi[0], phi, bytes, cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->pi[0], pi, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -390,6 +393,7 @@ extern "C" int teuk_set_state(teuk_handle *h, const double *phi, const double *p
 extern "C" int teuk_set_initial_device(teuk_handle *h, const double *phi, const double *pi)
 {
     if (!h || !phi) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_initial_device: NULL argument");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_initial_device: the handle belongs to a batch (remove it first)");
     const size_t bytes = (size_t)h->nr * h->nth * sizeof(double2);
     CU(cudaMemcpyAsync(h->phi[0], phi, bytes, cudaMemcpyDeviceToDevice, h->stream));
     if (pi) CU(cudaMemcpyAsync(h->pi[0], pi, bytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -399,6 +403,7 @@ extern "C" int teuk_set_initial_device(teuk_handle *h, const double *phi, const 
 extern "C" int teuk_set_source(teuk_handle *h, const teuk_orbit *o)
 {
     if (!h) return TEUK_ERR_BAD_ARG;
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_source: the handle belongs to a batch (remove it first)");
     CU(cudaStreamSynchronize(h->stream));
     destroy_graphs(h);
     if (!o) {
@@ -464,6 +469,7 @@ extern "C" int teuk_set_source(teuk_handle *h, const teuk_orbit *o)
 extern "C" int teuk_set_extraction(teuk_handle *h, double rstar_ext, int every, long capacity)
 {
     if (!h) return TEUK_ERR_BAD_ARG;
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_extraction: the handle belongs to a batch (remove it first)");
     const int i = (int)std::floor((rstar_ext - h->rstar_min) / h->h + 0.5);
     if (!std::isfinite(rstar_ext) || i < 0 || i >= h->nr || every < 1 || capacity < 1)
         return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_extraction: radius outside the grid, every < 1 or capacity < 1");
@@ -525,6 +531,7 @@ static int capture_graph(teuk_handle *h, int from)
 extern "C" int teuk_step(teuk_handle *h, long n)
 {
     if (!h || n < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_step: n < 0");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_step: the handle belongs to a batch (remove it first)");
     while (n >= h->chunk) {
         if (!h->graph[h->variant][h->cur]) {
             int rc = capture_graph(h, h->cur);
@@ -558,6 +565,7 @@ extern "C" int teuk_set_launch(teuk_handle *h, int rows_per_block)
 extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
 {
     if (!h) return TEUK_ERR_BAD_ARG;
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_option: the handle belongs to a batch (remove it first)");
     switch (option) {
     case TEUK_OPT_PDL:
         if (value != 0 && value != 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: PDL is 0 or 1");
@@ -608,6 +616,7 @@ extern "C" long teuk_launches_for(const teuk_handle *h, long n)
 extern "C" int teuk_set_kernel(teuk_handle *h, int variant)
 {
     if (!h || variant < 0 || variant > 2) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: variant 0, 1 or 2");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_kernel: the handle belongs to a batch (remove it first)");
     if ((variant == 0 && h->nth > kFusedMaxNth) || (variant == 2 && h->nth > 1024))
         return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: fused kernel needs nth <= 512, split nth <= 1024");
     if (variant != 0 && !h->phiH) {
@@ -650,6 +659,7 @@ extern "C" int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const dou
 {
     if (!h || !phi_in || !pi_in || !phi_out || !pi_out || step_index < 0)
         return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: NULL buffer or negative step index");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_step_noalloc: the handle belongs to a batch (remove it first)");
     if (h->nth > 1024)
         return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: needs nth <= 1024");
     const long long mids = (long long)(h->nr - 1) * h->nth;

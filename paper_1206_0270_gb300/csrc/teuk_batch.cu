@@ -98,6 +98,8 @@ extern "C" int teuk_batch_destroy(teuk_batch *b)
 {
     if (!b) return TEUK_ERR_BAD_ARG;
     cudaStreamSynchronize(b->stream);
+    for (auto &j : b->jobs)
+        if (j.member) j.h->in_batch = 0;  // the handles are driven by their owner again
     drop_graph(b);
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_off) cudaFree(b->d_off);
@@ -115,6 +117,7 @@ extern "C" int teuk_batch_add(teuk_batch *b, teuk_handle *h, long steps, int *jo
     if (h->nth > 1024) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: batched tiles need nth <= 1024");
     for (const auto &j : b->jobs)
         if (j.member && j.h == h) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: handle already in the batch");
+    if (h->in_batch) return bfail(b, TEUK_ERR_STATE, "teuk_batch_add: handle belongs to another batch");
     BCU(cudaStreamSynchronize(h->stream));  // the handle's own queued work comes first
     if (!h->phiH) {
         const size_t Nm = (size_t)(h->nr - 1) * h->nth;
@@ -129,6 +132,7 @@ extern "C" int teuk_batch_add(teuk_batch *b, teuk_handle *h, long steps, int *jo
     j.remaining = steps;
     j.member = true;
     b->jobs.push_back(j);
+    h->in_batch = 1;
     *job_id = (int)b->jobs.size() - 1;
     b->layout_dirty = true;
     return TEUK_OK;
@@ -141,6 +145,7 @@ extern "C" int teuk_batch_remove(teuk_batch *b, int job_id)
     BCU(cudaStreamSynchronize(b->stream));
     b->jobs[job_id].member = false;
     b->jobs[job_id].remaining = 0;
+    b->jobs[job_id].h->in_batch = 0;
     b->layout_dirty = true;
     return TEUK_OK;
 }

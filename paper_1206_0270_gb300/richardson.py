@@ -124,6 +124,6 @@ def run_ladder(levels, a, s, m, rstar_min, rstar_max, rstar_ext, init=None, sour
         B.sync()
         return [g.extract() for g in solvers]
     finally:
-        B.close()
+        B.close()                   # release the handles before destroying them
         for g in solvers:
             g.close()

@@ -73,12 +73,24 @@ class Result:
 
 
 class WaveformService:
-    """Continuous batching over teuk_batch with admission by device memory."""
+    """Continuous batching over teuk_batch with admission by device memory.
+
+    policy="share": every admitted job advances in every slice (processor
+    sharing: short jobs finish early, long ones stretch).
+    policy="fill": each slice runs admitted jobs in arrival order until they
+    hold `fill_points` grid points (enough to keep the FP64 pipe busy); the
+    others stay resident but paused, so the oldest jobs run at nearly full
+    speed and small jobs still share launches."""
 
     def __init__(self, memory_budget: int, slice_steps: int = 640, max_jobs: int = 4096,
-                 stream=None, clock: Callable[[], float] = time.perf_counter):
+                 stream=None, clock: Callable[[], float] = time.perf_counter, policy: str = "fill",
+                 fill_points: int = 2_000_000):
         if slice_steps < 2 or slice_steps % 2:
             raise ValueError("slice_steps must be even and >= 2")
+        if policy not in ("share", "fill"):
+            raise ValueError("policy is 'share' or 'fill'")
+        self.policy = policy
+        self.fill_points = int(fill_points)
         self.budget = int(memory_budget)
         self.slice = int(slice_steps)
         self.max_jobs = int(max_jobs)
@@ -143,25 +155,54 @@ class WaveformService:
             g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, self._dt(r), r.a, r.s, r.m)
             g.set_source(r0=r.r0, sigma=r.sigma)
             g.set_extraction(r.rstar_ext, r.every, capacity=self.slice // r.every + 2)
-            job = self.batch.add(g, r.steps)
             self._used += need
-            self._running[rid] = dict(solver=g, job=job, admitted=self.now(), t=[], phi=[], need=need)
+            self._running[rid] = dict(solver=g, job=None, remaining=r.steps, admitted=self.now(), t=[], phi=[],
+                                      need=need)
+
+    def _schedule(self):
+        """Choose the jobs that advance in the next slice and make the batch
+        hold exactly them (paused jobs keep their state on the device)."""
+        order = sorted(self._running, key=lambda rid: (self._submitted[rid], rid))
+        want, pts = set(), 0
+        for rid in order:
+            st = self._running[rid]
+            if st["remaining"] == 0:
+                continue
+            if self.policy == "fill" and want and pts >= self.fill_points:
+                break
+            want.add(rid)
+            r = self._requests[rid]
+            pts += r.nr * r.nth
+        for rid in order:
+            st = self._running[rid]
+            if st["job"] is not None and rid not in want:
+                st["remaining"] = self.batch.remaining(st["job"])
+                self.batch.remove(st["job"])
+                st["job"] = None
+            elif st["job"] is None and rid in want:
+                st["job"] = self.batch.add(st["solver"], st["remaining"])
 
     def _drain(self):
         """Stream every running job's new samples; retire finished jobs."""
         self.batch.sync()
         done = []
         for rid, st in self._running.items():
+            if st["job"] is None:
+                if st["remaining"] == 0:
+                    done.append(rid)          # nothing to step (steps = 0)
+                continue
             t, w = st["solver"].extract(cap=self.slice // self._requests[rid].every + 2)
             if len(t):
                 st["t"].append(t)
                 st["phi"].append(w)
-            if self.batch.remaining(st["job"]) == 0:
+            st["remaining"] = self.batch.remaining(st["job"])
+            if st["remaining"] == 0:
                 done.append(rid)
         fin = self.now()
         for rid in done:
             st = self._running.pop(rid)
-            self.batch.remove(st["job"])
+            if st["job"] is not None:
+                self.batch.remove(st["job"])
             st["solver"].close()
             self._used -= st["need"]
             r = self._requests[rid]
@@ -177,6 +218,7 @@ class WaveformService:
         Returns False when nothing is queued or running."""
         had_jobs = bool(self._running)
         if had_jobs:
+            self._schedule()
             self.batch.step(self.slice)
             self.slices += 1
         self._admit()
@@ -198,10 +240,10 @@ class WaveformService:
         return self.results
 
     def close(self):
+        self.batch.close()          # releases the handles, which are then destroyed
         for st in self._running.values():
             st["solver"].close()
         self._running.clear()
-        self.batch.close()
 
 
 def latency_stats(results) -> dict:

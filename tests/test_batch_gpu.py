@@ -146,6 +146,15 @@ def test_batch_bad_arguments(teuk):
         B.add(h, 10)              # twice
     with pytest.raises(teuk.TeukError):
         B.remove(7)
+    # a handle in a batch is driven by the batch only
+    for call in (lambda: h.step(1), lambda: h.set_source(r0=8.0, sigma=1.0),
+                 lambda: h.set_extraction(0.0, 2)):
+        with pytest.raises(teuk.TeukError) as e:
+            call()
+        assert e.value.code == -5
+    assert teuk.teuk_destroy(h.h) == -5
+    B.remove(0)
+    h.step(1)                    # usable again after removal
     with pytest.raises(teuk.TeukError):
         B.set_option(teuk.TEUK_OPT_BLOCK_THREADS, 100)
     assert B.step(0) == 0

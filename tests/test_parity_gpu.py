@@ -364,3 +364,66 @@ def test_nonfinite_state_is_reported(teuk):
     phi[5, 3] = np.nan
     g.set_initial(phi, np.zeros_like(phi))
     assert not g.check_finite()
+
+
+def _load_full_fixture():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "kerr_a0.9_8192x128_1e5.txt")
+    dt, W, S = None, [], []
+    for line in open(path):
+        if line.startswith("# dt"):
+            dt = float(line.split()[2])
+        elif line.startswith("W "):
+            W.append([float(x) for x in line.split()[1:]])
+        elif line.startswith("S "):
+            S.append([float(x) for x in line.split()[1:]])
+    W, S = np.array(W), np.array(S)
+    return dt, W[:, 0], W[:, 1] + 1j * W[:, 2], S
+
+
+def test_parity_kerr_8192x128_full_length_against_stored_oracle_run(teuk):
+    # The whole Kerr workload (1e5 steps) in the benchmark's launch
+    # configuration against the oracle's run of it, stored by
+    # tests/golden/make_kerr_full_fixture.py: the waveform at r* = 20 projected
+    # on -2Y_22 every 100 steps and the final state on four rows.
+    dt, t_ref, w_ref, rows = _load_full_fixture()
+    w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
+    g = teuk.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+    g.set_initial(np.zeros((w["nr"], w["nth"]), complex), np.zeros((w["nr"], w["nth"]), complex))
+    g.set_source(**w["source"])
+    g.set_extraction(20.0, 100, capacity=1100)
+    g.step(w["steps"])
+    t, ext = g.extract()
+    phi, pi = g.state()
+    th = inputs.theta_grid(w["nth"])
+    y = 2 * np.pi * np.sqrt(5 / (64 * np.pi)) * (1 + np.cos(th)) ** 2 * np.sin(th) * (np.pi / w["nth"])
+    np.testing.assert_array_equal(t, t_ref)
+    assert rel(ext @ y, w_ref) <= TOL
+    for i in np.unique(rows[:, 0]).astype(int):
+        sel = rows[:, 0] == i
+        j = rows[sel, 1].astype(int)
+        p_ref = rows[sel, 2] + 1j * rows[sel, 3]
+        q_ref = rows[sel, 4] + 1j * rows[sel, 5]
+        assert rel(phi[i, j], p_ref) <= TOL
+        assert rel(pi[i, j], q_ref) <= TOL
+
+
+def test_full_length_kerr_8192x128_linearity_and_determinism(teuk):
+    # Properties that hold at any length: two runs are bit-identical, and
+    # doubling the source amplitude doubles every value exactly.
+    w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
+    dt = O.stable_dt(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], w["c_r"],
+                     w["c_theta"])
+    out = []
+    for amp in (1.0, 1.0, 2.0):
+        g = teuk.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+        g.set_initial(np.zeros((w["nr"], w["nth"]), complex), np.zeros((w["nr"], w["nth"]), complex))
+        g.set_source(**{**w["source"], "amplitude": amp})
+        g.step(w["steps"])
+        assert g.check_finite()
+        out.append(g.state())
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        np.testing.assert_array_equal(x, y)
+    for x, y in zip(out[0], out[2]):
+        np.testing.assert_array_equal(2 * x, y)

@@ -37,13 +37,14 @@ def run_alone(S, r):
     return res[rid]
 
 
-def test_results_same_alone_and_in_the_mix(serve):
+@pytest.mark.parametrize("policy,fill", [("share", 0), ("fill", 60000), ("fill", 1)])
+def test_results_same_alone_and_in_the_mix(serve, policy, fill):
     S = serve
-    rs = reqs(S)
+    rs = reqs(S) + [S.Request(a=0.2, s=-2, m=2, nr=100, nth=8, steps=0, sigma=3.0, rstar_ext=10.0)]
     alone = [run_alone(S, r) for r in rs]
     # the mix: a budget that fits about two jobs at a time, staggered arrivals
     budget = 2 * S.footprint_bytes(rs[2], 64)
-    svc = S.WaveformService(memory_budget=budget, slice_steps=64)
+    svc = S.WaveformService(memory_budget=budget, slice_steps=64, policy=policy, fill_points=fill)
     ids = []
     for k, r in enumerate(rs):
         r2 = S.Request(**{**r.__dict__, "arrival": 0.002 * k})
