@@ -399,13 +399,13 @@ def test_parity_kerr_8192x128_full_length_against_stored_oracle_run(teuk):
     y = 2 * np.pi * np.sqrt(5 / (64 * np.pi)) * (1 + np.cos(th)) ** 2 * np.sin(th) * (np.pi / w["nth"])
     np.testing.assert_array_equal(t, t_ref)
     assert rel(ext @ y, w_ref) <= TOL
-    for i in np.unique(rows[:, 0]).astype(int):
-        sel = rows[:, 0] == i
-        j = rows[sel, 1].astype(int)
-        p_ref = rows[sel, 2] + 1j * rows[sel, 3]
-        q_ref = rows[sel, 4] + 1j * rows[sel, 5]
-        assert rel(phi[i, j], p_ref) <= TOL
-        assert rel(pi[i, j], q_ref) <= TOL
+    i, j = rows[:, 0].astype(int), rows[:, 1].astype(int)
+    p_ref = rows[:, 2] + 1j * rows[:, 3]
+    q_ref = rows[:, 4] + 1j * rows[:, 5]
+    # one scale over the stored rows (the rows beyond the wave front are still exactly zero)
+    assert rel(phi[i, j], p_ref) <= TOL
+    assert rel(pi[i, j], q_ref) <= TOL
+    assert abs(p_ref).max() > 0
 
 
 def test_full_length_kerr_8192x128_linearity_and_determinism(teuk):
