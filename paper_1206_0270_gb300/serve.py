@@ -15,6 +15,7 @@ this module only schedules.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import dataclasses
 import heapq
 import time
@@ -107,6 +108,9 @@ class WaveformService:
         self._next = 0
         self.results: dict = {}
         self._dt_cache: dict = {}
+        # time steps are prepared on host threads while the GPU runs slices
+        # (teuk_stable_dt scans the whole grid; the ctypes call releases the GIL)
+        self._pool = cf.ThreadPoolExecutor(max_workers=4)
         self.slices = 0
 
     # -- clock -------------------------------------------------------------
@@ -121,6 +125,7 @@ class WaveformService:
         self._next += 1
         self._requests[rid] = req
         self._submitted[rid] = max(req.arrival, 0.0)
+        self._dt_future(req)
         heapq.heappush(self._queue, (req.arrival, rid))
         return rid
 
@@ -133,14 +138,17 @@ class WaveformService:
     def memory_in_use(self) -> int:
         return self._used
 
+    def _dt_future(self, r: Request):
+        key = (r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m, r.c_r, r.c_theta)
+        if r.dt is None and key not in self._dt_cache:
+            self._dt_cache[key] = self._pool.submit(T.stable_dt, r.nr, r.nth, r.rstar_min, r.rstar_max,
+                                                    r.a, r.s, r.m, r.c_r, r.c_theta)
+        return key
+
     def _dt(self, r: Request) -> float:
         if r.dt is not None:
             return float(r.dt)
-        key = (r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m, r.c_r, r.c_theta)
-        if key not in self._dt_cache:
-            self._dt_cache[key] = T.stable_dt(r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m,
-                                              r.c_r, r.c_theta)
-        return self._dt_cache[key]
+        return self._dt_cache[self._dt_future(r)].result()
 
     def _admit(self):
         now = self.now()
@@ -150,6 +158,8 @@ class WaveformService:
             need = footprint_bytes(r, self.slice)
             if self._used + need > self.budget:
                 break                      # first-come first-served: wait for memory to free up
+            if r.dt is None and not self._dt_cache[self._dt_future(r)].done() and self._running:
+                break                      # its time step is still being prepared; others keep running
             heapq.heappop(self._queue)
             # each handle sets up on its own stream, concurrently with the running slice
             g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, self._dt(r), r.a, r.s, r.m)
@@ -240,6 +250,7 @@ class WaveformService:
         return self.results
 
     def close(self):
+        self._pool.shutdown(wait=True)
         self.batch.close()          # releases the handles, which are then destroyed
         for st in self._running.values():
             st["solver"].close()
