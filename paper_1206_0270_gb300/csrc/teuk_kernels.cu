@@ -520,8 +520,15 @@ int split_rows_per_block(int nth)
     return cols >= 256 ? 1 : 256 / cols;
 }
 
+#ifndef TEUK_SPLIT_THREADS
+#define TEUK_SPLIT_THREADS 1024
+#endif
+#ifndef TEUK_SPLIT_MINB
+#define TEUK_SPLIT_MINB 1
+#endif
+
 template <bool REAL>
-__global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
+__global__ void __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB) lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
                                                          const double2 *__restrict__ Pi,
                                                          double2 *__restrict__ PhiH,
                                                          double2 *__restrict__ PiH, int k)
@@ -556,7 +563,7 @@ __global__ void __launch_bounds__(1024) lw_predict_split(StepParams p, const dou
 }
 
 template <bool REAL>
-__global__ void __launch_bounds__(1024) lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
+__global__ void __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB) lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
                                                          const double2 *__restrict__ Pi,
                                                          const double2 *__restrict__ PhiH,
                                                          const double2 *__restrict__ PiH,
