@@ -36,8 +36,12 @@ WORKLOAD = "kerr_a0.9_s-2_m2_8192x128_r0_10"
 METRIC = "FP64 grid-pt updates/s"
 UNIT = "grid-pt updates/s"
 # FP64 work of one interior point update in the folded formulation of
-# Eqs. (3)-(4): 8 adds + 4 multiplies + 44 FMAs = 56 FP64 instructions = 100 flops.
+# Eqs. (3)-(4): 8 adds + 4 multiplies + 44 FMAs = 56 FP64 instructions = 100 flops;
+# per kernel: predictor (one mid-point) 4 adds + 4 multiplies + 20 FMAs = 48 flops,
+# corrector (one node) 4 adds + 24 FMAs = 52 flops.
 FLOPS_PER_UPDATE = 100
+FLOPS_PREDICTOR_POINT = 48
+FLOPS_CORRECTOR_POINT = 52
 # Algorithmic HBM bytes of one point update: read u^n, write u^{n+1} (4 doubles each).
 BYTES_PER_UPDATE_ALG = 64
 # Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
@@ -48,10 +52,10 @@ FP64_PEAK_FLOPS = 1.25e12
 FP64_INSTR_PER_UPDATE = 56
 FP64_FMA_PER_CLK_SM = 1.906
 NUM_SMS = 152
-# DRAM bytes (read + write) of one time step (predictor + corrector launches) from one
-# ncu capture (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and
-# launch sources whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(bytes_per_step=310.75e6,
+# DRAM bytes (read + write) per launch of each step kernel from one ncu capture
+# (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
+# sources whose SHA-256 is recorded here; reported as null otherwise.
+NCU_TRAFFIC = dict(predictor=125.85e6 + 14.82e6, corrector=151.02e6 + 19.06e6,
                    sources_sha256="8502b4c99c8be5c35d4ce2370b17f8f8f0be4c1b5c9dbb4ca9486d5005053fd4")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu", "paper_1206_0270_gb300/csrc/teuk_internal.h",
                    "paper_1206_0270_gb300/csrc/teuk_api.cu"]  # kernels, their layout, their launch
@@ -257,15 +261,26 @@ def run_gpu(args):
     launches = args.steps * S.launches_for(args.chunk)
     value = whole_job_rate(ws, upd_per_step * args.steps, total_ms / 1e3)
 
-    # ---- dominant kernel: average launch duration over the timed region --------------
-    per_launch_s = (total_ms / 1e3) / (args.steps * args.chunk)
+    # ---- per-kernel roofline ------------------------------------------------------------
+    # The time step is two kernels of nearly equal cost; each is timed live with
+    # CUDA events on the solver's stream (teuk_time_kernels, plain launches) and
+    # the longer one is reported as the dominant kernel.
+    per_launch_s = (total_ms / 1e3) / (args.steps * args.chunk)     # one step, inside the graph replay
     upd_per_launch = (nr - 2) * nth
-    achieved = FLOPS_PER_UPDATE * upd_per_launch / per_launch_s
-    traffic = NCU_TRAFFIC["bytes_per_step"] if NCU_TRAFFIC["sources_sha256"] == sources_sha256() else None
+    ms_pred, ms_corr = S.time_kernels(args.kernel_timing_steps)
+    kern = dict(lw_predict_split=(FLOPS_PREDICTOR_POINT * (nr - 1) * nth, ms_pred, "predictor"),
+                lw_correct_split=(FLOPS_CORRECTOR_POINT * (nr - 2) * nth, ms_corr, "corrector"))
+    dom = max(kern, key=lambda k: kern[k][1])
+    flops, ms, key = kern[dom]
+    achieved = flops / (ms / 1e3)
+    same_src = NCU_TRAFFIC["sources_sha256"] == sources_sha256()
     roofline = dict(bound="alu", achieved=achieved / 1e12, peak=FP64_PEAK_FLOPS / 1e12, unit="TFLOP/s",
-                    frac=achieved / FP64_PEAK_FLOPS, traffic=traffic,
-                    unit_of_launch="one time step: lw_predict_split + lw_correct_split",
+                    frac=achieved / FP64_PEAK_FLOPS, traffic=NCU_TRAFFIC[key] if same_src else None,
+                    kernel=dom, launch_ms=ms,
                     peak_source="nominal FP64 (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz)",
+                    kernels={k: dict(ms=v[1], tflops=v[0] / (v[1] / 1e3) / 1e12) for k, v in kern.items()},
+                    step_in_graph=dict(ms=per_launch_s * 1e3,
+                                       tflops=FLOPS_PER_UPDATE * upd_per_launch / per_launch_s / 1e12),
                     hbm_alg_gbs=BYTES_PER_UPDATE_ALG * upd_per_launch / per_launch_s / 1e9)
 
     # ---- end to end through the C ABI with host buffers ------------------------------
@@ -498,6 +513,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ref-steps", type=int, default=10, help="oracle time steps per reference step")
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
+    ap.add_argument("--kernel-timing-steps", type=int, default=64,
+                    help="steps timed kernel by kernel (after the timed region) for the roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batch_modes", "template_bank", "serving"],

@@ -186,6 +186,13 @@ int teuk_set_option(teuk_handle *h, int option, long value);
 /* Current fused-kernel launch shape. */
 int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *nblocks);
 
+/* Time the step kernels: advance n >= 1 steps with plain (non-graph,
+ * non-PDL) launches and CUDA events on the handle's stream around each
+ * kernel; ms_out[0] and ms_out[1] receive the average duration of the
+ * predictor and the corrector kernel (two-kernel variants), or of the fused
+ * step kernel and 0.  The steps count as progress.  Synchronises. */
+int teuk_time_kernels(teuk_handle *h, long n, double *ms_out);
+
 /* Number of kernel launches one teuk_step(h, n) issues for this handle's
  * configuration (graph replays count their kernel nodes). */
 long teuk_launches_for(const teuk_handle *h, long n);

@@ -605,6 +605,58 @@ extern "C" int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *n
     return TEUK_OK;
 }
 
+extern "C" int teuk_time_kernels(teuk_handle *h, long n, double *ms_out)
+{
+    if (!h || n < 1 || !ms_out) return fail(h, TEUK_ERR_BAD_ARG, "teuk_time_kernels: n >= 1 and ms_out needed");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_time_kernels: the handle belongs to a batch (remove it first)");
+    cudaEvent_t ev[3];
+    for (auto &e : ev) CU(cudaEventCreate(&e));
+    double acc[2] = {0.0, 0.0};
+    int rc = TEUK_OK;
+    for (long k = 0; k < n && rc == TEUK_OK; ++k) {
+        const int from = h->cur;
+        cudaError_t e = cudaEventRecord(ev[0], h->stream);
+        if (h->variant == 0) {
+            if (e == cudaSuccess)
+                e = launch_step_fused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], (int)k,
+                                      h->rows_per_block, h->nblocks, h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+        } else {
+            for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+                e = h->variant == 2 ? launch_step_split(h->sp, h->phi[from], h->pi[from], h->phi[1 - from],
+                                                        h->pi[1 - from], h->phiH, h->piH, (int)k, h->stream, false,
+                                                        part)
+                                    : launch_step_unfused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from],
+                                                          h->pi[1 - from], h->phiH, h->piH, (int)k, h->stream,
+                                                          part);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[1 + part], h->stream);
+            }
+        }
+        float t01 = 0, t12 = 0;
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t01, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t12, ev[1], ev[2]);
+        if (e != cudaSuccess) {
+            rc = fail(h, TEUK_ERR_CUDA, std::string("teuk_time_kernels: ") + cudaGetErrorString(e));
+            break;
+        }
+        acc[0] += t01;
+        acc[1] += t12;
+        h->cur = 1 - from;
+    }
+    if (rc == TEUK_OK) {
+        cudaError_t e = launch_advance(h->d_step, n, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = fail(h, TEUK_ERR_CUDA, std::string("teuk_time_kernels: ") + cudaGetErrorString(e));
+        h->nstep += n;
+        ms_out[0] = acc[0] / n;
+        ms_out[1] = acc[1] / n;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
 extern "C" long teuk_launches_for(const teuk_handle *h, long n)
 {
     if (!h || n < 0) return -1;

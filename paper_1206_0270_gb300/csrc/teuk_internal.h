@@ -117,12 +117,14 @@ cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const dou
                               double2 *PhiO, double2 *PiO, int k, int rows_per_block,
                               int nblocks, cudaStream_t st);
 
+// part: 0 = predictor kernel only, 1 = corrector kernel only, 2 = both
 cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const double2 *Pi,
                                 double2 *PhiO, double2 *PiO, double2 *PhiH, double2 *PiH, int k,
-                                cudaStream_t st);
+                                cudaStream_t st, int part = 2);
 
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
-                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl);
+                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl,
+                              int part = 2);
 
 cudaError_t launch_advance(long long *step_base, long long by, cudaStream_t st);
 

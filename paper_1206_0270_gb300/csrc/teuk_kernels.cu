@@ -492,17 +492,18 @@ __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
 
 cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const double2 *Pi,
                                 double2 *PhiO, double2 *PiO, double2 *PhiH, double2 *PiH, int k,
-                                cudaStream_t st)
+                                cudaStream_t st, int part)
 {
     const int threads = 256;
     const long long np = (long long)(p.nr - 1) * p.nth, nc = (long long)(p.nr - 2) * p.nth;
-    if (p.real_coef) {
-        lw_predict_kernel<true><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
-        lw_correct_kernel<true><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
+    if (part != 1) {
+        if (p.real_coef) lw_predict_kernel<true><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
+        else lw_predict_kernel<false><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
+    }
+    if (part != 0) {
+        if (p.real_coef) lw_correct_kernel<true><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
                                                                                   PhiO, PiO, k);
-    } else {
-        lw_predict_kernel<false><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
-        lw_correct_kernel<false><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
+        else lw_correct_kernel<false><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
                                                                                   PhiO, PiO, k);
     }
     return cudaGetLastError();
@@ -616,8 +617,10 @@ const void *split_kernel_ptr(int which, int real)
     return which ? (const void *)lw_correct_split<false> : (const void *)lw_predict_split<false>;
 }
 
+// part: 0 = predictor only, 1 = corrector only, 2 = both.
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
-                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl)
+                              double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl,
+                              int part)
 {
     const int R = split_rows_per_block(p.nth);
     cudaLaunchAttribute attr[1];
@@ -629,16 +632,21 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     cfg.stream = st;
     cfg.attrs = pdl ? attr : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;
-    cfg.gridDim = dim3((p.nr - 1 + R - 1) / R);
-    cudaError_t e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_predict_split<true>, p, Phi, Pi, PhiH, PiH, k)
-                                : cudaLaunchKernelEx(&cfg, lw_predict_split<false>, p, Phi, Pi, PhiH, PiH, k);
-    if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3((p.nr - 2 + R - 1) / R);
-    e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_correct_split<true>, p, Phi, Pi, (const double2 *)PhiH,
-                                         (const double2 *)PiH, PhiO, PiO, k)
-                    : cudaLaunchKernelEx(&cfg, lw_correct_split<false>, p, Phi, Pi, (const double2 *)PhiH,
-                                         (const double2 *)PiH, PhiO, PiO, k);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (part != 1) {
+        cfg.gridDim = dim3((p.nr - 1 + R - 1) / R);
+        e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_predict_split<true>, p, Phi, Pi, PhiH, PiH, k)
+                        : cudaLaunchKernelEx(&cfg, lw_predict_split<false>, p, Phi, Pi, PhiH, PiH, k);
+        if (e != cudaSuccess) return e;
+    }
+    if (part != 0) {
+        cfg.gridDim = dim3((p.nr - 2 + R - 1) / R);
+        e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_correct_split<true>, p, Phi, Pi, (const double2 *)PhiH,
+                                             (const double2 *)PiH, PhiO, PiO, k)
+                        : cudaLaunchKernelEx(&cfg, lw_correct_split<false>, p, Phi, Pi, (const double2 *)PhiH,
+                                             (const double2 *)PiH, PhiO, PiO, k);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

@@ -69,6 +69,7 @@ _SIGS = {
     "teuk_get_launch": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "teuk_step_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_long]),
     "teuk_set_option": (C.c_int, [_vp, C.c_int, C.c_long]),
+    "teuk_time_kernels": (C.c_int, [_vp, C.c_long, _dp]),
     "teuk_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
     "teuk_batch_add": (C.c_int, [_vp, _vp, C.c_long, C.POINTER(C.c_int)]),
     "teuk_batch_remove": (C.c_int, [_vp, C.c_int]),
@@ -232,6 +233,11 @@ class Solver:
 
     def launches_for(self, n):
         return teuk_launches_for(self.h, int(n))
+
+    def time_kernels(self, n):
+        out = np.zeros(2)
+        _check(teuk_time_kernels(self.h, int(n), _ptr(out)), self.h, "teuk_time_kernels")
+        return float(out[0]), float(out[1])
 
 
 def _bcheck(rc, b, what):

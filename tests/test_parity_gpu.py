@@ -282,6 +282,30 @@ def test_real_coefficient_path_equals_complex_path(teuk, kernel, a, s, m):
         np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_kernel_timing_steps_like_teuk_step(teuk, kernel):
+    nr, nth = 300, 64
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, 0.9, -2, 2)
+    u = inputs.random_fields(nr, nth, seed=5)
+    out = []
+    for timed in (False, True):
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2, kernel=kernel)
+        g.set_initial(*u)
+        g.set_source(**SRC)
+        g.step(3)
+        if timed:
+            ms = g.time_kernels(10)
+            assert ms[0] > 0 and (ms[1] > 0) == (kernel != 0)
+        else:
+            g.step(10)
+        g.step(5)
+        assert g.step_count == 18
+        out.append(g.state())
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        np.testing.assert_array_equal(x, y)
+
+
 def test_runs_are_deterministic(teuk):
     kw = dict(source=SRC, seed=4)
     a = run_pair(teuk, 200, 64, -20.0, 40.0, 0.9, -2, 2, 300, **kw)
