@@ -521,15 +521,22 @@ int split_rows_per_block(int nth)
     return cols >= 256 ? 1 : 256 / cols;
 }
 
+// Launch bounds of the split kernels.  The single-argument form leaves ptxas
+// free to pick the register count (48 / 52 for the complex kernels, so five
+// 256-thread tiles fit on an SM); an explicit minimum of one block per SM
+// makes it use up to 64 and costs a resident tile.  TEUK_SPLIT_MINB, when
+// defined, selects the two-argument form for register-budget experiments.
 #ifndef TEUK_SPLIT_THREADS
 #define TEUK_SPLIT_THREADS 1024
 #endif
-#ifndef TEUK_SPLIT_MINB
-#define TEUK_SPLIT_MINB 1
+#ifdef TEUK_SPLIT_MINB
+#define TEUK_SPLIT_BOUNDS __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB)
+#else
+#define TEUK_SPLIT_BOUNDS __launch_bounds__(TEUK_SPLIT_THREADS)
 #endif
 
 template <bool REAL>
-__global__ void __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB) lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
+__global__ void TEUK_SPLIT_BOUNDS lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
                                                          const double2 *__restrict__ Pi,
                                                          double2 *__restrict__ PhiH,
                                                          double2 *__restrict__ PiH, int k)
@@ -564,7 +571,7 @@ __global__ void __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB) lw_predic
 }
 
 template <bool REAL>
-__global__ void __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB) lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
+__global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
                                                          const double2 *__restrict__ Pi,
                                                          const double2 *__restrict__ PhiH,
                                                          const double2 *__restrict__ PiH,

@@ -168,6 +168,62 @@ def test_angular_operator_exact_on_quadratics(nth):
     assert np.all(out == 0)
 
 
+def _angular_part(S, r, s, m, nth):
+    """kappa L_theta S - W S on the theta grid at radius r (a = 0): the theta
+    derivatives of the Pi row of S in Eq. (1), discretised as the oracle does."""
+    from paper_1206_0270_gb300 import richardson  # noqa: F401  (host numpy only)
+    th = inputs.theta_grid(nth)
+    D = r * r - 2.0 * r
+    co = [O.coefficients(r, D, t, 0.0, s, m) for t in th]
+    kap = np.array([c["kappa"] for c in co])
+    W = np.array([c["W"] for c in co])
+    parity = 1 if m % 2 == 0 else -1
+    return kap * O.angular_op(S + 0j, parity) - W * S, kap
+
+
+@pytest.mark.parametrize("s,m", [(-2, 2), (-2, 1), (-2, 0), (0, 3), (2, 2), (2, 1)])
+def test_spin_weighted_harmonics_are_discrete_eigenfunctions(s, m):
+    """At a = 0 the angular terms of Eq. (1) (kappa L_theta and the theta part
+    of W, with the pole ghosts) form the spin-weighted spherical-harmonic
+    operator, whose eigenfunctions are sY_lm with eigenvalue
+    -(l - s)(l + s + 1) (Goldberg et al. 1967).  On the oracle's grid:
+      * sY_lm is an eigenfunction up to O(dtheta^2) in the sin(theta)-weighted
+        L2 norm (the natural norm on the sphere; next to a pole, odd-m rows
+        carry an O(dtheta) error on one cell, which that norm weights by
+        sin(theta_0) ~ dtheta);
+      * the Rayleigh quotients of two l's differ by -kappa [l2(l2+1) - l1(l1+1)]
+        (the theta-independent part of W cancels), kappa = Delta / r^4.
+    Catches a wrong sign or index in the angular stencil, the cot term, the
+    (m + s cos theta)^2 / sin^2 theta term or the ghost parity."""
+    from paper_1206_0270_gb300.richardson import swsh_theta
+    r = 12.0
+    kappa_exact = (r * r - 2.0 * r) / r ** 4
+    l1 = max(2, abs(m), abs(s))
+    l2 = l1 + 1
+    res, gap = [], []
+    for nth in (64, 128, 256):
+        th = inputs.theta_grid(nth)
+        w = np.sin(th)
+        lam = {}
+        for l in (l1, l2):
+            S = swsh_theta(s, l, m, th)
+            op, kap = _angular_part(S, r, s, m, nth)
+            np.testing.assert_allclose(kap, kappa_exact, rtol=1e-13)
+            lam[l] = np.sum(w * S * op) / np.sum(w * S * S)
+            e = op - lam[l] * S
+            res.append((l, nth, np.sqrt(np.sum(w * np.abs(e) ** 2) / np.sum(w * (kappa_exact * S) ** 2))))
+        want = -kappa_exact * (l2 * (l2 + 1) - l1 * (l1 + 1))
+        gap.append(abs((lam[l2] - lam[l1]) - want) / abs(want))
+    for l in (l1, l2):
+        errs = [e for (ll, _n, e) in res if ll == l]
+        assert errs[-1] < 2e-3, errs
+        for a_, b_ in zip(errs, errs[1:]):
+            assert math.log2(a_ / b_) > 1.8, errs
+    assert gap[-1] < 1e-3, gap
+    for a_, b_ in zip(gap, gap[1:]):
+        assert math.log2(a_ / b_) > 1.8, gap
+
+
 # ---------------------------------------------------------------------------
 # Eqs. (3)-(4): exact amplification matrix for constant coefficients
 # ---------------------------------------------------------------------------
