@@ -181,6 +181,10 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  * s = m = 0: 44 instead of 56 FP64 instructions per point); 0 keeps the
  * complex planes.  Both give the same numbers. */
 #define TEUK_OPT_REAL_PATH 4
+/* TEUK_OPT_SPLIT_ROWS: r* rows per CTA tile of the split kernels, 1..1024 /
+ * (nth rounded up to a multiple of 32); 0 (default) picks 256 / that width,
+ * at least 1.  A tile is one thread per point. */
+#define TEUK_OPT_SPLIT_ROWS 5
 int teuk_set_option(teuk_handle *h, int option, long value);
 
 /* Current fused-kernel launch shape. */

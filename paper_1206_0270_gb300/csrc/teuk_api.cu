@@ -501,7 +501,7 @@ static cudaError_t launch_one(teuk_handle *h, int from, int k, cudaStream_t st)
                                  h->rows_per_block, h->nblocks, st);
     if (h->variant == 2)
         return launch_step_split(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], h->phiH,
-                                 h->piH, k, st, h->pdl != 0);
+                                 h->piH, k, st, h->pdl != 0, 2, h->split_rows);
     return launch_step_unfused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from], h->pi[1 - from], h->phiH,
                                h->piH, k, st);
 }
@@ -580,6 +580,13 @@ extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
         destroy_graphs(h);
         h->chunk = (int)value;
         return TEUK_OK;
+    case TEUK_OPT_SPLIT_ROWS:
+        if (value < 0 || value * fused_block_threads(h->nth) > 1024)
+            return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: split rows must be 0 or 1..1024 / (nth rounded up to warps)");
+        CU(cudaStreamSynchronize(h->stream));
+        destroy_graphs(h);
+        h->split_rows = (int)value;
+        return TEUK_OK;
     case TEUK_OPT_REAL_PATH: {
         if (value != 0 && value != 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: real path is 0 or 1");
         const int real = (value == 1 && (h->a == 0.0 || (h->s == 0 && h->m == 0))) ? 1 : 0;
@@ -626,7 +633,7 @@ extern "C" int teuk_time_kernels(teuk_handle *h, long n, double *ms_out)
             for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
                 e = h->variant == 2 ? launch_step_split(h->sp, h->phi[from], h->pi[from], h->phi[1 - from],
                                                         h->pi[1 - from], h->phiH, h->piH, (int)k, h->stream, false,
-                                                        part)
+                                                        part, h->split_rows)
                                     : launch_step_unfused(h->sp, h->phi[from], h->pi[from], h->phi[1 - from],
                                                           h->pi[1 - from], h->phiH, h->piH, (int)k, h->stream,
                                                           part);

@@ -33,6 +33,7 @@ struct teuk_handle {
     int rows_per_block = 1, nblocks = 1;
     int pdl = 1;      // programmatic dependent launch of the split kernels
     int in_batch = 0; // batches this handle belongs to (0 or 1): it is driven by the batch
+    int split_rows = 0;  // r* rows per CTA tile of the split kernels (0 = automatic)
     int chunk = 64;   // time steps per captured graph (even)
     cudaGraphExec_t graph[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     std::string err;

@@ -124,7 +124,7 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
 
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
                               double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl,
-                              int part = 2);
+                              int part = 2, int rows = 0);
 
 cudaError_t launch_advance(long long *step_base, long long by, cudaStream_t st);
 
@@ -151,7 +151,7 @@ int fused_block_threads(int nth);
 size_t fused_smem_bytes(int nth);
 const void *fused_kernel_ptr(int real);
 int split_rows_per_block(int nth);
-size_t split_smem_bytes(int nth);
+size_t split_smem_bytes(int nth, int rows = 0);
 const void *split_kernel_ptr(int which, int real);
 
 }  // namespace teuk

@@ -617,25 +617,29 @@ __global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *
     allow_dependents();  // after the last store
 }
 
-size_t split_smem_bytes(int nth) { return sizeof(double2) * (size_t)split_rows_per_block(nth) * (nth + 2); }
+size_t split_smem_bytes(int nth, int rows)
+{
+    return sizeof(double2) * (size_t)(rows > 0 ? rows : split_rows_per_block(nth)) * (nth + 2);
+}
 const void *split_kernel_ptr(int which, int real)
 {
     if (real) return which ? (const void *)lw_correct_split<true> : (const void *)lw_predict_split<true>;
     return which ? (const void *)lw_correct_split<false> : (const void *)lw_predict_split<false>;
 }
 
-// part: 0 = predictor only, 1 = corrector only, 2 = both.
+// part: 0 = predictor only, 1 = corrector only, 2 = both.  rows: r* rows per
+// CTA tile (0 = 256 / nth rounded to warps, at least 1).
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
                               double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl,
-                              int part)
+                              int part, int rows)
 {
-    const int R = split_rows_per_block(p.nth);
+    const int R = rows > 0 ? rows : split_rows_per_block(p.nth);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(fused_block_threads(p.nth), R);
-    cfg.dynamicSmemBytes = split_smem_bytes(p.nth);
+    cfg.dynamicSmemBytes = split_smem_bytes(p.nth, R);
     cfg.stream = st;
     cfg.attrs = pdl ? attr : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;

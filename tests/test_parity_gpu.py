@@ -180,15 +180,18 @@ def test_launch_shapes_agree_bitwise(teuk):
 
 
 def test_tuning_options_agree_bitwise(teuk):
-    # programmatic dependent launch and the graph chunk change scheduling only
+    # programmatic dependent launch, the graph chunk and the split tile height
+    # change scheduling only
     nr, nth = 260, 48
     dt = O.stable_dt(nr, nth, -20.0, 40.0, 0.9, -2, 2)
     u = inputs.random_fields(nr, nth, seed=13)
     ref = None
-    for pdl, chunk in [(1, 64), (0, 64), (1, 2), (1, 128), (0, 6)]:
+    for pdl, chunk, rows in [(1, 64, 0), (0, 64, 0), (1, 2, 0), (1, 128, 0), (0, 6, 0), (1, 64, 1), (1, 6, 3),
+                             (0, 64, 16)]:
         g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
         g.set_option(teuk.TEUK_OPT_PDL, pdl)
         g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, chunk)
+        g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, rows)
         g.set_initial(*u)
         g.set_source(**SRC)
         g.set_extraction(10.0, 3, capacity=200)
@@ -202,9 +205,14 @@ def test_tuning_options_agree_bitwise(teuk):
             for x, y in zip(st, ref):
                 np.testing.assert_array_equal(x, y)
         g.close()
+    g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
     with pytest.raises(teuk.TeukError):
-        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
         g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, 3)
+    with pytest.raises(teuk.TeukError):
+        g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, 17)   # 17 x 64 threads > 1024
+    with pytest.raises(teuk.TeukError):
+        g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, -1)
+    g.close()
 
 
 @pytest.mark.parametrize("nr,nth", [(40, 513), (20, 1024), (10, 96), (6, 32), (300, 128)])
