@@ -153,12 +153,12 @@ long teuk_step_count(const teuk_handle *h);
  * Returns TEUK_ERR_NONFINITE when not.  Synchronises. */
 int teuk_check_finite(teuk_handle *h, int *finite);
 
-/* Select the step kernel: 0 = fused radial-marching kernel (default),
- * 1 = two-kernel predictor/corrector with a half-step buffer in device
- * memory, 2 = the same two kernels over 2D tiles with the angular neighbour
- * sums shared in shared memory (0 needs nth <= 512, 2 needs nth <= 1024; the
- * default is the first of 0, 2, 1 that fits).  All compute the
- * same Eqs. (3)-(4) and give bit-identical results. */
+/* Select the step kernel: 0 = fused radial-marching kernel, 1 = two-kernel
+ * predictor/corrector with a half-step buffer in device memory, 2 = the same
+ * two kernels over 2D tiles with the angular neighbour sums shared in shared
+ * memory (0 needs nth <= 256, 2 needs nth <= 512; the default is 2 where it
+ * fits, else 1).  All compute the same Eqs. (3)-(4) and give bit-identical
+ * results. */
 int teuk_set_kernel(teuk_handle *h, int variant);
 
 /* Launch shape of the fused kernel: radial rows per CTA (one CTA per strip
@@ -181,7 +181,7 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  * s = m = 0: 44 instead of 56 FP64 instructions per point); 0 keeps the
  * complex planes.  Both give the same numbers. */
 #define TEUK_OPT_REAL_PATH 4
-/* TEUK_OPT_SPLIT_ROWS: r* rows per CTA tile of the split kernels, 1..1024 /
+/* TEUK_OPT_SPLIT_ROWS: r* rows per CTA tile of the split kernels, 1..512 /
  * (nth rounded up to a multiple of 32); 0 (default) picks 256 / that width,
  * at least 1.  A tile is one thread per point. */
 #define TEUK_OPT_SPLIT_ROWS 5
@@ -218,7 +218,7 @@ long teuk_launches_for(const teuk_handle *h, long n);
  *
  * The half step is kept in a static device array of 32 MiB inside libteuk:
  * every GPU that loads the library holds it until the process exits, and it
- * limits the grid to (nr - 1) * nth <= 1,048,576 (larger grids and nth > 1024
+ * limits the grid to (nr - 1) * nth <= 1,048,576 (larger grids and nth > 512
  * return TEUK_ERR_BAD_ARG).  All calls share that array and it keeps the last
  * call's contents, so calls that overlap on the GPU (different streams or
  * handles running at once) race: issue them one after another on one stream.
@@ -246,7 +246,7 @@ int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in,
  * teuk_set_* , teuk_step_noalloc and teuk_destroy on it return
  * TEUK_ERR_STATE until it is removed (or the batch destroyed); call
  * teuk_batch_sync() before reading a job's results through its handle
- * (teuk_extract, teuk_get_state).  Jobs need nth <= 1024.  A batch allocates its job table (and a job's
+ * (teuk_extract, teuk_get_state).  Jobs need nth <= 512.  A batch allocates its job table (and a job's
  * half-step buffer if the handle has none).
  * ------------------------------------------------------------------------ */
 typedef struct teuk_batch teuk_batch;
@@ -276,7 +276,7 @@ int teuk_batch_sync(teuk_batch *b);
 /* TEUK_OPT_PDL, TEUK_OPT_GRAPH_CHUNK or TEUK_OPT_BLOCK_THREADS. */
 int teuk_batch_set_option(teuk_batch *b, int option, long value);
 
-/* Time each candidate CTA size (256, 512, 1024 threads; at least the widest
+/* Time each candidate CTA size (128, 256, 512 threads; at least the widest
  * job's row) on the batch's own jobs -- the timed steps count as progress --
  * and keep the fastest; *best_block receives it.  Synchronises. */
 int teuk_batch_autotune(teuk_batch *b, int *best_block);
@@ -288,6 +288,29 @@ long teuk_batch_launches_for(const teuk_batch *b, long n);
 const char *teuk_batch_last_error(const teuk_batch *b);
 
 int teuk_batch_destroy(teuk_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Arithmetic check.  The Pi rows of Eqs. (3)-(4) are sums of 6 to 10
+ * products of FP64 coefficients and fields; the step kernels evaluate them
+ * in 64-bit fixed point on the integer pipe: exact 106-bit products, aligned
+ * and truncated to 2^-57 of the largest product, summed, and rounded once to
+ * FP64 (error <= n 2^-57 max|c_k x_k| + 2^-53 |sum|); where that is not
+ * possible (an input not finite, a result below 2^-823 or overflowing) the
+ * kernels use FP64 fused multiply-adds instead.  The paper has no
+ * counterpart: it is an implementation of its double-precision sums for a
+ * GPU whose FP64 pipe is narrow.
+ *
+ * teuk_fixed_dot evaluates that arithmetic for `count` independent sums of
+ * `nterms` (1..16) terms: out[i] = sum_k (-1)^flip[i*nterms+k]
+ * c[i*nterms+k] x[i*nterms+k], ok[i] = 1 where the fixed-point sum applies
+ * (ok[i] = 0: out[i] unspecified; the kernels would use FP64 there).
+ * on_device = 0 runs the host build of the same code, 1 the device build
+ * (copies through temporary device buffers; synchronous).  All pointers are
+ * host pointers owned by the caller.  Returns TEUK_ERR_BAD_ARG for nterms
+ * outside 1..16, count < 0 or a NULL array, TEUK_ERR_OOM / TEUK_ERR_CUDA on
+ * device failures. */
+int teuk_fixed_dot(int on_device, int nterms, long count, const double *c, const double *x,
+                   const unsigned *flip, double *out, int *ok);
 
 /* Message of the last failed call on this handle ("" if none). */
 const char *teuk_last_error(const teuk_handle *h);

@@ -22,7 +22,6 @@
 using namespace teuk;
 
 static const double kPi = 3.14159265358979323846;
-static const int kFusedMaxNth = 512;  // the fused kernel keeps a row ahead in registers: <= 512 threads
 
 // ---------------------------------------------------------------------------
 // Helpers
@@ -313,22 +312,10 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     p.src = SourceWindow{0, -1, 0, -1, nullptr, nullptr, 0.0, 0};
     p.ext = Extraction{-1, 1, 1, nullptr};
     p.step_base = h->d_step;
-    h->variant = nth <= 1024 ? 2 : 1;
-    if (nth <= 1024) {
-        const size_t smem = fused_smem_bytes(nth);
-        if (smem > 48 * 1024)
-            for (int rl = 0; rl < 2; ++rl)
-                if (cudaFuncSetAttribute(fused_kernel_ptr(rl), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                    cudaSuccess)
-                    return bail(TEUK_ERR_CUDA);
-        choose_launch(h, 0);
-        const size_t ssm = split_smem_bytes(nth);
-        if (ssm > 48 * 1024)
-            for (int w = 0; w < 4; ++w)
-                if (cudaFuncSetAttribute(split_kernel_ptr(w & 1, w >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ssm) != cudaSuccess)
-                    return bail(TEUK_ERR_CUDA);
-    }
+    h->variant = nth <= kTileMaxThreads ? 2 : 1;
+    // Shared memory stays below the 48 KB default: the fused kernel takes
+    // 64 (nth + 2) bytes <= 16.5 KB, a split tile 16 R (TW + 2) <= 8.3 KB.
+    if (nth <= kFusedMaxNth) choose_launch(h, 0);  // the fused kernel's shape, for when it is selected
     if (h->variant != 0) {  // the two-kernel variants keep the half step in device memory
         if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return bail(TEUK_ERR_OOM); }
         h->piH = h->phiH + Nm;
@@ -555,7 +542,7 @@ extern "C" int teuk_step(teuk_handle *h, long n)
 extern "C" int teuk_set_launch(teuk_handle *h, int rows_per_block)
 {
     if (!h || rows_per_block < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_launch: rows_per_block < 0");
-    if (h->nth > kFusedMaxNth) return fail(h, TEUK_ERR_STATE, "teuk_set_launch: fused kernel needs nth <= 512");
+    if (h->nth > kFusedMaxNth) return fail(h, TEUK_ERR_STATE, "teuk_set_launch: fused kernel needs nth <= 256");
     CU(cudaStreamSynchronize(h->stream));
     destroy_graphs(h);
     choose_launch(h, rows_per_block);
@@ -581,8 +568,8 @@ extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
         h->chunk = (int)value;
         return TEUK_OK;
     case TEUK_OPT_SPLIT_ROWS:
-        if (value < 0 || value * fused_block_threads(h->nth) > 1024)
-            return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: split rows must be 0 or 1..1024 / (nth rounded up to warps)");
+        if (value < 0 || value * split_tile_width(h->nth) > kTileMaxThreads)
+            return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: split rows must be 0 or 1..512 / (split tile width)");
         CU(cudaStreamSynchronize(h->stream));
         destroy_graphs(h);
         h->split_rows = (int)value;
@@ -676,8 +663,8 @@ extern "C" int teuk_set_kernel(teuk_handle *h, int variant)
 {
     if (!h || variant < 0 || variant > 2) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: variant 0, 1 or 2");
     if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_kernel: the handle belongs to a batch (remove it first)");
-    if ((variant == 0 && h->nth > kFusedMaxNth) || (variant == 2 && h->nth > 1024))
-        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: fused kernel needs nth <= 512, split nth <= 1024");
+    if ((variant == 0 && h->nth > kFusedMaxNth) || (variant == 2 && h->nth > kTileMaxThreads))
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_kernel: fused kernel needs nth <= 256, split nth <= 512");
     if (variant != 0 && !h->phiH) {
         const size_t Nm = (size_t)(h->nr - 1) * h->nth;
         if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) {
@@ -719,8 +706,8 @@ extern "C" int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const dou
     if (!h || !phi_in || !pi_in || !phi_out || !pi_out || step_index < 0)
         return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: NULL buffer or negative step index");
     if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_step_noalloc: the handle belongs to a batch (remove it first)");
-    if (h->nth > 1024)
-        return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: needs nth <= 1024");
+    if (h->nth > kTileMaxThreads)
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: needs nth <= 512");
     const long long mids = (long long)(h->nr - 1) * h->nth;
     if (mids > kNoAllocMaxMid)
         return fail(h, TEUK_ERR_BAD_ARG,

@@ -114,7 +114,7 @@ extern "C" int teuk_batch_add(teuk_batch *b, teuk_handle *h, long steps, int *jo
     if (!b || !h || steps < 0 || !job_id) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: bad argument");
     *job_id = -1;
     if (h->device != b->device) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: handle on another device");
-    if (h->nth > 1024) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: batched tiles need nth <= 1024");
+    if (h->nth > kTileMaxThreads) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: batched tiles need nth <= 512");
     for (const auto &j : b->jobs)
         if (j.member && j.h == h) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_add: handle already in the batch");
     if (h->in_batch) return bfail(b, TEUK_ERR_STATE, "teuk_batch_add: handle belongs to another batch");
@@ -171,7 +171,7 @@ static int pick_block(const teuk_batch *b)
     for (int id : b->active) widest = std::max(widest, colpad_of(b->jobs[id].h->nth));
     int blk = std::max(256, widest);
     if (b->block_request >= widest) blk = b->block_request;
-    return std::min(blk, 1024);
+    return std::min(blk, kTileMaxThreads);
 }
 
 // Rebuild the job table and tile offsets for the jobs with steps left.
@@ -327,8 +327,8 @@ extern "C" int teuk_batch_set_option(teuk_batch *b, int option, long value)
         b->chunk = (int)value;
         break;
     case TEUK_OPT_BLOCK_THREADS:
-        if (value != 0 && (value < 32 || value > 1024 || value % 32))
-            return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: block threads 0 or a multiple of 32 <= 1024");
+        if (value != 0 && (value < 32 || value > kTileMaxThreads || value % 32))
+            return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: block threads 0 or a multiple of 32 <= 512");
         b->block_request = (int)value;
         b->layout_dirty = true;
         break;
@@ -349,7 +349,7 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best_block)
     if (b->active.empty()) return bfail(b, TEUK_ERR_STATE, "teuk_batch_autotune: no job has steps left");
     int widest = 32;
     for (int id : b->active) widest = std::max(widest, colpad_of(b->jobs[id].h->nth));
-    const int cands[] = {256, 512, 1024};
+    const int cands[] = {128, 256, 512};
     cudaEvent_t e0, e1;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));

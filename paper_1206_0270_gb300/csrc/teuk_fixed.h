@@ -1,0 +1,164 @@
+// teuk_fixed.h -- sums of products of FP64 numbers in 64-bit fixed point.
+//
+// The Pi rows of the predictor (Eq. 3) and corrector (Eq. 4) are short sums
+// sum_k f_k c_k x_k (f_k = +-1, 6 to 10 terms) of FP64 coefficients and
+// fields.  GB300 issues FP64 FMAs at under 2 per clock per SM but 32-bit
+// integer multiply-adds at about 60, so these sums are evaluated on the
+// integer pipe:
+//
+//   * each operand is split into its 53-bit significand m and exponent e,
+//     value = m 2^(e - 1075) (subnormals: no hidden bit, e = 1, which is
+//     exact; zeros never set the frame);
+//   * each product m_c m_x (at most 106 bits) is formed exactly with four
+//     32 x 32 -> 64-bit multiply-adds;
+//   * all products are aligned to the largest product exponent E and
+//     truncated to units of 2^(E - 2103): the largest product keeps at least
+//     57 bits (2^104 <= m_c m_x), every product is below 2^59 units, and up
+//     to 16 of them sum without overflow in a signed 64-bit integer;
+//   * the integer sum is rounded once to FP64, to nearest, ties to even.
+//
+// Error: |result - exact| <= n 2^-57 max_k |c_k x_k| + 2^-53 |exact|
+// (truncation of n products, then one rounding), which is at or below the
+// error of the same sum formed by FP64 fused multiply-adds (each of its n
+// roundings is relative to a partial sum).  Integer addition is exact and
+// associative, so the result does not depend on the order of the terms, and
+// terms whose coefficient or field is zero change nothing, not even the
+// frame.
+//
+// The sum reports failure, and the caller evaluates it with FP64 FMAs
+// instead, when an input is not finite or the result is below 2^-823 (there
+// a product with a subnormal field could have set the frame; coefficients of
+// the scheme are far below the 2^170 this bound allows) or would overflow.
+//
+// Everything here is plain integer arithmetic on host and device, so the
+// same code is tested on the CPU against exact rational arithmetic.
+#pragma once
+#include <stdint.h>
+#include <string.h>
+
+#ifdef __CUDACC__
+#define TEUK_FX_HD __host__ __device__ __forceinline__
+#else
+#define TEUK_FX_HD static inline
+#endif
+
+namespace teuk {
+
+TEUK_FX_HD uint64_t fx_bits(double v)
+{
+#ifdef __CUDA_ARCH__
+    return (uint64_t)__double_as_longlong(v);
+#else
+    uint64_t u;
+    memcpy(&u, &v, sizeof u);
+    return u;
+#endif
+}
+
+TEUK_FX_HD double fx_double(uint64_t u)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double v;
+    memcpy(&v, &u, sizeof v);
+    return v;
+#endif
+}
+
+TEUK_FX_HD int fx_clz64(uint64_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// p >> s for any s >= 0 (0 once s >= 64; PTX shr clamps the shift count)
+TEUK_FX_HD uint64_t fx_shr(uint64_t p, uint32_t s)
+{
+#ifdef __CUDA_ARCH__
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(p), "r"(s));
+    return r;
+#else
+    return s >= 64 ? 0 : p >> s;
+#endif
+}
+
+// An FP64 number split for the fixed-point sums.
+struct Fx {
+    uint32_t mhi, mlo;  // significand: high 21 bits (hidden bit included for normal numbers), low 32 bits
+    int e;              // max(biased exponent, 1); -4096 for +-0
+    uint32_t neg;       // sign bit
+    uint32_t braw;      // biased exponent field (2047: not finite)
+};
+
+TEUK_FX_HD Fx fx_unpack(double v)
+{
+    const uint64_t u = fx_bits(v);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const uint32_t eraw = (hi >> 20) & 0x7FFu;
+    const bool zero = ((hi & 0x7FFFFFFFu) | lo) == 0;
+    Fx o;
+    o.mhi = (hi & 0xFFFFFu) | (eraw ? 0x100000u : 0u);
+    o.mlo = lo;
+    o.e = zero ? -4096 : (eraw ? (int)eraw : 1);
+    o.neg = hi >> 31;
+    o.braw = eraw;
+    return o;
+}
+
+// floor(m_c m_x / 2^47) of the exact 106-bit product
+TEUK_FX_HD uint64_t fx_prod47(const Fx &c, const Fx &x)
+{
+    const uint64_t t0 = (uint64_t)c.mlo * x.mlo;
+    const uint64_t t1 = (uint64_t)c.mlo * x.mhi + (t0 >> 32);
+    const uint64_t t2 = (uint64_t)c.mhi * x.mlo + t1;
+    const uint64_t t3 = (uint64_t)c.mhi * x.mhi + (t2 >> 32);
+    // m_c m_x = t3 2^64 + (t2 mod 2^32) 2^32 + (t0 mod 2^32)
+    return (t3 << 17) | ((t2 & 0xFFFFFFFFu) >> 15);
+}
+
+// *out = sum_k (-1)^flip[k] c[k] x[k] for N <= 16 terms.  Returns false
+// (with *out unspecified) when the caller must use FP64 arithmetic instead.
+template <int N>
+TEUK_FX_HD bool fx_dot(const Fx *c, const Fx *x, const uint32_t *flip, double *out)
+{
+    static_assert(N >= 1 && N <= 16, "at most 16 terms fit the 64-bit accumulator");
+    int T[N];
+    int E = 0;
+    uint32_t braw = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        T[k] = c[k].e + x[k].e;  // negative when either factor is zero
+        E = T[k] > E ? T[k] : E;
+        braw = c[k].braw > braw ? c[k].braw : braw;
+        braw = x[k].braw > braw ? x[k].braw : braw;
+    }
+    uint64_t acc = 0;  // two's complement, units of 2^(E - 2103)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const uint64_t v = fx_shr(fx_prod47(c[k], x[k]), (uint32_t)(E - T[k]));
+        acc += (c[k].neg ^ x[k].neg ^ flip[k]) ? (uint64_t)0 - v : v;
+    }
+    const uint32_t neg = (uint32_t)(acc >> 63);
+    const uint64_t mag = neg ? (uint64_t)0 - acc : acc;
+    const int lz = fx_clz64(mag);
+    const uint64_t nrm = mag << (lz & 63);  // leading one at bit 63
+    uint64_t m = nrm >> 11;                 // 53-bit significand
+    const uint32_t guard = (uint32_t)(nrm >> 10) & 1u;
+    const uint32_t sticky = (nrm & 0x3FFu) != 0;
+    m += guard & (sticky | (uint32_t)(m & 1u));
+    const int eb = E - 1017 - lz;  // biased exponent of the leading one
+    // (eb - 1) 2^52 + m: the hidden bit lifts the exponent field to eb, and a
+    // significand that rounds up to 2^53 carries into it
+    const uint64_t r = (((uint64_t)(eb - 1) << 52) + m) | ((uint64_t)neg << 63);
+    *out = mag == 0 ? 0.0 : fx_double(r);
+    return braw < 0x7FFu && (mag == 0 || (eb >= 200 && eb <= 2045));
+}
+
+
+
+}  // namespace teuk

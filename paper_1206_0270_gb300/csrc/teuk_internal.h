@@ -37,6 +37,14 @@
 
 namespace teuk {
 
+// Thread limits of the step kernels.  Their Pi rows are fixed-point sums
+// (teuk_fixed.h) that need up to 128 registers per thread (split and batch
+// kernels) or about 230 (the fused kernel, which also holds the next row's
+// loads), so their launch bounds admit 512 and 256 threads per CTA.  One
+// thread covers one theta point of a tile row.
+constexpr int kTileMaxThreads = 512;  // split and batch tiles: nth <= 512
+constexpr int kFusedMaxNth = 256;     // fused kernel: nth <= 256
+
 // Predictor planes: rows hp = 0 .. nr-2 (mid-point r*_{hp+1/2}), nth values each.
 struct PredPlanes {
     const double *pa, *pb, *eb, *KA, *KC;
@@ -150,6 +158,8 @@ const void *batch_kernel_ptr(int which);
 int fused_block_threads(int nth);
 size_t fused_smem_bytes(int nth);
 const void *fused_kernel_ptr(int real);
+int split_tile_width(int nth);
+int split_theta_tiles(int nth);
 int split_rows_per_block(int nth);
 size_t split_smem_bytes(int nth, int rows = 0);
 const void *split_kernel_ptr(int which, int real);

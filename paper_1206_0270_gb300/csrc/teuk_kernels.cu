@@ -15,6 +15,7 @@
 // shared memory.  The only redundant work is one predictor row per strip.
 #include "teuk_internal.h"
 #include "teuk_physics.h"
+#include "teuk_fixed.h"
 
 namespace teuk {
 
@@ -244,22 +245,72 @@ __device__ __forceinline__ double2 kmul(const double2 c, const double2 x, const 
 
 // Predictor (Eq. 3) at one mid-point.  phi0/pi0: u at row hp, phi1/pi1: u at
 // row hp + 1, sup/sdn: sigma = Phi_hp + Phi_{hp+1} at j+1, j-1.
+// The Phi row and the sums tau, sigma run on the FP64 pipe; the Pi row
+// P1 tau + eb Pi1 + Q1 Phi0 + Q2 Phi1 + KA sup + KC sdn is a fixed-point sum
+// on the integer pipe (teuk_fixed.h), with this FP64 evaluation as fallback.
+template <bool REAL>
+__device__ __forceinline__ double2 pred_pi_fp64(const PredCoef &c, const Ops ops, double2 tau, double2 phi0,
+                                                double2 phi1, double2 pi1, double2 sup, double2 sdn)
+{
+    // P1 Pi_i + P2 Pi_{i+1} = P1 tau + (P2 - P1) Pi_{i+1}, tau = Pi_i + Pi_{i+1}, P2 - P1 = 2 beta (eb)
+    double2 o = kmul<REAL>(c.P1, tau, ops);
+    rfma(o, c.eb, pi1);
+    kfma<REAL>(o, c.Q1, phi0);
+    kfma<REAL>(o, c.Q2, phi1);
+    rfma(o, c.KA, sup);
+    rfma(o, c.KC, sdn);
+    return o;
+}
+
+// TEUK_FIXED_POINT 0 builds all-FP64 kernels (the Pi rows as FMA chains),
+// for comparison; the default evaluates the Pi rows in fixed point.
+#ifndef TEUK_FIXED_POINT
+#define TEUK_FIXED_POINT 1
+#endif
+
+template <bool REAL>
+__device__ __forceinline__ double2 pred_pi(const PredCoef &c, const Ops ops, double2 tau, double2 phi0,
+                                           double2 phi1, double2 pi1, double2 sup, double2 sdn)
+{
+    if (!TEUK_FIXED_POINT) return pred_pi_fp64<REAL>(c, ops, tau, phi0, phi1, pi1, sup, sdn);
+    const Fx tr = fx_unpack(tau.x), ti = fx_unpack(tau.y), pr = fx_unpack(pi1.x), pim = fx_unpack(pi1.y);
+    const Fx ar = fx_unpack(phi0.x), ai = fx_unpack(phi0.y), br = fx_unpack(phi1.x), bi = fx_unpack(phi1.y);
+    const Fx ur = fx_unpack(sup.x), ui = fx_unpack(sup.y), dr = fx_unpack(sdn.x), di = fx_unpack(sdn.y);
+    const Fx P1r = fx_unpack(c.P1.x), eb = fx_unpack(c.eb), Q1r = fx_unpack(c.Q1.x), Q2r = fx_unpack(c.Q2.x);
+    const Fx KA = fx_unpack(c.KA), KC = fx_unpack(c.KC);
+    double2 o;
+    bool ok;
+    if (REAL) {
+        const Fx C[6] = {P1r, eb, Q1r, Q2r, KA, KC};
+        const Fx Xr[6] = {tr, pr, ar, br, ur, dr};
+        const Fx Xi[6] = {ti, pim, ai, bi, ui, di};
+        const uint32_t F[6] = {0, 0, 0, 0, 0, 0};
+        ok = fx_dot<6>(C, Xr, F, &o.x);
+        ok &= fx_dot<6>(C, Xi, F, &o.y);
+    } else {
+        const Fx P1i = fx_unpack(c.P1.y), Q1i = fx_unpack(c.Q1.y), Q2i = fx_unpack(c.Q2.y);
+        const Fx C[9] = {P1r, P1i, eb, Q1r, Q1i, Q2r, Q2i, KA, KC};
+        const Fx Xr[9] = {tr, ti, pr, ar, ai, br, bi, ur, dr};
+        const uint32_t Fr[9] = {0, 1, 0, 0, 1, 0, 1, 0, 0};
+        const Fx Xi[9] = {ti, tr, pim, ai, ar, bi, br, ui, di};
+        const uint32_t Fi[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        ok = fx_dot<9>(C, Xr, Fr, &o.x);
+        ok &= fx_dot<9>(C, Xi, Fi, &o.y);
+    }
+    if (!ok) o = pred_pi_fp64<REAL>(c, ops, tau, phi0, phi1, pi1, sup, sdn);
+    return o;
+}
+
 template <bool REAL>
 __device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, const Ops ops, double2 phi0,
                                               double2 pi0, double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
-    // P1 Pi_i + P2 Pi_{i+1} = P1 tau + (P2 - P1) Pi_{i+1}, tau = Pi_i + Pi_{i+1}, P2 - P1 = 2 beta (eb)
     HalfStep o;
     const double2 tau = add2(pi0, pi1, ops);
     o.phi = make_double2(fma_rn(c.pa, phi0.x, ops.nzero), fma_rn(c.pa, phi0.y, ops.nzero));
     rfma(o.phi, c.pb, phi1);
     rfma(o.phi, q, tau);
-    o.pi = kmul<REAL>(c.P1, tau, ops);
-    rfma(o.pi, c.eb, pi1);
-    kfma<REAL>(o.pi, c.Q1, phi0);
-    kfma<REAL>(o.pi, c.Q2, phi1);
-    rfma(o.pi, c.KA, sup);
-    rfma(o.pi, c.KC, sdn);
+    o.pi = pred_pi<REAL>(c, ops, tau, phi0, phi1, pi1, sup, sdn);
     return o;
 }
 
@@ -273,18 +324,13 @@ __device__ __forceinline__ HalfStep predict(const StepParams &p, size_t k, doubl
 }
 
 // Corrector (Eq. 4) at one node.  hp: half step at i + 1/2, hm: at i - 1/2,
-// sup/sdn: sigma' = Phi^{i+1/2} + Phi^{i-1/2} at j+1, j-1.
+// sup/sdn: sigma' = Phi^{i+1/2} + Phi^{i-1/2} at j+1, j-1.  As in the
+// predictor, the Pi row is a fixed-point sum with an FP64 fallback.
 template <bool REAL>
-__device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, const Ops ops, double2 phi,
-                                          double2 pi, const HalfStep &hp, const HalfStep &hm, double2 sup,
-                                          double2 sdn, double2 *phi_out, double2 *pi_out)
+__device__ __forceinline__ double2 corr_pi_fp64(const CorrCoef &c, const Ops ops, double2 pi, double2 tau,
+                                                const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn)
 {
     // R1 Pi^{+} + R2 Pi^{-} = R1 tau' + (R2 - R1) Pi^{-}, tau' = Pi^{+} + Pi^{-}, R2 - R1 = -2 tb (nt2)
-    const double2 tau = add2(hp.pi, hm.pi, ops);
-    double2 nphi = phi;
-    rfma(nphi, -c.tb, hp.phi);
-    rfma(nphi, c.tb, hm.phi);
-    rfma(nphi, half_dt, tau);
     double2 npi = pi;
     kfma<REAL>(npi, c.R1, tau);
     rfma(npi, c.nt2, hm.pi);
@@ -292,8 +338,56 @@ __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, con
     kfma<REAL>(npi, c.R4, hm.phi);
     rfma(npi, c.KA, sup);
     rfma(npi, c.KC, sdn);
+    return npi;
+}
+
+template <bool REAL>
+__device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, double2 pi, double2 tau,
+                                           const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn)
+{
+    if (!TEUK_FIXED_POINT) return corr_pi_fp64<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
+    const Fx one = fx_unpack(1.0);
+    const Fx pr = fx_unpack(pi.x), pim = fx_unpack(pi.y), tr = fx_unpack(tau.x), ti = fx_unpack(tau.y);
+    const Fx mr = fx_unpack(hm.pi.x), mi = fx_unpack(hm.pi.y);
+    const Fx ar = fx_unpack(hp.phi.x), ai = fx_unpack(hp.phi.y), br = fx_unpack(hm.phi.x), bi = fx_unpack(hm.phi.y);
+    const Fx ur = fx_unpack(sup.x), ui = fx_unpack(sup.y), dr = fx_unpack(sdn.x), di = fx_unpack(sdn.y);
+    const Fx R1r = fx_unpack(c.R1.x), nt2 = fx_unpack(c.nt2), R3r = fx_unpack(c.R3.x), R4r = fx_unpack(c.R4.x);
+    const Fx KA = fx_unpack(c.KA), KC = fx_unpack(c.KC);
+    double2 o;
+    bool ok;
+    if (REAL) {
+        const Fx C[7] = {one, R1r, nt2, R3r, R4r, KA, KC};
+        const Fx Xr[7] = {pr, tr, mr, ar, br, ur, dr};
+        const Fx Xi[7] = {pim, ti, mi, ai, bi, ui, di};
+        const uint32_t F[7] = {0, 0, 0, 0, 0, 0, 0};
+        ok = fx_dot<7>(C, Xr, F, &o.x);
+        ok &= fx_dot<7>(C, Xi, F, &o.y);
+    } else {
+        const Fx R1i = fx_unpack(c.R1.y), R3i = fx_unpack(c.R3.y), R4i = fx_unpack(c.R4.y);
+        const Fx C[10] = {one, R1r, R1i, nt2, R3r, R3i, R4r, R4i, KA, KC};
+        const Fx Xr[10] = {pr, tr, ti, mr, ar, ai, br, bi, ur, dr};
+        const uint32_t Fr[10] = {0, 0, 1, 0, 0, 1, 0, 1, 0, 0};
+        const Fx Xi[10] = {pim, ti, tr, mi, ai, ar, bi, br, ui, di};
+        const uint32_t Fi[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        ok = fx_dot<10>(C, Xr, Fr, &o.x);
+        ok &= fx_dot<10>(C, Xi, Fi, &o.y);
+    }
+    if (!ok) o = corr_pi_fp64<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
+    return o;
+}
+
+template <bool REAL>
+__device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, const Ops ops, double2 phi,
+                                          double2 pi, const HalfStep &hp, const HalfStep &hm, double2 sup,
+                                          double2 sdn, double2 *phi_out, double2 *pi_out)
+{
+    const double2 tau = add2(hp.pi, hm.pi, ops);
+    double2 nphi = phi;
+    rfma(nphi, -c.tb, hp.phi);
+    rfma(nphi, c.tb, hm.phi);
+    rfma(nphi, half_dt, tau);
     *phi_out = nphi;
-    *pi_out = npi;
+    *pi_out = corr_pi<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
 }
 
 template <bool REAL>
@@ -314,7 +408,7 @@ size_t fused_smem_bytes(int nth) { return sizeof(double2) * 4 * (size_t)(nth + 2
 int fused_block_threads(int nth) { return ((nth + 31) / 32) * 32; }
 
 template <bool REAL>
-__global__ void __launch_bounds__(512) lw_step_fused(StepParams p, const double2 *__restrict__ Phi,
+__global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, const double2 *__restrict__ Phi,
                                                       const double2 *__restrict__ Pi,
                                                       double2 *__restrict__ PhiO,
                                                       double2 *__restrict__ PiO, int k, int rpb)
@@ -515,19 +609,35 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
 // and shared with the angular neighbours through shared memory.
 // ---------------------------------------------------------------------------
 
-int split_rows_per_block(int nth)
+// Split tiles: TW theta columns (a multiple of 32, at most 128) by R r* rows,
+// one thread per point.  Rows wider than 128 are cut into equal tiles; each
+// tile forms its two halo sums sigma(j0 - 1) and sigma(j0 + TW) itself.
+// Small CTAs keep several tiles resident per SM (the fixed-point Pi rows need
+// up to 128 registers per thread).
+int split_tile_width(int nth)
 {
     const int cols = fused_block_threads(nth);
-    return cols >= 256 ? 1 : 256 / cols;
+    const int tiles = (cols + 127) / 128;
+    return (((nth + tiles - 1) / tiles) + 31) / 32 * 32;
+}
+int split_theta_tiles(int nth)
+{
+    const int tw = split_tile_width(nth);
+    return (nth + tw - 1) / tw;
+}
+int split_rows_per_block(int nth)
+{
+    const int tw = split_tile_width(nth);
+    return tw >= 128 ? 1 : 128 / tw;
 }
 
 // Launch bounds of the split kernels.  The single-argument form leaves ptxas
-// free to pick the register count (48 / 52 for the complex kernels, so five
-// 256-thread tiles fit on an SM); an explicit minimum of one block per SM
-// makes it use up to 64 and costs a resident tile.  TEUK_SPLIT_MINB, when
-// defined, selects the two-argument form for register-budget experiments.
+// free to pick the register count up to 65536 / threads; an explicit minimum
+// of one block per SM made it use more registers than needed and cost a
+// resident tile.  TEUK_SPLIT_MINB, when defined, selects the two-argument
+// form for register-budget experiments.
 #ifndef TEUK_SPLIT_THREADS
-#define TEUK_SPLIT_THREADS 1024
+#define TEUK_SPLIT_THREADS kTileMaxThreads
 #endif
 #ifdef TEUK_SPLIT_MINB
 #define TEUK_SPLIT_BOUNDS __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB)
@@ -537,27 +647,34 @@ int split_rows_per_block(int nth)
 
 template <bool REAL>
 __global__ void TEUK_SPLIT_BOUNDS lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
-                                                         const double2 *__restrict__ Pi,
-                                                         double2 *__restrict__ PhiH,
-                                                         double2 *__restrict__ PiH, int k)
+                                                   const double2 *__restrict__ Pi, double2 *__restrict__ PhiH,
+                                                   double2 *__restrict__ PiH, int k)
 {
     extern __shared__ double2 smem[];
-    const int nth = p.nth, W = nth + 2;
-    const int j = threadIdx.x;
+    const int nth = p.nth, TW = blockDim.x, tx = threadIdx.x;
+    const int j0 = blockIdx.y * TW, j = j0 + tx;
     const bool colok = j < nth;
     const int jj = colok ? j : nth - 1;
     const int hp = blockIdx.x * blockDim.y + threadIdx.y;
     const bool rowok = hp < p.nr - 1;
     const int hq = rowok ? hp : p.nr - 2;
-    double2 *row = smem + threadIdx.y * W;
-    if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
+    double2 *row = smem + threadIdx.y * (TW + 2);
     const size_t k0 = (size_t)hq * nth + jj;
     const PredCoef c = load_pred<REAL>(p, k0);
     grid_dependency_wait();
     const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth), pi1 = ldcg(Pi + k0 + nth);
-    if (colok) row[j + 1] = add2(phi0, phi1, ops_of(p));
+    const Ops ops = ops_of(p);
+    row[tx + 1] = colok ? add2(phi0, phi1, ops) : make_double2(0.0, 0.0);
+    // halo sums from the neighbouring tiles; zero at the poles (the ghost
+    // values are folded into the coefficients) and past the last column
+    const size_t kr = (size_t)hq * nth;
+    if (tx == 0)
+        row[0] = j0 > 0 ? add2(ldcg(Phi + kr + j0 - 1), ldcg(Phi + kr + nth + j0 - 1), ops) : make_double2(0.0, 0.0);
+    if (tx == TW - 1)
+        row[TW + 1] = j0 + TW < nth ? add2(ldcg(Phi + kr + j0 + TW), ldcg(Phi + kr + nth + j0 + TW), ops)
+                                    : make_double2(0.0, 0.0);
     __syncthreads();
-    HalfStep o = predict_c<REAL>(c, p.q, ops_of(p), phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
+    HalfStep o = predict_c<REAL>(c, p.q, ops, phi0, pi0, phi1, pi1, row[tx + 2], row[tx]);
     const SourceWindow &sw = p.src;
     if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
         const long long n = ldcg(p.step_base) + k;
@@ -572,22 +689,19 @@ __global__ void TEUK_SPLIT_BOUNDS lw_predict_split(StepParams p, const double2 *
 
 template <bool REAL>
 __global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
-                                                         const double2 *__restrict__ Pi,
-                                                         const double2 *__restrict__ PhiH,
-                                                         const double2 *__restrict__ PiH,
-                                                         double2 *__restrict__ PhiO,
-                                                         double2 *__restrict__ PiO, int k)
+                                                   const double2 *__restrict__ Pi, const double2 *__restrict__ PhiH,
+                                                   const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
+                                                   double2 *__restrict__ PiO, int k)
 {
     extern __shared__ double2 smem[];
-    const int nth = p.nth, W = nth + 2;
-    const int j = threadIdx.x;
+    const int nth = p.nth, TW = blockDim.x, tx = threadIdx.x;
+    const int j0 = blockIdx.y * TW, j = j0 + tx;
     const bool colok = j < nth;
     const int jj = colok ? j : nth - 1;
     const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
     const bool rowok = i <= p.nr - 2;
     const int iq = rowok ? i : p.nr - 2;
-    double2 *row = smem + threadIdx.y * W;
-    if (threadIdx.x < 2) row[threadIdx.x == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
+    double2 *row = smem + threadIdx.y * (TW + 2);
     const size_t kc = (size_t)iq * nth + jj;
     const CorrCoef c = load_corr<REAL>(p, kc);
     grid_dependency_wait();
@@ -597,10 +711,17 @@ __global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *
     hm.phi = ldcg(PhiH + kc - nth);
     hm.pi = ldcg(PiH + kc - nth);
     const double2 phi = ldcg(Phi + kc), pi = ldcg(Pi + kc);
-    if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops_of(p));
+    const Ops ops = ops_of(p);
+    row[tx + 1] = colok ? add2(hp.phi, hm.phi, ops) : make_double2(0.0, 0.0);
+    const size_t kr = (size_t)iq * nth;
+    if (tx == 0)
+        row[0] = j0 > 0 ? add2(ldcg(PhiH + kr + j0 - 1), ldcg(PhiH + kr - nth + j0 - 1), ops) : make_double2(0.0, 0.0);
+    if (tx == TW - 1)
+        row[TW + 1] = j0 + TW < nth ? add2(ldcg(PhiH + kr + j0 + TW), ldcg(PhiH + kr - nth + j0 + TW), ops)
+                                    : make_double2(0.0, 0.0);
     __syncthreads();
     double2 nphi, npi;
-    correct_c<REAL>(c, p.half_dt, ops_of(p), phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
+    correct_c<REAL>(c, p.half_dt, ops, phi, pi, hp, hm, row[tx + 2], row[tx], &nphi, &npi);
     const long long n = ldcg(p.step_base) + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
@@ -619,7 +740,7 @@ __global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *
 
 size_t split_smem_bytes(int nth, int rows)
 {
-    return sizeof(double2) * (size_t)(rows > 0 ? rows : split_rows_per_block(nth)) * (nth + 2);
+    return sizeof(double2) * (size_t)(rows > 0 ? rows : split_rows_per_block(nth)) * (split_tile_width(nth) + 2);
 }
 const void *split_kernel_ptr(int which, int real)
 {
@@ -638,20 +759,21 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(fused_block_threads(p.nth), R);
+    const int TW = split_tile_width(p.nth), tiles = split_theta_tiles(p.nth);
+    cfg.blockDim = dim3(TW, R);
     cfg.dynamicSmemBytes = split_smem_bytes(p.nth, R);
     cfg.stream = st;
     cfg.attrs = pdl ? attr : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;
     cudaError_t e = cudaSuccess;
     if (part != 1) {
-        cfg.gridDim = dim3((p.nr - 1 + R - 1) / R);
+        cfg.gridDim = dim3((p.nr - 1 + R - 1) / R, tiles);
         e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_predict_split<true>, p, Phi, Pi, PhiH, PiH, k)
                         : cudaLaunchKernelEx(&cfg, lw_predict_split<false>, p, Phi, Pi, PhiH, PiH, k);
         if (e != cudaSuccess) return e;
     }
     if (part != 0) {
-        cfg.gridDim = dim3((p.nr - 2 + R - 1) / R);
+        cfg.gridDim = dim3((p.nr - 2 + R - 1) / R, tiles);
         e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_correct_split<true>, p, Phi, Pi, (const double2 *)PhiH,
                                              (const double2 *)PiH, PhiO, PiO, k)
                         : cudaLaunchKernelEx(&cfg, lw_correct_split<false>, p, Phi, Pi, (const double2 *)PhiH,
@@ -699,7 +821,7 @@ __device__ __forceinline__ int batch_prologue(const JobDesc *jobs, const int *of
     return blockIdx.x - ldcg(off + jb);
 }
 
-__global__ void __launch_bounds__(1024) lw_predict_batch(const JobDesc *__restrict__ jobs,
+__global__ void __launch_bounds__(kTileMaxThreads) lw_predict_batch(const JobDesc *__restrict__ jobs,
                                                          const int *__restrict__ off, int njobs, int k, Ops ops)
 {
     extern __shared__ double2 smem[];
@@ -741,7 +863,7 @@ __global__ void __launch_bounds__(1024) lw_predict_batch(const JobDesc *__restri
     allow_dependents();
 }
 
-__global__ void __launch_bounds__(1024) lw_correct_batch(const JobDesc *__restrict__ jobs,
+__global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDesc *__restrict__ jobs,
                                                          const int *__restrict__ off, int njobs, int k, Ops ops)
 {
     extern __shared__ double2 smem[];

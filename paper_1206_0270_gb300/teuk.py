@@ -71,6 +71,8 @@ _SIGS = {
     "teuk_step_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_long]),
     "teuk_set_option": (C.c_int, [_vp, C.c_int, C.c_long]),
     "teuk_time_kernels": (C.c_int, [_vp, C.c_long, _dp]),
+    "teuk_fixed_dot": (C.c_int, [C.c_int, C.c_int, C.c_long, _dp, _dp, C.POINTER(C.c_uint), _dp,
+                                 C.POINTER(C.c_int)]),
     "teuk_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
     "teuk_batch_add": (C.c_int, [_vp, _vp, C.c_long, C.POINTER(C.c_int)]),
     "teuk_batch_remove": (C.c_int, [_vp, C.c_int]),
@@ -117,6 +119,27 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def fixed_dot(c, x, flip=None, device=False):
+    """Fixed-point sums of the Pi rows (teuk_fixed_dot): c, x of shape
+    (count, nterms) float64, flip the same shape (0/1, default 0).  Returns
+    (out float64 (count,), ok bool (count,)); device=True runs the device
+    build of the arithmetic."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if c.ndim != 2 or c.shape != x.shape:
+        raise ValueError("c and x must have the same shape (count, nterms)")
+    fl = np.zeros(c.shape, np.uint32) if flip is None else np.ascontiguousarray(flip, dtype=np.uint32)
+    if fl.shape != c.shape:
+        raise ValueError("flip must have the shape of c")
+    out = np.zeros(c.shape[0])
+    ok = np.zeros(c.shape[0], np.int32)
+    rc = teuk_fixed_dot(1 if device else 0, c.shape[1], c.shape[0], c.ctypes.data_as(_dp), x.ctypes.data_as(_dp),
+                        fl.ctypes.data_as(C.POINTER(C.c_uint)), out.ctypes.data_as(_dp),
+                        ok.ctypes.data_as(C.POINTER(C.c_int)))
+    _check(rc, None, "teuk_fixed_dot")
+    return out, ok.astype(bool)
 
 
 def stable_dt(nr, nth, rstar_min, rstar_max, a, s, m, c_r=0.5, c_theta=0.1):

@@ -1,0 +1,137 @@
+"""The fixed-point sums of the Pi rows (teuk_fixed_dot): the host build of
+the arithmetic the step kernels run, against exact rational arithmetic.
+
+Bound (stated in include/teuk.h): |out - exact| <= n 2^-57 max_k |c_k x_k|
++ 2^-53 |exact| wherever ok; ok is false only for non-finite inputs, results
+below 2^-823, or overflow.  The device build is compared with the host build
+bit for bit in the GPU test at the end."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+T = pytest.importorskip("paper_1206_0270_gb300.teuk", reason="libteuk.so not built")
+
+
+def exact_sum(c, x, flip):
+    return sum((-1 if f else 1) * Fraction(float(a)) * Fraction(float(b)) for a, b, f in zip(c, x, flip))
+
+
+def check_bound(c, x, flip, out, ok):
+    n = c.shape[1]
+    for i in range(c.shape[0]):
+        if not ok[i]:
+            continue
+        ex = exact_sum(c[i], x[i], flip[i])
+        mx = max(abs(Fraction(float(a)) * Fraction(float(b))) for a, b in zip(c[i], x[i]))
+        bound = n * Fraction(2) ** -57 * mx + abs(ex) * Fraction(2) ** -53
+        assert abs(Fraction(float(out[i])) - ex) <= bound, (i, c[i], x[i], flip[i], out[i], float(ex))
+
+
+def random_case(rng, count, n, kind):
+    c = rng.standard_normal((count, n)) * 10.0 ** rng.integers(-3, 3, (count, n))
+    x = rng.standard_normal((count, n)) * 10.0 ** rng.integers(-6, 6, (count, n))
+    flip = rng.integers(0, 2, (count, n)).astype(np.uint32)
+    if kind == "cancel" and n > 1:
+        # last term nearly cancels the others: the sum keeps only a few bits
+        sg = np.where(flip == 1, -1.0, 1.0)
+        part = np.sum(sg[:, :-1] * c[:, :-1] * x[:, :-1], axis=1)
+        x[:, -1] = -part / (sg[:, -1] * c[:, -1]) * (1 + 1e-12 * rng.standard_normal(count))
+    elif kind == "zeros":
+        x[rng.random((count, n)) < 0.4] = 0.0
+        c[rng.random((count, n)) < 0.2] = 0.0
+    elif kind == "wide":
+        x *= 10.0 ** rng.integers(-250, 250, (count, 1))
+        x *= 10.0 ** rng.integers(-30, 30, (count, n))
+    return c, x, flip
+
+
+@pytest.mark.parametrize("n", [1, 2, 6, 7, 9, 10, 16])
+@pytest.mark.parametrize("kind", ["plain", "cancel", "zeros", "wide"])
+def test_error_bound_against_exact_arithmetic(n, kind):
+    rng = np.random.default_rng(1000 * n + len(kind))
+    c, x, flip = random_case(rng, 400, n, kind)
+    out, ok = T.fixed_dot(c, x, flip)
+    assert ok.mean() > 0.9
+    check_bound(c, x, flip, out, ok)
+
+
+def test_subnormal_and_tiny_inputs():
+    rng = np.random.default_rng(7)
+    c = rng.standard_normal((300, 9))
+    x = rng.standard_normal((300, 9))
+    x[:100, :3] = 1e-310                      # subnormal fields beside normal ones
+    x[100:200] *= 1e-300                      # tiny results: FP64 fallback
+    x[200:, 4] = 5e-324
+    out, ok = T.fixed_dot(c, x)
+    assert ok[:100].all() and not ok[100:200].any()
+    check_bound(c, x, np.zeros_like(x, dtype=np.uint32), out, ok)
+
+
+def test_exact_results_ties_and_zero():
+    # exactly representable sums come out exactly
+    out, ok = T.fixed_dot(np.array([[3.0, 0.25, -7.0]]), np.array([[5.0, 8.0, 0.5]]))
+    assert ok[0] and out[0] == 15.0 + 2.0 - 3.5
+    # ties go to even: 1 + 2^-53 -> 1, 1 + 3 2^-53 -> 1 + 2^-51
+    out, ok = T.fixed_dot(np.array([[1.0, 2.0 ** -53], [1.0, 3 * 2.0 ** -53]]), np.ones((2, 2)))
+    assert ok.all() and out[0] == 1.0 and out[1] == 1.0 + 2.0 ** -51
+    # x - x = +0, all-zero sums are +0
+    out, ok = T.fixed_dot(np.array([[0.1, 0.1], [0.0, 0.0]]), np.array([[3.0, 3.0], [1.0, -2.0]]),
+                          np.array([[0, 1], [0, 0]]))
+    assert ok.all() and np.all(out == 0.0) and not np.signbit(out).any()
+    # a single product: the truncated low 47 bits of the 106-bit product do
+    # not reach the sticky bit, so a window that ends on an exact tie rounds
+    # to even where the exact product would round up (within the bound:
+    # 2^-57 + half an ulp); otherwise it is the correctly rounded product
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal(4000), rng.standard_normal(4000)
+    out, ok = T.fixed_dot(a[:, None], b[:, None])
+    assert ok.all() and np.mean(out == a * b) > 0.98
+    assert np.all(np.abs(out - a * b) <= np.spacing(np.abs(a * b)))
+
+
+def test_order_and_zero_terms_do_not_change_bits():
+    rng = np.random.default_rng(11)
+    c, x, flip = random_case(rng, 300, 9, "plain")
+    out, ok = T.fixed_dot(c, x, flip)
+    perm = rng.permutation(9)
+    out_p, ok_p = T.fixed_dot(c[:, perm], x[:, perm], flip[:, perm])
+    assert np.array_equal(ok, ok_p) and np.array_equal(out[ok], out_p[ok])
+    # interleave zero-coefficient terms with large fields (as the complex path
+    # does where the imaginary coefficient parts vanish)
+    cz = np.concatenate([c, np.zeros((300, 4))], axis=1)
+    xz = np.concatenate([x, 1e200 * rng.standard_normal((300, 4))], axis=1)
+    fz = np.concatenate([flip, np.ones((300, 4), np.uint32)], axis=1)
+    out_z, ok_z = T.fixed_dot(cz, xz, fz)
+    assert np.array_equal(ok, ok_z) and np.array_equal(out[ok], out_z[ok])
+
+
+def test_doubling_the_fields_doubles_the_sum_exactly():
+    rng = np.random.default_rng(5)
+    c, x, flip = random_case(rng, 300, 10, "cancel")
+    out, ok = T.fixed_dot(c, x, flip)
+    out2, ok2 = T.fixed_dot(c, 2.0 * x, flip)
+    both = ok & ok2
+    assert both.mean() > 0.9 and np.array_equal(out2[both], 2.0 * out[both])
+
+
+def test_fallback_conditions():
+    c = np.ones((4, 3))
+    x = np.array([[np.inf, 1.0, 1.0], [np.nan, 1.0, 1.0], [1e308, 1e308, 1e308], [1.0, 2.0, 3.0]])
+    c[2] = 10.0                              # 3e309 overflows
+    out, ok = T.fixed_dot(c, x)
+    assert list(ok) == [False, False, False, True] and out[3] == 6.0
+    with pytest.raises(T.TeukError):
+        T.fixed_dot(np.ones((2, 17)), np.ones((2, 17)))
+
+
+@pytest.mark.gpu
+def test_device_build_equals_host_build():
+    rng = np.random.default_rng(2026)
+    for n in (6, 7, 9, 10, 16):
+        for kind in ("plain", "cancel", "zeros", "wide"):
+            c, x, flip = random_case(rng, 20000, n, kind)
+            oh, kh = T.fixed_dot(c, x, flip, device=False)
+            od, kd = T.fixed_dot(c, x, flip, device=True)
+            assert np.array_equal(kh, kd)
+            assert np.array_equal(oh[kh].view(np.uint64), od[kd].view(np.uint64))

@@ -98,9 +98,9 @@ def test_parity_ragged_and_tiny(teuk, nr, nth):
 
 
 def test_parity_wide_theta_kernel_limits(teuk):
-    # nth = 512 is the widest fused block, 1024 the widest split tile; 1030
-    # runs the two-kernel variant.
-    for nth, kern in [(512, 0), (513, 2), (1024, 2), (1030, 1)]:
+    # nth = 256 is the widest fused block, 512 the widest split tile; wider
+    # rows run the two-kernel variant.
+    for nth, kern in [(256, 0), (257, 2), (512, 2), (513, 1), (1030, 1)]:
         out = run_pair(teuk, 40, nth, -10.0, 30.0, 0.9, -2, 2, 6, source=dict(r0=5.0, sigma=1.0), kernel=kern,
                        seed=1)
         assert_parity(out)
@@ -155,6 +155,16 @@ def test_kernel_variants_agree_bitwise(teuk):
         for x, y in zip(a["gpu"], b["gpu"]):
             np.testing.assert_array_equal(x, y)
         np.testing.assert_array_equal(a["gpu_w"][1], b["gpu_w"][1])
+    # rows cut into several theta tiles (halo sums from the neighbouring
+    # tiles): 2 tiles of 128, 3 tiles of 128 (the last one ragged), 4 of 128
+    for nth, fused in [(256, True), (300, False), (512, False)]:
+        kw = dict(source=dict(r0=5.0, sigma=1.0), ext=(0.0, 3), seed=nth)
+        a = run_pair(teuk, 40, nth, -10.0, 30.0, 0.9, -2, 2, 9, kernel=1, **kw)
+        for kern in (2, 0) if fused else (2,):
+            b = run_pair(teuk, 40, nth, -10.0, 30.0, 0.9, -2, 2, 9, kernel=kern, **kw)
+            for x, y in zip(a["gpu"], b["gpu"]):
+                np.testing.assert_array_equal(x, y)
+            np.testing.assert_array_equal(a["gpu_w"][1], b["gpu_w"][1])
 
 
 def test_launch_shapes_agree_bitwise(teuk):
@@ -187,7 +197,7 @@ def test_tuning_options_agree_bitwise(teuk):
     u = inputs.random_fields(nr, nth, seed=13)
     ref = None
     for pdl, chunk, rows in [(1, 64, 0), (0, 64, 0), (1, 2, 0), (1, 128, 0), (0, 6, 0), (1, 64, 1), (1, 6, 3),
-                             (0, 64, 16)]:
+                             (0, 64, 8)]:
         g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
         g.set_option(teuk.TEUK_OPT_PDL, pdl)
         g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, chunk)
@@ -209,13 +219,13 @@ def test_tuning_options_agree_bitwise(teuk):
     with pytest.raises(teuk.TeukError):
         g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, 3)
     with pytest.raises(teuk.TeukError):
-        g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, 17)   # 17 x 64 threads > 1024
+        g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, 9)    # 9 x 64 threads > 512
     with pytest.raises(teuk.TeukError):
         g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, -1)
     g.close()
 
 
-@pytest.mark.parametrize("nr,nth", [(40, 513), (20, 1024), (10, 96), (6, 32), (300, 128)])
+@pytest.mark.parametrize("nr,nth", [(40, 512), (20, 257), (10, 96), (6, 32), (300, 128), (20, 513)])
 def test_pdl_small_grids_match_plain_launches(teuk, nr, nth):
     # Few CTAs per kernel leave stale lines in the read-only cache if a kernel
     # launched with programmatic dependent launch read its predecessor's output
