@@ -36,7 +36,7 @@ WORKLOAD = "kerr_a0.9_s-2_m2_8192x128_r0_10"
 METRIC = "FP64 grid-pt updates/s"
 UNIT = "grid-pt updates/s"
 # FP64 work of one interior point update in the folded formulation of
-# Eqs. (3)-(4): 8 adds + 4 multiplies + 44 FMAs = 56 FP64 instructions = 100 flops;
+# Eqs. (3)-(4): 8 adds + 4 multiplies + 44 FMAs = 100 flops (algorithmic);
 # per kernel: predictor (one mid-point) 4 adds + 4 multiplies + 20 FMAs = 48 flops,
 # corrector (one node) 4 adds + 24 FMAs = 52 flops.
 FLOPS_PER_UPDATE = 100
@@ -46,10 +46,13 @@ FLOPS_CORRECTOR_POINT = 52
 BYTES_PER_UPDATE_ALG = 64
 # Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
 FP64_PEAK_FLOPS = 1.25e12
-# The same step as FP64 instructions: adds and multiplies are issued as FMAs,
-# so all 56 occupy the FP64 pipe like an FMA.  Measured issue rate of that
-# pipe on GB300 (FMA-chain probe): 1.906 per clock per SM.
-FP64_INSTR_PER_UPDATE = 56
+# How the kernels execute that work: the Phi rows and the sums tau, sigma on
+# the FP64 pipe (20 instructions per update, adds and multiplies issued as
+# FMAs), the Pi rows as fixed-point sums of 38 exact integer products per
+# update on the integer pipes.  Measured FP64 issue rate on GB300
+# (FMA-chain probe): 1.906 per clock per SM.
+FP64_INSTR_PER_UPDATE = 20
+FIXED_POINT_PRODUCTS_PER_UPDATE = 38
 FP64_FMA_PER_CLK_SM = 1.906
 NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
@@ -57,8 +60,9 @@ NUM_SMS = 152
 # sources whose SHA-256 is recorded here; reported as null otherwise.
 NCU_TRAFFIC = dict(predictor=125.85e6 + 14.82e6, corrector=151.02e6 + 19.06e6,
                    sources_sha256="8502b4c99c8be5c35d4ce2370b17f8f8f0be4c1b5c9dbb4ca9486d5005053fd4")
-TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu", "paper_1206_0270_gb300/csrc/teuk_internal.h",
-                   "paper_1206_0270_gb300/csrc/teuk_api.cu"]  # kernels, their layout, their launch
+TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu", "paper_1206_0270_gb300/csrc/teuk_fixed.h",
+                   "paper_1206_0270_gb300/csrc/teuk_internal.h",
+                   "paper_1206_0270_gb300/csrc/teuk_api.cu"]  # kernels, their arithmetic, layout, launch
 
 
 def sources_sha256():
@@ -277,7 +281,8 @@ def run_gpu(args):
     roofline = dict(bound="alu", achieved=achieved / 1e12, peak=FP64_PEAK_FLOPS / 1e12, unit="TFLOP/s",
                     frac=achieved / FP64_PEAK_FLOPS, traffic=NCU_TRAFFIC[key] if same_src else None,
                     kernel=dom, launch_ms=ms,
-                    peak_source="nominal FP64 (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz)",
+                    peak_source="nominal FP64 (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz); achieved counts the "
+                                "algorithmic FP64 flops, of which the Pi-row products run on the integer pipes",
                     kernels={k: dict(ms=v[1], tflops=v[0] / (v[1] / 1e3) / 1e12) for k, v in kern.items()},
                     step_in_graph=dict(ms=per_launch_s * 1e3,
                                        tflops=FLOPS_PER_UPDATE * upd_per_launch / per_launch_s / 1e12),
@@ -325,6 +330,8 @@ def run_gpu(args):
                 config=dict(workload=WORKLOAD, nr=nr, nth=nth, a=w["a"], s=w["s"], m=w["m"],
                             rstar=[w["rstar_min"], w["rstar_max"]], dt=dt, time_steps_per_step=args.chunk,
                             kernel="split predictor/corrector tiles, CUDA-graph replay",
+                            arithmetic="FP64; Pi-row sums as exact integer products in 64-bit fixed point, "
+                                       "rounded once to FP64 (error <= n 2^-57 max|c x| + 2^-53 |sum|)",
                             l2="inputs larger than L2 (state 2x33.5 MB + coefficients 193 MB per time step)",
                             parallelism="replicas" if ws > 1 else "single GPU"),
                 roofline=roofline, e2e=e2e, gpu_launches=int(launches),
@@ -335,6 +342,7 @@ def run_gpu(args):
         # FP64 pipe occupancy at the clock seen during the timed region
         pipe = NUM_SMS * FP64_FMA_PER_CLK_SM * clocks["sm_mhz"] * 1e6
         roofline["fp64_instr_per_update"] = FP64_INSTR_PER_UPDATE
+        roofline["fixed_point_products_per_update"] = FIXED_POINT_PRODUCTS_PER_UPDATE
         roofline["fp64_pipe_frac"] = FP64_INSTR_PER_UPDATE * upd_per_launch / per_launch_s / pipe
     if ws == 1 and not args.no_cpu_baseline:
         per = args.cpu_sample_steps
@@ -385,11 +393,12 @@ def run_batch_workload(args):
             dts[key] = T.stable_dt(j["nr"], j["nth"], rmin, rmax, j["a"], j["s"], j["m"])
         j["dt"] = dts[key]
 
-    def make_all():
+    def make_all(own_streams=False):
         out = []
         for j in jobs:
             dt = j["dt"]
-            g = T.Solver(j["nr"], j["nth"], rmin, rmax, dt, j["a"], j["s"], j["m"], stream=stream)
+            g = T.Solver(j["nr"], j["nth"], rmin, rmax, dt, j["a"], j["s"], j["m"],
+                         stream=None if own_streams else stream)
             g.set_source(r0=j["r0"], sigma=j["sigma"])
             g.set_extraction(ext["rstar"], ext["every"], capacity=j["steps"] // ext["every"] + 1)
             out.append(g)
@@ -408,13 +417,19 @@ def run_batch_workload(args):
     launches_single = sum(g.launches_for(j["steps"]) for g, j in zip(solvers, jobs))
     for g in solvers:
         g.close()
-    # batched: every job in one batch, CTA size autotuned on the jobs themselves
-    solvers = make_all()
+    # batched: every job in one batch (each job on its own stream, so that
+    # per-job launches can overlap), launch mode and CTA size autotuned on the
+    # jobs themselves
+    solvers = make_all(own_streams=True)
     B = T.Batch(stream=stream)
     for g, j in zip(solvers, jobs):
         B.add(g, j["steps"])
     t0 = time.perf_counter()
-    best = B.autotune()
+    if args.batch_mode == "auto":
+        best = B.autotune()
+    else:
+        B.set_option(T.TEUK_OPT_BATCH_MODE, int(args.batch_mode))
+        best = 0 if args.batch_mode == "1" else 128
     B.step(10 ** 9)
     B.sync()
     for g in solvers:
@@ -428,7 +443,8 @@ def run_batch_workload(args):
                 steps=1, warmup=0, ms_per_step=1e3 * t_batch, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=args.workload, jobs=n, steps_scale=args.steps_scale,
-                            point_updates=upd, block_threads=best),
+                            point_updates=upd, block_threads=best,
+                            batch_mode="per-job launches" if best == 0 else "one persistent launch per step"),
                 one_by_one=dict(value=n / t_single, unit="waveforms/s", seconds=t_single,
                                 gpu_launches=int(launches_single)),
                 batched=dict(seconds=t_batch, grid_pt_updates_per_s=upd / t_batch),
@@ -522,6 +538,8 @@ def main():
                          "waveforms/s against one job at a time")
     ap.add_argument("--steps-scale", type=float, default=0.2,
                     help="batched workloads: fraction of each job's step count that is run")
+    ap.add_argument("--batch-mode", default="auto", choices=["auto", "0", "1"],
+                    help="batch workloads: launch mode (autotuned by default)")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--slice", type=int, default=640, help="serving: time steps per batch slice")

@@ -175,7 +175,7 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  *     (default 64). */
 #define TEUK_OPT_PDL 1
 #define TEUK_OPT_GRAPH_CHUNK 2
-#define TEUK_OPT_BLOCK_THREADS 3  /* batches only: CTA threads, 0 = automatic */
+#define TEUK_OPT_BLOCK_THREADS 3  /* batches only: CTA threads, a multiple of 32 <= 512; 0 = automatic (128) */
 /* TEUK_OPT_REAL_PATH: 1 (default) stores real coefficient planes and uses
  * real-by-complex products when every coefficient is real (a = 0, or
  * s = m = 0: 44 instead of 56 FP64 instructions per point); 0 keeps the
@@ -185,6 +185,12 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  * (nth rounded up to a multiple of 32); 0 (default) picks 256 / that width,
  * at least 1.  A tile is one thread per point. */
 #define TEUK_OPT_SPLIT_ROWS 5
+/* TEUK_OPT_BATCH_MODE (batches only): 1 (default) advances every job with its
+ * own kernels on its own stream (graph replay per chunk), the jobs running
+ * concurrently; 0 advances all jobs with one persistent predictor and one
+ * corrector launch per step that work through a tile list of every job.
+ * Both give the same numbers as stepping each handle alone. */
+#define TEUK_OPT_BATCH_MODE 6
 int teuk_set_option(teuk_handle *h, int option, long value);
 
 /* Current fused-kernel launch shape. */
@@ -273,12 +279,16 @@ int teuk_batch_remaining(const teuk_batch *b, int job_id, long *remaining);
 /* Wait for the batch's queued work. */
 int teuk_batch_sync(teuk_batch *b);
 
-/* TEUK_OPT_PDL, TEUK_OPT_GRAPH_CHUNK or TEUK_OPT_BLOCK_THREADS. */
+/* TEUK_OPT_PDL, TEUK_OPT_GRAPH_CHUNK, TEUK_OPT_BLOCK_THREADS (persistent
+ * launch) or TEUK_OPT_BATCH_MODE. */
 int teuk_batch_set_option(teuk_batch *b, int option, long value);
 
-/* Time each candidate CTA size (128, 256, 512 threads; at least the widest
- * job's row) on the batch's own jobs -- the timed steps count as progress --
- * and keep the fastest; *best_block receives it.  Synchronises. */
+/* Time the persistent launch at each candidate CTA size (64, 128, 256
+ * threads; a job's rows are cut into theta tiles of at most the CTA width)
+ * and the per-job launches on the batch's own jobs -- the timed steps count
+ * as progress -- and keep the fastest; *best_block receives its CTA size, or
+ * 0 when per-job launches won (TEUK_OPT_BATCH_MODE is set accordingly).
+ * Synchronises. */
 int teuk_batch_autotune(teuk_batch *b, int *best_block);
 
 /* Kernel launches that teuk_batch_step(b, n) issues when no job finishes. */

@@ -515,10 +515,10 @@ static int capture_graph(teuk_handle *h, int from)
     return TEUK_OK;
 }
 
-extern "C" int teuk_step(teuk_handle *h, long n)
+// n steps on the handle's stream (graph replay per chunk); also used by
+// batches that run their jobs with per-job launches.
+int teuk_step_handle(teuk_handle *h, long n)
 {
-    if (!h || n < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_step: n < 0");
-    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_step: the handle belongs to a batch (remove it first)");
     while (n >= h->chunk) {
         if (!h->graph[h->variant][h->cur]) {
             int rc = capture_graph(h, h->cur);
@@ -537,6 +537,13 @@ extern "C" int teuk_step(teuk_handle *h, long n)
         h->nstep += n;
     }
     return TEUK_OK;
+}
+
+extern "C" int teuk_step(teuk_handle *h, long n)
+{
+    if (!h || n < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_step: n < 0");
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_step: the handle belongs to a batch (remove it first)");
+    return teuk_step_handle(h, n);
 }
 
 extern "C" int teuk_set_launch(teuk_handle *h, int rows_per_block)

@@ -29,7 +29,8 @@ struct teuk_batch {
     struct Job {
         teuk_handle *h = nullptr;
         long long remaining = 0;
-        bool member = false;  // still in the batch (not removed)
+        bool member = false;     // still in the batch (not removed)
+        cudaEvent_t done = nullptr;  // per-job launches: the job's slice has finished
     };
     std::vector<Job> jobs;
 
@@ -42,10 +43,13 @@ struct teuk_batch {
     int pred_tiles = 0, corr_tiles = 0;
     size_t smem = 0;
     int block = 0;          // CTA threads in use
+    int ctas = 0;           // persistent CTAs per launch (resident on all SMs)
     int block_request = 0;  // 0 = automatic
     bool layout_dirty = true;
     cudaGraphExec_t graph = nullptr;
     int pdl = 1, chunk = 64;
+    int mode = 1;                     // 0: one persistent launch for all jobs; 1: per-job launches
+    cudaEvent_t fork = nullptr;       // per-job launches: the slice may start
     std::string err;
 };
 
@@ -62,7 +66,6 @@ static int bfail(teuk_batch *b, int code, const std::string &msg)
             return bfail(b, TEUK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-static int colpad_of(int nth) { return ((nth + 31) / 32) * 32; }
 
 static void drop_graph(teuk_batch *b)
 {
@@ -101,6 +104,9 @@ extern "C" int teuk_batch_destroy(teuk_batch *b)
     for (auto &j : b->jobs)
         if (j.member) j.h->in_batch = 0;  // the handles are driven by their owner again
     drop_graph(b);
+    for (auto &j : b->jobs)
+        if (j.done) cudaEventDestroy(j.done);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_off) cudaFree(b->d_off);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -164,14 +170,11 @@ extern "C" int teuk_batch_sync(teuk_batch *b)
     return TEUK_OK;
 }
 
-// CTA size: at least 256 threads, at least the widest job's padded row.
+// CTA size: 128 threads unless requested otherwise.  A job's rows are cut
+// into theta tiles of at most the CTA width, so any CTA size fits any job.
 static int pick_block(const teuk_batch *b)
 {
-    int widest = 32;
-    for (int id : b->active) widest = std::max(widest, colpad_of(b->jobs[id].h->nth));
-    int blk = std::max(256, widest);
-    if (b->block_request >= widest) blk = b->block_request;
-    return std::min(blk, kTileMaxThreads);
+    return b->block_request ? b->block_request : 128;
 }
 
 // Rebuild the job table and tile offsets for the jobs with steps left.
@@ -212,19 +215,25 @@ static int rebuild(teuk_batch *b)
         d.pi[0] = h->pi[0]; d.pi[1] = h->pi[1];
         d.phiH = h->phiH; d.piH = h->piH;
         d.cur = h->cur;
-        d.colpad = colpad_of(h->nth);
-        d.rows = std::max(1, b->block / d.colpad);
-        const int pt = (h->nr - 1 + d.rows - 1) / d.rows, ct = (h->nr - 2 + d.rows - 1) / d.rows;
+        d.tw = tile_width_for(h->nth, b->block);
+        d.rows = std::max(1, b->block / d.tw);
+        d.tiles = (h->nth + d.tw - 1) / d.tw;
+        const int pt = (h->nr - 1 + d.rows - 1) / d.rows * d.tiles, ct = (h->nr - 2 + d.rows - 1) / d.rows * d.tiles;
         poff[q + 1] = poff[q] + pt;
         coff[q + 1] = coff[q] + ct;
-        smem = std::max(smem, batch_smem_bytes(b->block, d.rows, h->nth));
     }
     b->pred_tiles = poff[nj];
     b->corr_tiles = coff[nj];
+    smem = batch_smem_bytes(b->block);
     b->smem = smem;
-    if (smem > 48 * 1024)
-        for (int w = 0; w < 2; ++w)
-            BCU(cudaFuncSetAttribute(batch_kernel_ptr(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int sms = 0, per_sm = 0;
+    BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    for (int w = 0; w < 2; ++w) {
+        int n = 0;
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel_ptr(w), b->block, smem));
+        per_sm = w == 0 ? n : std::min(per_sm, n);
+    }
+    b->ctas = std::max(1, sms * std::max(1, per_sm));
     BCU(cudaMemcpyAsync(b->d_jobs, b->host_desc.data(), nj * sizeof(JobDesc), cudaMemcpyHostToDevice, b->stream));
     BCU(cudaMemcpyAsync(b->d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     b->layout_dirty = false;
@@ -248,7 +257,7 @@ static cudaError_t launch_batch_steps(teuk_batch *b, int k0, int n, cudaStream_t
     const int nj = (int)b->active.size();
     for (int k = k0; k < k0 + n; ++k) {
         cudaError_t e = launch_step_batch(b->d_jobs, b->d_off, b->d_off + (b->cap_jobs + 1), nj, b->pred_tiles,
-                                          b->corr_tiles, b->block, b->smem, 1.0, -0.0, k, st,
+                                          b->corr_tiles, b->block, b->smem, b->ctas, 1.0, -0.0, k, st,
                                           b->pdl != 0 && k > k0, b->pdl != 0);
         if (e != cudaSuccess) return e;
     }
@@ -271,6 +280,68 @@ static int capture(teuk_batch *b)
     return TEUK_OK;
 }
 
+// Per-job launches: every job advances min(L, its remaining steps) on its
+// own stream with its own kernels (graph replay per chunk), the jobs running
+// concurrently; the batch stream first releases and then waits for all of
+// them.  Returns the largest advance.
+static int per_job_slice(teuk_batch *b, long long L, long long *advanced)
+{
+    if (!b->fork) BCU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    BCU(cudaEventRecord(b->fork, b->stream));
+    long long most = 0;
+    for (int id : b->active) {
+        auto &j = b->jobs[id];
+        const long long n = std::min(L, j.remaining);
+        if (!j.done) BCU(cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming));
+        BCU(cudaStreamWaitEvent(j.h->stream, b->fork, 0));
+        const int rc = teuk_step_handle(j.h, (long)n);
+        if (rc) return bfail(b, rc, "batch: " + j.h->err);
+        BCU(cudaEventRecord(j.done, j.h->stream));
+        BCU(cudaStreamWaitEvent(b->stream, j.done, 0));
+        j.remaining -= n;
+        if (j.remaining == 0 || (n & 1)) b->layout_dirty = true;  // leaves, or the table's buffer parity is stale
+        most = std::max(most, n);
+    }
+    *advanced = most;
+    return TEUK_OK;
+}
+
+// One slice of L steps for the active jobs in the current mode (per-job
+// launches: each job advances up to L steps).
+static int run_slice(teuk_batch *b, long long L)
+{
+    if (b->mode == 1) {
+        long long adv = 0;
+        return per_job_slice(b, L, &adv);
+    } else {
+        if (L == b->chunk) {
+            if (!b->graph) {
+                int rc = capture(b);
+                if (rc) return rc;
+            }
+            BCU(cudaGraphLaunch(b->graph, b->stream));
+        } else {
+            BCU(launch_batch_steps(b, 0, (int)L, b->stream));
+        }
+        for (int id : b->active) {
+            b->jobs[id].h->nstep += L;
+            b->jobs[id].h->cur ^= (int)(L & 1);
+        }
+    }
+    bool finished = false;
+    for (int id : b->active) {
+        b->jobs[id].remaining -= L;
+        finished |= b->jobs[id].remaining == 0;
+    }
+    if (finished) {
+        b->layout_dirty = true;  // finished jobs leave at this slice boundary
+    } else if (b->mode == 0 && (L & 1)) {
+        int rc = refresh_cur(b);
+        if (rc) return rc;
+    }
+    return TEUK_OK;
+}
+
 extern "C" int teuk_batch_step(teuk_batch *b, long max_steps, long *steps_done)
 {
     if (!b || max_steps < 0) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_step: bad argument");
@@ -281,31 +352,17 @@ extern "C" int teuk_batch_step(teuk_batch *b, long max_steps, long *steps_done)
             if (rc) return rc;
         }
         if (b->active.empty()) break;
+        if (b->mode == 1) {  // jobs advance independently: no common slices
+            long long adv = 0;
+            int rc = per_job_slice(b, max_steps - done, &adv);
+            if (rc) return rc;
+            done += (long)adv;
+            break;
+        }
         long long L = std::min<long long>(b->chunk, max_steps - done);
         for (int id : b->active) L = std::min(L, b->jobs[id].remaining);
-        if (L == b->chunk) {
-            if (!b->graph) {
-                int rc = capture(b);
-                if (rc) return rc;
-            }
-            BCU(cudaGraphLaunch(b->graph, b->stream));
-        } else {
-            BCU(launch_batch_steps(b, 0, (int)L, b->stream));
-        }
-        bool finished = false;
-        for (int id : b->active) {
-            auto &j = b->jobs[id];
-            j.h->nstep += L;
-            j.h->cur ^= (int)(L & 1);
-            j.remaining -= L;
-            finished |= j.remaining == 0;
-        }
-        if (finished) {
-            b->layout_dirty = true;  // finished jobs leave at this slice boundary
-        } else if (L & 1) {
-            int rc = refresh_cur(b);
-            if (rc) return rc;
-        }
+        int rc = run_slice(b, L);
+        if (rc) return rc;
         done += (long)L;
     }
     if (steps_done) *steps_done = done;
@@ -325,6 +382,12 @@ extern "C" int teuk_batch_set_option(teuk_batch *b, int option, long value)
         if (value < 2 || value > 4096 || value % 2)
             return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: graph chunk must be even, 2..4096");
         b->chunk = (int)value;
+        break;
+    case TEUK_OPT_BATCH_MODE:
+        if (value != 0 && value != 1) return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: batch mode is 0 or 1");
+        BCU(cudaStreamSynchronize(b->stream));
+        b->mode = (int)value;
+        b->layout_dirty = true;
         break;
     case TEUK_OPT_BLOCK_THREADS:
         if (value != 0 && (value < 32 || value > kTileMaxThreads || value % 32))
@@ -347,52 +410,75 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best_block)
         if (rc) return rc;
     }
     if (b->active.empty()) return bfail(b, TEUK_ERR_STATE, "teuk_batch_autotune: no job has steps left");
-    int widest = 32;
-    for (int id : b->active) widest = std::max(widest, colpad_of(b->jobs[id].h->nth));
-    const int cands[] = {128, 256, 512};
+    // per-job launches, then the persistent launch at three CTA sizes; each
+    // candidate gets an equal share of the steps the shortest job has left
+    const int cands[][2] = {{1, 0}, {0, 64}, {0, 128}, {0, 256}};
+    const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
+    long long share = 1LL << 62;
+    for (int id : b->active) share = std::min(share, b->jobs[id].remaining / ncand);
     cudaEvent_t e0, e1;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));
-    int best = 0;
+    int best_mode = b->mode, best = b->block_request;
     double best_rate = -1.0;
-    const int saved = b->block_request;
-    for (int c : cands) {
-        if (c < widest) continue;
+    for (const auto &c : cands) {
+        if (b->layout_dirty) {
+            int rc = rebuild(b);
+            if (rc) return rc;
+        }
         long long pts = 0, minrem = 1LL << 62;
         for (int id : b->active) minrem = std::min(minrem, b->jobs[id].remaining);
-        if (minrem < 2) break;
-        b->block_request = c;
+        const long long budget = std::min(share, minrem) & ~1LL;
+        if (b->active.empty() || budget < 8) break;
+        b->mode = c[0];
+        if (c[0] == 0) b->block_request = c[1];
         b->layout_dirty = true;
         int rc = rebuild(b);
         if (rc) return rc;
         for (int id : b->active) pts += (long long)(b->jobs[id].h->nr - 2) * b->jobs[id].h->nth;
-        const long n = (long)std::min<long long>(minrem, 2 * b->chunk) & ~1L;
-        BCU(launch_batch_steps(b, 0, 2, b->stream));  // warm-up, counted as progress
+        // warm-up of up to one chunk (captures the graphs it replays), then
+        // the timed steps; both count as progress
+        const long long warm = std::min<long long>(b->chunk, budget / 2) & ~1LL;
+        const long long n = std::min<long long>(2 * b->chunk, budget - warm) & ~1LL;
+        rc = run_slice(b, warm);
+        if (rc) return rc;
         BCU(cudaEventRecord(e0, b->stream));
-        BCU(launch_batch_steps(b, 0, (int)n - 2, b->stream));
+        for (long long left = n; left > 0;) {  // whole chunks replay the captured graphs
+            const long long L = std::min<long long>(left, b->chunk);
+            rc = run_slice(b, L);
+            if (rc) return rc;
+            left -= L;
+        }
         BCU(cudaEventRecord(e1, b->stream));
         BCU(cudaEventSynchronize(e1));
         float ms = 0;
         BCU(cudaEventElapsedTime(&ms, e0, e1));
-        for (int id : b->active) {
-            b->jobs[id].h->nstep += n;
-            b->jobs[id].remaining -= n;
+        const double rate = (double)pts * (double)n / (ms > 0 ? ms : 1e-3);
+        if (rate > best_rate) {
+            best_rate = rate;
+            best_mode = c[0];
+            best = c[0] == 0 ? c[1] : b->block_request;
         }
-        const double rate = (double)pts * (n - 2) / (ms > 0 ? ms : 1e-3);
-        if (rate > best_rate) { best_rate = rate; best = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->block_request = best ? best : saved;
+    b->mode = best_mode;
+    b->block_request = best;
     b->layout_dirty = true;
-    if (best_block) *best_block = best;
+    if (best_block) *best_block = best_mode == 0 ? best : 0;
     return TEUK_OK;
 }
 
 extern "C" long teuk_batch_launches_for(const teuk_batch *b, long n)
 {
-    // each step is two launches, each slice adds one counter update
     if (!b || n < 0) return -1;
+    if (b->mode == 1) {  // every job launches its own kernels
+        long total = 0;
+        for (const auto &j : b->jobs)
+            if (j.member && j.remaining > 0) total += teuk_launches_for(j.h, n);
+        return total;
+    }
+    // each step is two launches, each slice adds one counter update
     const long slices = (n + b->chunk - 1) / b->chunk;
     return 2 * n + slices;
 }

@@ -38,3 +38,8 @@ struct teuk_handle {
     cudaGraphExec_t graph[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     std::string err;
 };
+
+// n steps on the handle's own stream, without the batch-membership check
+// (teuk_step checks, then calls this; batches call it for their jobs).
+int teuk_step_handle(teuk_handle *h, long n);
+

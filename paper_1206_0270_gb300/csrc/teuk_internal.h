@@ -96,9 +96,9 @@ struct JobDesc {
     double2 *phi[2], *pi[2];  // state, ping-pong
     double2 *phiH, *piH;      // half step
     int cur;                  // buffer holding the state at the start of the slice
-    int rows;                 // rows per tile
-    int colpad;
-    int pad_;
+    int rows;                 // r* rows per tile
+    int tw;                   // theta columns per tile (a multiple of 32)
+    int tiles;                // theta tiles per row
 };
 
 // ---------------------------------------------------------------------------
@@ -146,13 +146,16 @@ cudaError_t launch_zero_boundary_rows(double2 *Phi, double2 *Pi, int nr, int nth
 cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long long npts,
                                    unsigned long long *count, cudaStream_t st);
 
+// Persistent batch kernels: `ctas` CTAs of `block` threads work through the
+// tiles of all jobs (min(ctas, tiles) CTAs per launch).
 cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const int *corr_off, int njobs,
-                              int pred_tiles, int corr_tiles, int block, size_t smem, double one, double nzero,
-                              int k, cudaStream_t st, bool pdl_pred, bool pdl_corr);
+                              int pred_tiles, int corr_tiles, int block, size_t smem, int ctas, double one,
+                              double nzero, int k, cudaStream_t st, bool pdl_pred, bool pdl_corr);
 
 cudaError_t launch_advance_batch(const JobDesc *jobs, int njobs, long long by, cudaStream_t st);
 
-size_t batch_smem_bytes(int block, int rows, int nth);
+size_t batch_smem_bytes(int block);
+int tile_width_for(int nth, int max_width);
 const void *batch_kernel_ptr(int which);
 
 int fused_block_threads(int nth);

@@ -17,6 +17,8 @@
 #include "teuk_physics.h"
 #include "teuk_fixed.h"
 
+#include <algorithm>
+
 namespace teuk {
 
 // ---------------------------------------------------------------------------
@@ -614,12 +616,17 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
 // tile forms its two halo sums sigma(j0 - 1) and sigma(j0 + TW) itself.
 // Small CTAs keep several tiles resident per SM (the fixed-point Pi rows need
 // up to 128 registers per thread).
-int split_tile_width(int nth)
+#ifndef TEUK_SPLIT_TILE_MAX
+#define TEUK_SPLIT_TILE_MAX 128
+#endif
+// Width of equal theta tiles of at most max_width columns (a multiple of 32).
+int tile_width_for(int nth, int max_width)
 {
     const int cols = fused_block_threads(nth);
-    const int tiles = (cols + 127) / 128;
+    const int tiles = (cols + max_width - 1) / max_width;
     return (((nth + tiles - 1) / tiles) + 31) / 32 * 32;
 }
+int split_tile_width(int nth) { return tile_width_for(nth, TEUK_SPLIT_TILE_MAX); }
 int split_theta_tiles(int nth)
 {
     const int tw = split_tile_width(nth);
@@ -628,7 +635,7 @@ int split_theta_tiles(int nth)
 int split_rows_per_block(int nth)
 {
     const int tw = split_tile_width(nth);
-    return tw >= 128 ? 1 : 128 / tw;
+    return tw >= TEUK_SPLIT_TILE_MAX ? 1 : TEUK_SPLIT_TILE_MAX / tw;
 }
 
 // Launch bounds of the split kernels.  The single-argument form leaves ptxas
@@ -789,11 +796,6 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
 
 // Dynamic shared memory of a batch CTA: the job descriptor, then `rows` rows
 // of nth + 2 sums.
-size_t batch_smem_bytes(int block, int rows, int nth)
-{
-    (void)block;
-    return ((sizeof(JobDesc) + 15) / 16) * 16 + sizeof(double2) * (size_t)rows * (nth + 2);
-}
 
 // Largest j < njobs with off[j] <= b (off is increasing, off[0] = 0).
 __device__ __forceinline__ int find_job(const int *off, int njobs, int b)
@@ -806,123 +808,214 @@ __device__ __forceinline__ int find_job(const int *off, int njobs, int b)
     return lo;
 }
 
-// Copy the CTA's job descriptor to shared memory (through L2: the host
-// rewrites the table between slices) and return the tile index.
-__device__ __forceinline__ int batch_prologue(const JobDesc *jobs, const int *off, int njobs, JobDesc *sj)
+// The batch kernels are persistent: a fixed grid of CTAs, CTA c working
+// through tiles [c T / G, (c + 1) T / G) in order.  A CTA copies a job's
+// descriptor to shared memory (through L2: the host rewrites the table
+// between slices) only when its range enters the next job, and alternates
+// two sigma-row buffers so that each tile needs one barrier.
+struct BatchCursor {
+    int jb = -1, beg = 0, end = 0;  // current job and its tile range
+    int rb = 0, tt = 0;             // r* row block and theta tile of the current tile
+    int tx = 0, ty = 0;             // this thread's column and row within a tile
+};
+
+__device__ __forceinline__ void batch_enter(const JobDesc *jobs, const int *off, int njobs, int tile,
+                                            BatchCursor &cur, JobDesc *sj)
 {
-    __shared__ int s_job;
-    if (threadIdx.x == 0) s_job = find_job(off, njobs, blockIdx.x);
-    __syncthreads();
-    const int jb = s_job;
+    if (tile < cur.end) return;  // uniform over the CTA
+    __syncthreads();             // every thread is done with the previous descriptor
+    int jb = cur.jb < 0 ? find_job(off, njobs, tile) : cur.jb + 1;
+    while (jb + 1 < njobs && ldcg(off + jb + 1) <= tile) ++jb;
     const unsigned long long *src = (const unsigned long long *)(jobs + jb);
     unsigned long long *dst = (unsigned long long *)sj;
     for (int w = threadIdx.x; w < (int)(sizeof(JobDesc) / 8); w += blockDim.x) dst[w] = ldcg(src + w);
+    cur.jb = jb;
+    cur.beg = ldcg(off + jb);
+    cur.end = ldcg(off + jb + 1);
+    // the tile geometry of the job, read from the table (the copy is not yet visible)
+    const int tw = ldcg(&jobs[jb].tw), tiles = ldcg(&jobs[jb].tiles);
+    cur.ty = threadIdx.x / tw;
+    cur.tx = threadIdx.x - cur.ty * tw;
+    cur.rb = (tile - cur.beg) / tiles;
+    cur.tt = tile - cur.beg - cur.rb * tiles;
     __syncthreads();
-    return blockIdx.x - ldcg(off + jb);
 }
 
+// Move the cursor to the next tile of the same job (the caller re-enters
+// when it leaves the job).
+__device__ __forceinline__ void batch_next(const JobDesc &J, BatchCursor &cur)
+{
+    if (++cur.tt == J.tiles) {
+        cur.tt = 0;
+        ++cur.rb;
+    }
+}
+
+// Tile of the current job at the cursor: theta columns from j0 = tt tw;
+// threads past the job's rows only join the barrier.
+struct BatchTile {
+    int tx, tyc, j0, j, jj, rb;
+    bool slot, colok;
+};
+
+__device__ __forceinline__ BatchTile batch_tile(const JobDesc &J, const BatchCursor &cur)
+{
+    BatchTile t;
+    const int R = J.rows;
+    t.rb = cur.rb;
+    t.j0 = cur.tt * J.tw;
+    t.tx = cur.tx;
+    t.slot = cur.ty < R;
+    t.tyc = t.slot ? cur.ty : R - 1;
+    t.j = t.j0 + t.tx;
+    t.colok = t.slot && t.j < J.p.nth;
+    t.jj = t.j < J.p.nth ? t.j : J.p.nth - 1;
+    return t;
+}
+
+#ifndef TEUK_BATCH_REAL_BRANCH
+#define TEUK_BATCH_REAL_BRANCH 1
+#endif
+
+// Row buffer words (double2) per buffer for a CTA of `block` threads: R rows
+// of tw + 2 with R tw <= block and R <= block / 32.
+__host__ __device__ __forceinline__ int batch_row_words(int block) { return block + 2 * (block / 32); }
+
 __global__ void __launch_bounds__(kTileMaxThreads) lw_predict_batch(const JobDesc *__restrict__ jobs,
-                                                         const int *__restrict__ off, int njobs, int k, Ops ops)
+                                                                     const int *__restrict__ off, int njobs,
+                                                                     int ntiles, int k, Ops ops)
 {
     extern __shared__ double2 smem[];
     JobDesc &J = *(JobDesc *)smem;
-    double2 *rows = smem + (sizeof(JobDesc) + 15) / 16;
-    const int tile = batch_prologue(jobs, off, njobs, &J);
-    const StepParams &p = J.p;
-    const int nth = p.nth, W = nth + 2, colpad = J.colpad, R = J.rows;
-    const int ty = threadIdx.x / colpad, j = threadIdx.x - ty * colpad;
-    const bool slot = ty < R;                 // threads past R rows only join the barrier
-    const int tyc = slot ? ty : R - 1;
-    const bool colok = slot && j < nth;
-    const int jj = j < nth ? j : nth - 1;
-    const int hp = tile * R + tyc;
-    const bool rowok = slot && hp < p.nr - 1;
-    const int hq = min(hp, p.nr - 2);
-    double2 *row = rows + tyc * W;
-    if (slot && j < 2) row[j == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
-    const size_t k0 = (size_t)hq * nth + jj;
-    const bool real = p.real_coef != 0;  // uniform over the CTA
-    const PredCoef c = real ? load_pred<true>(p, k0) : load_pred<false>(p, k0);
-    grid_dependency_wait();
-    const int from = J.cur ^ (k & 1);
-    const double2 *Phi = J.phi[from], *Pi = J.pi[from];
-    const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth), pi1 = ldcg(Pi + k0 + nth);
-    if (colok) row[j + 1] = add2(phi0, phi1, ops);
-    __syncthreads();
-    HalfStep o = real ? predict_c<true>(c, p.q, ops, phi0, pi0, phi1, pi1, row[jj + 2], row[jj])
-                      : predict_c<false>(c, p.q, ops, phi0, pi0, phi1, pi1, row[jj + 2], row[jj]);
-    const SourceWindow &sw = p.src;
-    if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
-        const long long n = ldcg(p.step_base) + k;
-        rfma(o.pi, ldg(sw.gP + (size_t)(hq - sw.mid_lo) * nth + jj), unit_phase(sw.m_omega * ((double)n * p.dt)));
+    double2 *rowbuf = smem + (sizeof(JobDesc) + 15) / 16;
+    const int bw = batch_row_words(blockDim.x);
+    const int t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
+    BatchCursor cur;
+    for (int tile = t0; tile < t1; ++tile) {
+        batch_enter(jobs, off, njobs, tile, cur, &J);
+        const BatchTile t = batch_tile(J, cur);
+        const StepParams &p = J.p;
+        const int nth = p.nth, tw = J.tw;
+        const int hp = t.rb * J.rows + t.tyc;
+        const bool rowok = t.slot && hp < p.nr - 1;
+        const int hq = min(hp, p.nr - 2);
+        double2 *row = rowbuf + (tile & 1) * bw + t.tyc * (tw + 2);
+        const size_t k0 = (size_t)hq * nth + t.jj;
+        const bool real = TEUK_BATCH_REAL_BRANCH && p.real_coef != 0;  // uniform over the CTA
+        const PredCoef c = real ? load_pred<true>(p, k0) : load_pred<false>(p, k0);
+        if (tile == t0) grid_dependency_wait();
+        const int from = J.cur ^ (k & 1);
+        const double2 *Phi = J.phi[from], *Pi = J.pi[from];
+        const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth),
+                      pi1 = ldcg(Pi + k0 + nth);
+        if (t.slot) {
+            row[t.tx + 1] = t.colok ? add2(phi0, phi1, ops) : make_double2(0.0, 0.0);
+            const size_t kr = (size_t)hq * nth;
+            if (t.tx == 0)
+                row[0] = t.j0 > 0 ? add2(ldcg(Phi + kr + t.j0 - 1), ldcg(Phi + kr + nth + t.j0 - 1), ops)
+                                  : make_double2(0.0, 0.0);
+            if (t.tx == tw - 1)
+                row[tw + 1] = t.j0 + tw < nth
+                                  ? add2(ldcg(Phi + kr + t.j0 + tw), ldcg(Phi + kr + nth + t.j0 + tw), ops)
+                                  : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        HalfStep o = real ? predict_c<true>(c, p.q, ops, phi0, pi0, phi1, pi1, row[t.tx + 2], row[t.tx])
+                          : predict_c<false>(c, p.q, ops, phi0, pi0, phi1, pi1, row[t.tx + 2], row[t.tx]);
+        const SourceWindow &sw = p.src;
+        if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
+            const long long n = ldcg(p.step_base) + k;
+            rfma(o.pi, ldg(sw.gP + (size_t)(hq - sw.mid_lo) * nth + t.jj),
+                 unit_phase(sw.m_omega * ((double)n * p.dt)));
+        }
+        if (t.colok && rowok) {
+            J.phiH[k0] = o.phi;
+            J.piH[k0] = o.pi;
+        }
+        batch_next(J, cur);
     }
-    if (colok && rowok) {
-        J.phiH[k0] = o.phi;
-        J.piH[k0] = o.pi;
-    }
-    allow_dependents();
+    allow_dependents();  // after the CTA's last store
 }
 
 __global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDesc *__restrict__ jobs,
-                                                         const int *__restrict__ off, int njobs, int k, Ops ops)
+                                                                     const int *__restrict__ off, int njobs,
+                                                                     int ntiles, int k, Ops ops)
 {
     extern __shared__ double2 smem[];
     JobDesc &J = *(JobDesc *)smem;
-    double2 *rows = smem + (sizeof(JobDesc) + 15) / 16;
-    const int tile = batch_prologue(jobs, off, njobs, &J);
-    const StepParams &p = J.p;
-    const int nth = p.nth, W = nth + 2, colpad = J.colpad, R = J.rows;
-    const int ty = threadIdx.x / colpad, j = threadIdx.x - ty * colpad;
-    const bool slot = ty < R;
-    const int tyc = slot ? ty : R - 1;
-    const bool colok = slot && j < nth;
-    const int jj = j < nth ? j : nth - 1;
-    const int i = 1 + tile * R + tyc;
-    const bool rowok = slot && i <= p.nr - 2;
-    const int iq = min(i, p.nr - 2);
-    double2 *row = rows + tyc * W;
-    if (slot && j < 2) row[j == 0 ? 0 : nth + 1] = make_double2(0.0, 0.0);
-    const size_t kc = (size_t)iq * nth + jj;
-    const bool real = p.real_coef != 0;
-    const CorrCoef c = real ? load_corr<true>(p, kc) : load_corr<false>(p, kc);
-    grid_dependency_wait();
-    const int from = J.cur ^ (k & 1);
-    const double2 *Phi = J.phi[from], *Pi = J.pi[from];
-    double2 *PhiO = J.phi[1 - from], *PiO = J.pi[1 - from];
-    HalfStep hp, hm;
-    hp.phi = ldcg(J.phiH + kc);
-    hp.pi = ldcg(J.piH + kc);
-    hm.phi = ldcg(J.phiH + kc - nth);
-    hm.pi = ldcg(J.piH + kc - nth);
-    const double2 phi = ldcg(Phi + kc), pi = ldcg(Pi + kc);
-    if (colok) row[j + 1] = add2(hp.phi, hm.phi, ops);
-    __syncthreads();
-    double2 nphi, npi;
-    if (real)
-        correct_c<true>(c, p.half_dt, ops, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
-    else
-        correct_c<false>(c, p.half_dt, ops, phi, pi, hp, hm, row[jj + 2], row[jj], &nphi, &npi);
-    const long long n = ldcg(p.step_base) + k;
-    const SourceWindow &sw = p.src;
-    if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
-        rfma(npi, ldg(sw.gC + (size_t)(iq - sw.node_lo) * nth + jj),
-             unit_phase(sw.m_omega * (((double)n + 0.5) * p.dt)));
-    if (colok && rowok) {
-        PhiO[kc] = nphi;
-        PiO[kc] = npi;
-        if (iq == p.ext.i_ext && ((n + 1) % p.ext.every) == 0) {
-            const long long slot_k = ((n + 1) / p.ext.every - 1) % p.ext.capacity;
-            p.ext.ring[(size_t)slot_k * nth + j] = nphi;
+    double2 *rowbuf = smem + (sizeof(JobDesc) + 15) / 16;
+    const int bw = batch_row_words(blockDim.x);
+    const int t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
+    BatchCursor cur;
+    for (int tile = t0; tile < t1; ++tile) {
+        batch_enter(jobs, off, njobs, tile, cur, &J);
+        const BatchTile t = batch_tile(J, cur);
+        const StepParams &p = J.p;
+        const int nth = p.nth, tw = J.tw;
+        const int i = 1 + t.rb * J.rows + t.tyc;
+        const bool rowok = t.slot && i <= p.nr - 2;
+        const int iq = min(i, p.nr - 2);
+        double2 *row = rowbuf + (tile & 1) * bw + t.tyc * (tw + 2);
+        const size_t kc = (size_t)iq * nth + t.jj;
+        const bool real = TEUK_BATCH_REAL_BRANCH && p.real_coef != 0;
+        const CorrCoef c = real ? load_corr<true>(p, kc) : load_corr<false>(p, kc);
+        if (tile == t0) grid_dependency_wait();
+        const int from = J.cur ^ (k & 1);
+        const double2 *Phi = J.phi[from], *Pi = J.pi[from];
+        double2 *PhiO = J.phi[1 - from], *PiO = J.pi[1 - from];
+        HalfStep hp, hm;
+        hp.phi = ldcg(J.phiH + kc);
+        hp.pi = ldcg(J.piH + kc);
+        hm.phi = ldcg(J.phiH + kc - nth);
+        hm.pi = ldcg(J.piH + kc - nth);
+        const double2 phi = ldcg(Phi + kc), pi = ldcg(Pi + kc);
+        if (t.slot) {
+            row[t.tx + 1] = t.colok ? add2(hp.phi, hm.phi, ops) : make_double2(0.0, 0.0);
+            const size_t kr = (size_t)iq * nth;
+            if (t.tx == 0)
+                row[0] = t.j0 > 0 ? add2(ldcg(J.phiH + kr + t.j0 - 1), ldcg(J.phiH + kr - nth + t.j0 - 1), ops)
+                                  : make_double2(0.0, 0.0);
+            if (t.tx == tw - 1)
+                row[tw + 1] = t.j0 + tw < nth
+                                  ? add2(ldcg(J.phiH + kr + t.j0 + tw), ldcg(J.phiH + kr - nth + t.j0 + tw), ops)
+                                  : make_double2(0.0, 0.0);
         }
+        __syncthreads();
+        double2 nphi, npi;
+        if (real)
+            correct_c<true>(c, p.half_dt, ops, phi, pi, hp, hm, row[t.tx + 2], row[t.tx], &nphi, &npi);
+        else
+            correct_c<false>(c, p.half_dt, ops, phi, pi, hp, hm, row[t.tx + 2], row[t.tx], &nphi, &npi);
+        const long long n = ldcg(p.step_base) + k;
+        const SourceWindow &sw = p.src;
+        if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
+            rfma(npi, ldg(sw.gC + (size_t)(iq - sw.node_lo) * nth + t.jj),
+                 unit_phase(sw.m_omega * (((double)n + 0.5) * p.dt)));
+        if (t.colok && rowok) {
+            PhiO[kc] = nphi;
+            PiO[kc] = npi;
+            if (iq == p.ext.i_ext && ((n + 1) % p.ext.every) == 0) {
+                const long long slot_k = ((n + 1) / p.ext.every - 1) % p.ext.capacity;
+                p.ext.ring[(size_t)slot_k * nth + t.j] = nphi;
+            }
+        }
+        batch_next(J, cur);
     }
     allow_dependents();
 }
 
 const void *batch_kernel_ptr(int which) { return which ? (const void *)lw_correct_batch : (const void *)lw_predict_batch; }
 
+size_t batch_smem_bytes(int block)
+{
+    return ((sizeof(JobDesc) + 15) / 16) * 16 + 2 * sizeof(double2) * (size_t)batch_row_words(block);
+}
+
 cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const int *corr_off, int njobs,
-                              int pred_tiles, int corr_tiles, int block, size_t smem, double one, double nzero,
-                              int k, cudaStream_t st, bool pdl_pred, bool pdl_corr)
+                              int pred_tiles, int corr_tiles, int block, size_t smem, int ctas, double one,
+                              double nzero, int k, cudaStream_t st, bool pdl_pred, bool pdl_corr)
 {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -934,13 +1027,13 @@ cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const in
     cfg.attrs = pdl_pred ? attr : nullptr;
     cfg.numAttrs = pdl_pred ? 1 : 0;
     const Ops ops{one, nzero};
-    cfg.gridDim = dim3(pred_tiles);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, lw_predict_batch, jobs, pred_off, njobs, k, ops);
+    cfg.gridDim = dim3(std::min(ctas, pred_tiles));
+    cudaError_t e = cudaLaunchKernelEx(&cfg, lw_predict_batch, jobs, pred_off, njobs, pred_tiles, k, ops);
     if (e != cudaSuccess) return e;
     cfg.attrs = pdl_corr ? attr : nullptr;
     cfg.numAttrs = pdl_corr ? 1 : 0;
-    cfg.gridDim = dim3(corr_tiles);
-    e = cudaLaunchKernelEx(&cfg, lw_correct_batch, jobs, corr_off, njobs, k, ops);
+    cfg.gridDim = dim3(std::min(ctas, corr_tiles));
+    e = cudaLaunchKernelEx(&cfg, lw_correct_batch, jobs, corr_off, njobs, corr_tiles, k, ops);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -60,13 +60,16 @@ def run_alone(T):
     return res
 
 
-@pytest.mark.parametrize("pdl,chunk,block", [(1, 64, 0), (0, 64, 0), (1, 8, 512), (1, 2, 256)])
-def test_batch_equals_individual_runs(teuk, pdl, chunk, block):
+@pytest.mark.parametrize("pdl,chunk,block,mode", [(1, 64, 0, 0), (0, 64, 0, 0), (1, 8, 512, 0), (1, 2, 256, 0),
+                                                  (1, 64, 64, 0), (1, 64, 0, 1), (0, 2, 0, 1), (1, 6, 0, 1)])
+def test_batch_equals_individual_runs(teuk, pdl, chunk, block, mode):
+    # mode 0: one persistent launch for all jobs; mode 1: per-job launches
     alone = run_alone(teuk)
     B = teuk.Batch()
     B.set_option(teuk.TEUK_OPT_PDL, pdl)
     B.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, chunk)
     B.set_option(teuk.TEUK_OPT_BLOCK_THREADS, block)
+    B.set_option(teuk.TEUK_OPT_BATCH_MODE, mode)
     solvers = []
     for q, j in enumerate(JOBS):
         g, _ = make(teuk, j, q)
@@ -92,9 +95,14 @@ def test_batch_in_slices_remove_and_autotune(teuk):
         solvers.append(g)
         B.add(g, j["steps"])
     best = B.autotune()          # timed steps count as progress
-    assert best in (128, 256, 512)
+    assert best in (0, 64, 128, 256)
     B.step(5)
+    B.set_option(teuk.TEUK_OPT_BATCH_MODE, 0)  # switch modes mid-run, odd slices
     B.step(33)
+    B.set_option(teuk.TEUK_OPT_BATCH_MODE, 1)
+    B.step(7)
+    B.set_option(teuk.TEUK_OPT_BATCH_MODE, 0)
+    B.step(3)
     B.sync()
     # take job 1 out, finish it alone, the others in the batch
     r1 = B.remaining(1)
