@@ -58,8 +58,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
 # sources whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(predictor=125.85e6 + 14.82e6, corrector=151.02e6 + 19.06e6,
-                   sources_sha256="8502b4c99c8be5c35d4ce2370b17f8f8f0be4c1b5c9dbb4ca9486d5005053fd4")
+NCU_TRAFFIC = dict(predictor=125.87e6 + 16.44e6, corrector=151.02e6 + 19.69e6,
+                   sources_sha256="2bc76c2eab00e8bb32aec46a0ffd7026e2b871068ec8660b0eaf159671b0cdac")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu", "paper_1206_0270_gb300/csrc/teuk_fixed.h",
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",
                    "paper_1206_0270_gb300/csrc/teuk_api.cu"]  # kernels, their arithmetic, layout, launch
