@@ -471,9 +471,9 @@ def run_serving(args):
     reqs = [request(d) for d in raw]
     upd = sum((r.nr - 2) * r.nth * r.steps for r in reqs)
     budget = int(args.memory_gb * 2 ** 30)
-    # continuous batching, both scheduling policies
+    # continuous batching, the three scheduling policies
     per_policy = {}
-    for policy in ("fill", "share"):
+    for policy in ("fill", "share", "priority"):
         svc = S.WaveformService(memory_budget=budget, slice_steps=args.slice, policy=policy)
         for r in reqs:
             svc.submit(r)
@@ -513,6 +513,10 @@ def run_serving(args):
                 share_policy=dict(value=n / per_policy["share"][0], unit="waveforms/s",
                                   latency_s=dict(p50=per_policy["share"][1]["p50"], p99=per_policy["share"][1]["p99"],
                                                  mean=per_policy["share"][1]["mean"])),
+                priority_policy=dict(value=n / per_policy["priority"][0], unit="waveforms/s",
+                                     latency_s=dict(p50=per_policy["priority"][1]["p50"],
+                                                    p99=per_policy["priority"][1]["p99"],
+                                                    mean=per_policy["priority"][1]["mean"])),
                 one_by_one=dict(value=n / wall1, unit="waveforms/s",
                                 latency_s=dict(p50=float(np.percentile(lat1, 50)),
                                                p99=float(np.percentile(lat1, 99)), mean=float(lat1.mean()))))

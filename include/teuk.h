@@ -121,6 +121,15 @@ int teuk_set_source(teuk_handle *h, const teuk_orbit *orbit);
  * rstar_ext.  Allocates the ring buffer; clears earlier samples. */
 int teuk_set_extraction(teuk_handle *h, double rstar_ext, int every, long capacity);
 
+/* Run the handle's future work on `cuda_stream` (a cudaStream_t owned by the
+ * caller; NULL: a stream the handle creates and owns).  Synchronises the
+ * handle's current stream first and releases it if the handle created it.
+ * Results do not depend on the stream.  Allowed for handles in a batch (the
+ * batch's per-job launches use the handle's stream): a scheduler can move a
+ * job to a stream of another priority between slices.  The paper has no
+ * counterpart. */
+int teuk_set_stream(teuk_handle *h, void *cuda_stream);
+
 /* Advance n >= 0 time steps, asynchronously on the handle's stream.  Full
  * chunks of steps replay a captured CUDA graph. */
 int teuk_step(teuk_handle *h, long n);

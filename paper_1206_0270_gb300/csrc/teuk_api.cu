@@ -539,6 +539,24 @@ int teuk_step_handle(teuk_handle *h, long n)
     return TEUK_OK;
 }
 
+extern "C" int teuk_set_stream(teuk_handle *h, void *cuda_stream)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    CU(cudaStreamSynchronize(h->stream));  // everything queued on the old stream completes first
+    if (h->own_stream) {
+        cudaStreamDestroy(h->stream);
+        h->own_stream = false;
+    }
+    h->stream = nullptr;
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    return TEUK_OK;
+}
+
 extern "C" int teuk_step(teuk_handle *h, long n)
 {
     if (!h || n < 0) return fail(h, TEUK_ERR_BAD_ARG, "teuk_step: n < 0");

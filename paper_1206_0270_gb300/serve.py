@@ -79,17 +79,22 @@ class WaveformService:
     policy="share": every admitted job advances in every slice (processor
     sharing: short jobs finish early, long ones stretch).
     policy="fill": each slice runs admitted jobs in arrival order until they
-    hold `fill_points` grid points (enough to keep the FP64 pipe busy); the
-    others stay resident but paused, so the oldest jobs run at nearly full
-    speed and small jobs still share launches."""
+    hold `fill_points` grid points (enough to keep the GPU busy); the others
+    stay resident but paused, so the oldest jobs run at nearly full speed and
+    small jobs still share launches.
+    policy="priority": every admitted job advances in every slice, but the
+    jobs that "fill" would run (the oldest, up to `fill_points`) run on
+    high-priority CUDA streams and the others on low-priority ones, so the
+    younger jobs take only what the older ones leave of the GPU (the batch's
+    per-job launches run each job on its own stream)."""
 
     def __init__(self, memory_budget: int, slice_steps: int = 640, max_jobs: int = 4096,
                  stream=None, clock: Callable[[], float] = time.perf_counter, policy: str = "fill",
                  fill_points: int = 2_000_000):
         if slice_steps < 2 or slice_steps % 2:
             raise ValueError("slice_steps must be even and >= 2")
-        if policy not in ("share", "fill"):
-            raise ValueError("policy is 'share' or 'fill'")
+        if policy not in ("share", "fill", "priority"):
+            raise ValueError("policy is 'share', 'fill' or 'priority'")
         self.policy = policy
         self.fill_points = int(fill_points)
         self.budget = int(memory_budget)
@@ -112,6 +117,11 @@ class WaveformService:
         # (teuk_stable_dt scans the whole grid; the ctypes call releases the GIL)
         self._pool = cf.ThreadPoolExecutor(max_workers=4)
         self.slices = 0
+        self._prio = None
+        if policy == "priority":
+            import torch
+            low, high = torch.cuda.Stream.priority_range()  # least and greatest priority
+            self._prio = (low, high)
 
     # -- clock -------------------------------------------------------------
     def now(self) -> float:
@@ -162,12 +172,16 @@ class WaveformService:
                 break                      # its time step is still being prepared; others keep running
             heapq.heappop(self._queue)
             # each handle sets up on its own stream, concurrently with the running slice
-            g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, self._dt(r), r.a, r.s, r.m)
+            low_stream = None
+            if self._prio is not None:
+                import torch
+                low_stream = torch.cuda.Stream(priority=self._prio[0])
+            g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, self._dt(r), r.a, r.s, r.m, stream=low_stream)
             g.set_source(r0=r.r0, sigma=r.sigma)
             g.set_extraction(r.rstar_ext, r.every, capacity=self.slice // r.every + 2)
             self._used += need
             self._running[rid] = dict(solver=g, job=None, remaining=r.steps, admitted=self.now(), t=[], phi=[],
-                                      need=need)
+                                      need=need, high=False)
 
     def _schedule(self):
         """Choose the jobs that advance in the next slice and make the batch
@@ -178,9 +192,16 @@ class WaveformService:
             st = self._running[rid]
             if st["remaining"] == 0:
                 continue
-            if self.policy == "fill" and want and pts >= self.fill_points:
-                break
+            if self.policy != "share" and want and pts >= self.fill_points:
+                if self.policy == "fill":
+                    break
+                want.add(rid)  # priority: runs, at low priority
+                continue
             want.add(rid)
+            if self.policy == "priority" and not st["high"]:
+                import torch
+                st["solver"].set_stream(torch.cuda.Stream(priority=self._prio[1]))  # promoted for good
+                st["high"] = True
             r = self._requests[rid]
             pts += r.nr * r.nth
         for rid in order:

@@ -60,6 +60,7 @@ _SIGS = {
     "teuk_set_source": (C.c_int, [_vp, C.POINTER(teuk_orbit)]),
     "teuk_set_extraction": (C.c_int, [_vp, C.c_double, C.c_int, C.c_long]),
     "teuk_step": (C.c_int, [_vp, C.c_long]),
+    "teuk_set_stream": (C.c_int, [_vp, _vp]),
     "teuk_extract": (C.c_int, [_vp, _dp, _dp, C.c_long, C.POINTER(C.c_long)]),
     "teuk_get_state": (C.c_int, [_vp, _dp, _dp]),
     "teuk_get_state_device": (C.c_int, [_vp, _vp, _vp]),
@@ -162,6 +163,7 @@ class Solver:
         _check(teuk_create(C.byref(self.grid), float(a), int(s), int(m), _stream_handle(stream),
                            C.byref(h)), what="teuk_create")
         self.h = h
+        self._stream = stream  # keeps a caller's stream object alive as long as the handle uses it
         if kernel is not None:
             self.set_kernel(kernel)
 
@@ -215,6 +217,12 @@ class Solver:
 
     def step(self, n):
         _check(teuk_step(self.h, int(n)), self.h, "teuk_step")
+
+    def set_stream(self, stream=None):
+        """Run future work on `stream` (torch.cuda.Stream, a raw handle, or None
+        for a stream of the handle's own); waits for the current stream."""
+        _check(teuk_set_stream(self.h, _stream_handle(stream)), self.h, "teuk_set_stream")
+        self._stream = stream
 
     @property
     def step_count(self):

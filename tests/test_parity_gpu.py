@@ -474,3 +474,30 @@ def test_full_length_kerr_8192x128_linearity_and_determinism(teuk):
         assert big.sum() > 0.1 * x.size
         np.testing.assert_array_equal(2 * x[big], y[big])
         np.testing.assert_allclose(2 * x, y, rtol=1e-13, atol=1e-290)
+
+
+def test_set_stream_keeps_results(teuk):
+    # moving a handle to another stream between steps changes scheduling only
+    import torch
+    nr, nth = 200, 64
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, 0.9, -2, 2)
+    u = inputs.random_fields(nr, nth, seed=21)
+    a = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
+    a.set_initial(*u)
+    a.set_source(**SRC)
+    a.step(150)
+    ref = a.state()
+    a.close()
+    b = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
+    b.set_initial(*u)
+    b.set_source(**SRC)
+    b.step(70)
+    hi = torch.cuda.Stream(priority=torch.cuda.Stream.priority_range()[1])
+    b.set_stream(hi)
+    b.step(64)
+    b.set_stream(None)
+    b.step(16)
+    st = b.state()
+    b.close()
+    np.testing.assert_array_equal(st[0], ref[0])
+    np.testing.assert_array_equal(st[1], ref[1])
