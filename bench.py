@@ -59,10 +59,11 @@ NUM_SMS = 152
 # (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
 # sources whose SHA-256 is recorded here; reported as null otherwise.
 NCU_TRAFFIC = dict(predictor=125.87e6 + 16.44e6, corrector=151.02e6 + 19.69e6,
-                   sources_sha256="2bc76c2eab00e8bb32aec46a0ffd7026e2b871068ec8660b0eaf159671b0cdac")
-TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu", "paper_1206_0270_gb300/csrc/teuk_fixed.h",
-                   "paper_1206_0270_gb300/csrc/teuk_internal.h",
-                   "paper_1206_0270_gb300/csrc/teuk_api.cu"]  # kernels, their arithmetic, layout, launch
+                   sources_sha256="731c75ff13cee43440c7368dc15a383bb12cea69705ebdab75ac12f0778585a9")
+TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
+                   "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
+                   "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits
+                   "paper_1206_0270_gb300/csrc/teuk_handle.h"]     # launch defaults (PDL, graph chunk)
 
 
 def sources_sha256():
