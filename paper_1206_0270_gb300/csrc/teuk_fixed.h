@@ -110,6 +110,25 @@ TEUK_FX_HD Fx fx_unpack(double v)
     return o;
 }
 
+// Split of a coefficient that is known to be finite and either normal or
+// exactly zero (the step kernels' coefficient planes guarantee it): no
+// subnormal case and no finiteness flag.  A zero gets e = -4096, so its
+// product is shifted out entirely; for every such input the term contributes
+// exactly what fx_unpack's split gives.
+TEUK_FX_HD Fx fx_unpack_coef(double v)
+{
+    const uint64_t u = fx_bits(v);
+    const uint32_t hi = (uint32_t)(u >> 32);
+    const int eraw = (int)((hi >> 20) & 0x7FFu);
+    Fx o;
+    o.mhi = (hi & 0xFFFFFu) | 0x100000u;
+    o.mlo = (uint32_t)u;
+    o.e = eraw ? eraw : -4096;
+    o.neg = hi >> 31;
+    o.braw = 0;
+    return o;
+}
+
 // floor(m_c m_x / 2^47) of the exact 106-bit product
 TEUK_FX_HD uint64_t fx_prod47(const Fx &c, const Fx &x)
 {

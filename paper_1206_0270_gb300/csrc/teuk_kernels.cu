@@ -102,6 +102,12 @@ __device__ __forceinline__ double2 unit_phase(double ph)
 // Setup: coefficient planes from the radial and angular tables
 // ---------------------------------------------------------------------------
 
+// The Pi-row coefficients feed the fixed-point sums, whose coefficient split
+// assumes normal numbers or exact zeros: a subnormal value (below 2^-1022,
+// far below any coefficient of the scheme) is stored as zero.
+__device__ __forceinline__ double normal_or_zero(double v) { return fabs(v) < 0x1p-1022 ? 0.0 : v; }
+__device__ __forceinline__ double2 normal_or_zero(double2 v) { return make_double2(normal_or_zero(v.x), normal_or_zero(v.y)); }
+
 __global__ void setup_kernel(SetupParams sp)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,39 +133,39 @@ __global__ void setup_kernel(SetupParams sp)
         const double q = 0.25 * sp.dt;
         sp.pa[k] = 0.5 + beta;
         sp.pb[k] = 0.5 - beta;
-        sp.eb[k] = 2.0 * beta;
+        sp.eb[k] = normal_or_zero(2.0 * beta);
         const double2 P1 = make_double2(0.5 - beta - q * c.ct_re, -q * c.ct_im);
         const double2 Q1 = make_double2(-g_re - q * wr, -g_im - q * wi);
         const double2 Q2 = make_double2(g_re - q * wr, g_im - q * wi);
         if (sp.real_coef) {
-            ((double *)sp.P1)[k] = P1.x;
-            ((double *)sp.Q1)[k] = Q1.x;
-            ((double *)sp.Q2)[k] = Q2.x;
+            ((double *)sp.P1)[k] = normal_or_zero(P1.x);
+            ((double *)sp.Q1)[k] = normal_or_zero(Q1.x);
+            ((double *)sp.Q2)[k] = normal_or_zero(Q2.x);
         } else {
-            sp.P1[k] = P1;
-            sp.Q1[k] = Q1;
-            sp.Q2[k] = Q2;
+            sp.P1[k] = normal_or_zero(P1);
+            sp.Q1[k] = normal_or_zero(Q1);
+            sp.Q2[k] = normal_or_zero(Q2);
         }
-        sp.KAp[k] = q * c.kappa * A;
-        sp.KCp[k] = q * c.kappa * C;
+        sp.KAp[k] = normal_or_zero(q * c.kappa * A);
+        sp.KCp[k] = normal_or_zero(q * c.kappa * C);
     } else {
         const double hd = 0.5 * sp.dt;
         sp.tb[k] = 2.0 * beta;
-        sp.nt2[k] = -4.0 * beta;
+        sp.nt2[k] = normal_or_zero(-4.0 * beta);
         const double2 R1 = make_double2(2.0 * beta - hd * c.ct_re, -hd * c.ct_im);
         const double2 R3 = make_double2(2.0 * g_re - hd * wr, 2.0 * g_im - hd * wi);
         const double2 R4 = make_double2(-2.0 * g_re - hd * wr, -2.0 * g_im - hd * wi);
         if (sp.real_coef) {
-            ((double *)sp.R1)[k] = R1.x;
-            ((double *)sp.R3)[k] = R3.x;
-            ((double *)sp.R4)[k] = R4.x;
+            ((double *)sp.R1)[k] = normal_or_zero(R1.x);
+            ((double *)sp.R3)[k] = normal_or_zero(R3.x);
+            ((double *)sp.R4)[k] = normal_or_zero(R4.x);
         } else {
-            sp.R1[k] = R1;
-            sp.R3[k] = R3;
-            sp.R4[k] = R4;
+            sp.R1[k] = normal_or_zero(R1);
+            sp.R3[k] = normal_or_zero(R3);
+            sp.R4[k] = normal_or_zero(R4);
         }
-        sp.KAc[k] = hd * c.kappa * A;
-        sp.KCc[k] = hd * c.kappa * C;
+        sp.KAc[k] = normal_or_zero(hd * c.kappa * A);
+        sp.KCc[k] = normal_or_zero(hd * c.kappa * C);
         sp.b_node[k] = c.b;
     }
 }
@@ -278,8 +284,9 @@ __device__ __forceinline__ double2 pred_pi(const PredCoef &c, const Ops ops, dou
     const Fx tr = fx_unpack(tau.x), ti = fx_unpack(tau.y), pr = fx_unpack(pi1.x), pim = fx_unpack(pi1.y);
     const Fx ar = fx_unpack(phi0.x), ai = fx_unpack(phi0.y), br = fx_unpack(phi1.x), bi = fx_unpack(phi1.y);
     const Fx ur = fx_unpack(sup.x), ui = fx_unpack(sup.y), dr = fx_unpack(sdn.x), di = fx_unpack(sdn.y);
-    const Fx P1r = fx_unpack(c.P1.x), eb = fx_unpack(c.eb), Q1r = fx_unpack(c.Q1.x), Q2r = fx_unpack(c.Q2.x);
-    const Fx KA = fx_unpack(c.KA), KC = fx_unpack(c.KC);
+    const Fx P1r = fx_unpack_coef(c.P1.x), eb = fx_unpack_coef(c.eb), Q1r = fx_unpack_coef(c.Q1.x),
+             Q2r = fx_unpack_coef(c.Q2.x);
+    const Fx KA = fx_unpack_coef(c.KA), KC = fx_unpack_coef(c.KC);
     double2 o;
     bool ok;
     if (REAL) {
@@ -290,7 +297,7 @@ __device__ __forceinline__ double2 pred_pi(const PredCoef &c, const Ops ops, dou
         ok = fx_dot<6>(C, Xr, F, &o.x);
         ok &= fx_dot<6>(C, Xi, F, &o.y);
     } else {
-        const Fx P1i = fx_unpack(c.P1.y), Q1i = fx_unpack(c.Q1.y), Q2i = fx_unpack(c.Q2.y);
+        const Fx P1i = fx_unpack_coef(c.P1.y), Q1i = fx_unpack_coef(c.Q1.y), Q2i = fx_unpack_coef(c.Q2.y);
         const Fx C[9] = {P1r, P1i, eb, Q1r, Q1i, Q2r, Q2i, KA, KC};
         const Fx Xr[9] = {tr, ti, pr, ar, ai, br, bi, ur, dr};
         const uint32_t Fr[9] = {0, 1, 0, 0, 1, 0, 1, 0, 0};
@@ -348,13 +355,14 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
                                            const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn)
 {
     if (!TEUK_FIXED_POINT) return corr_pi_fp64<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
-    const Fx one = fx_unpack(1.0);
+    const Fx one = fx_unpack_coef(1.0);
     const Fx pr = fx_unpack(pi.x), pim = fx_unpack(pi.y), tr = fx_unpack(tau.x), ti = fx_unpack(tau.y);
     const Fx mr = fx_unpack(hm.pi.x), mi = fx_unpack(hm.pi.y);
     const Fx ar = fx_unpack(hp.phi.x), ai = fx_unpack(hp.phi.y), br = fx_unpack(hm.phi.x), bi = fx_unpack(hm.phi.y);
     const Fx ur = fx_unpack(sup.x), ui = fx_unpack(sup.y), dr = fx_unpack(sdn.x), di = fx_unpack(sdn.y);
-    const Fx R1r = fx_unpack(c.R1.x), nt2 = fx_unpack(c.nt2), R3r = fx_unpack(c.R3.x), R4r = fx_unpack(c.R4.x);
-    const Fx KA = fx_unpack(c.KA), KC = fx_unpack(c.KC);
+    const Fx R1r = fx_unpack_coef(c.R1.x), nt2 = fx_unpack_coef(c.nt2), R3r = fx_unpack_coef(c.R3.x),
+             R4r = fx_unpack_coef(c.R4.x);
+    const Fx KA = fx_unpack_coef(c.KA), KC = fx_unpack_coef(c.KC);
     double2 o;
     bool ok;
     if (REAL) {
@@ -365,7 +373,7 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
         ok = fx_dot<7>(C, Xr, F, &o.x);
         ok &= fx_dot<7>(C, Xi, F, &o.y);
     } else {
-        const Fx R1i = fx_unpack(c.R1.y), R3i = fx_unpack(c.R3.y), R4i = fx_unpack(c.R4.y);
+        const Fx R1i = fx_unpack_coef(c.R1.y), R3i = fx_unpack_coef(c.R3.y), R4i = fx_unpack_coef(c.R4.y);
         const Fx C[10] = {one, R1r, R1i, nt2, R3r, R3i, R4r, R4i, KA, KC};
         const Fx Xr[10] = {pr, tr, ti, mr, ar, ai, br, bi, ur, dr};
         const uint32_t Fr[10] = {0, 0, 1, 0, 0, 1, 0, 1, 0, 0};
