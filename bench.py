@@ -58,8 +58,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
 # sources whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(predictor=125.87e6 + 16.44e6, corrector=151.02e6 + 19.69e6,
-                   sources_sha256="731c75ff13cee43440c7368dc15a383bb12cea69705ebdab75ac12f0778585a9")
+NCU_TRAFFIC = dict(predictor=125.86e6 + 16.36e6, corrector=151.01e6 + 19.77e6,
+                   sources_sha256="4e6128c7a54195a41a4fe8ae13a7a2eaec1152b3ad376c26f37b8d6767ac2bce")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits
