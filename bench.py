@@ -59,7 +59,7 @@ NUM_SMS = 152
 # (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
 # sources whose SHA-256 is recorded here; reported as null otherwise.
 NCU_TRAFFIC = dict(predictor=125.86e6 + 16.36e6, corrector=151.01e6 + 19.77e6,
-                   sources_sha256="4e6128c7a54195a41a4fe8ae13a7a2eaec1152b3ad376c26f37b8d6767ac2bce")
+                   sources_sha256="db3abb72fbb3c38d0846a9076d0760e19620ce393b4391a8c9968c7bee996eb6")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits
@@ -67,11 +67,17 @@ TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and
 
 
 def sources_sha256():
+    """SHA-256 of the code of TRAFFIC_SOURCES with comments and blank space
+    removed, so that editing a comment does not invalidate the capture."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                 # line comments
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

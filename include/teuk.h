@@ -187,12 +187,13 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
 #define TEUK_OPT_BLOCK_THREADS 3  /* batches only: CTA threads, a multiple of 32 <= 512; 0 = automatic (128) */
 /* TEUK_OPT_REAL_PATH: 1 (default) stores real coefficient planes and uses
  * real-by-complex products when every coefficient is real (a = 0, or
- * s = m = 0: 44 instead of 56 FP64 instructions per point); 0 keeps the
+ * s = m = 0: 6 and 7 instead of 9 and 10 products per Pi row); 0 keeps the
  * complex planes.  Both give the same numbers. */
 #define TEUK_OPT_REAL_PATH 4
 /* TEUK_OPT_SPLIT_ROWS: r* rows per CTA tile of the split kernels, 1..512 /
- * (nth rounded up to a multiple of 32); 0 (default) picks 256 / that width,
- * at least 1.  A tile is one thread per point. */
+ * (tile width); a tile is up to 128 theta columns (rows wider than 128 are
+ * cut into equal tiles, a multiple of 32 wide), one thread per point.  0
+ * (default) picks 128 / tile width, at least 1. */
 #define TEUK_OPT_SPLIT_ROWS 5
 /* TEUK_OPT_BATCH_MODE (batches only): 1 (default) advances every job with its
  * own kernels on its own stream (graph replay per chunk), the jobs running

@@ -5,8 +5,9 @@
 // coefficients, apart from the source phase.  The setup kernel folds every
 // constant of the scheme (dt, h, dtheta, the 1/2 averages, the diagonal of
 // the angular stencil, the pole ghosts) into per-point coefficient planes, so
-// that a step costs 56 FP64 instructions per point (FP64 throughput is the
-// scarce resource on GB300; bytes are not).
+// that a step is 100 flops per point (56 FP64 instructions; the kernels run 20
+// of them on the FP64 pipe and the Pi rows as fixed-point sums on the integer
+// pipes: FP64 throughput is the scarce resource on GB300; bytes are not).
 //
 // With u_i = (Phi_i, Pi_i) the state at node i, sigma_j = Phi_{i,j} +
 // Phi_{i+1,j} and tau = Pi_i + Pi_{i+1}, the predictor (Eq. 3) at the

@@ -4,11 +4,16 @@
 // of arXiv:1206.0270, for u = (Phi, Pi) on an (r*, theta) grid, with the
 // point-particle source added to the Pi row and the waveform row copied to a
 // ring buffer.  All constants of the scheme are folded into the coefficient
-// planes built by setup_kernel (the formulas are in teuk_internal.h), so the
-// step costs 56 FP64 instructions per point (8 adds and 4 multiplies, issued
-// as FMAs, and 44 FMAs).
+// planes built by setup_kernel (the formulas are in teuk_internal.h).  Per
+// point update, the Phi rows and the sums tau, sigma take 20 FP64
+// instructions (adds and multiplies issued as FMAs); the Pi rows are sums of
+// 38 products evaluated in 64-bit fixed point on the integer pipes
+// (teuk_fixed.h), with FP64 FMA chains as the fallback.  All on the FP64
+// pipe, the step would be 56 FP64 instructions (100 flops).
 //
-// The fused kernel assigns one thread per theta index j and lets each CTA
+// Default kernels: lw_predict_split / lw_correct_split, one thread per point
+// over theta tiles of at most 128 columns.  The fused kernel assigns one
+// thread per theta index j and lets each CTA
 // march along r* over a contiguous strip of rows: the predictor value at
 // i + 1/2 is computed once, used by the correctors at i and i + 1, and never
 // leaves registers; the angular neighbours j +- 1 are exchanged through
