@@ -327,6 +327,27 @@ def run_gpu(args):
                h2d_bytes_per_step=2 * nr * nth * 16, d2h_bytes_per_step=nsamp * (nth * 16 + 8))
     E.close()
 
+    # ---- the same workload with every Pi-row product as an FP64 FMA ------------------
+    F = T.Solver(nr, nth, w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"], stream=stream)
+    F.set_option(T.TEUK_OPT_FIXED_POINT, 0)
+    F.set_initial(np.zeros((nr, nth), complex), np.zeros((nr, nth), complex))
+    F.set_source(**w["source"])
+    F.set_extraction(ex["rstar"], ex["every"], capacity=max(16, 2 * samples_per_step * 16))
+    n_fp64 = min(args.steps, 5)
+    for _ in range(max(1, args.warmup)):
+        F.step(args.chunk)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n_fp64):
+        F.step(args.chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = reduce_max(e0.elapsed_time(e1), "cuda")
+    all_fp64 = dict(value=whole_job_rate(ws, upd_per_step * n_fp64, fp64_ms / 1e3), unit=UNIT, steps=n_fp64,
+                    arithmetic="every Pi-row product as an FP64 FMA (TEUK_OPT_FIXED_POINT 0)")
+    F.close()
+
     if rank != 0:
         S.close()
         return 0
@@ -341,7 +362,7 @@ def run_gpu(args):
                                        "rounded once to FP64 (error <= n 2^-57 max|c x| + 2^-53 |sum|)",
                             l2="inputs larger than L2 (state 2x33.5 MB + coefficients 193 MB per time step)",
                             parallelism="replicas" if ws > 1 else "single GPU"),
-                roofline=roofline, e2e=e2e, gpu_launches=int(launches),
+                roofline=roofline, e2e=e2e, gpu_launches=int(launches), all_fp64=all_fp64,
                 step_ms_min=min(step_ms), step_ms_median=statistics.median(step_ms))
     clocks = clk.summary()
     if clocks:

@@ -201,6 +201,12 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  * corrector launch per step that work through a tile list of every job.
  * Both give the same numbers as stepping each handle alone. */
 #define TEUK_OPT_BATCH_MODE 6
+/* TEUK_OPT_FIXED_POINT: 1 (default) evaluates the Pi rows of Eqs. (3)-(4) as
+ * fixed-point sums on the integer pipes (see teuk_fixed_dot: exact products,
+ * one rounding, at least as accurate as the FP64 sum); 0 evaluates every
+ * product with FP64 fused multiply-adds.  The two differ only by rounding
+ * (both agree with the oracle to about 1e-14 per step). */
+#define TEUK_OPT_FIXED_POINT 7
 int teuk_set_option(teuk_handle *h, int option, long value);
 
 /* Current fused-kernel launch shape. */

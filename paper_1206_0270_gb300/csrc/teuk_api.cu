@@ -176,7 +176,7 @@ static void choose_launch(teuk_handle *h, int rows_per_block)
     if (rows_per_block <= 0) {
         const int threads = fused_block_threads(h->nth);
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(h->sp.real_coef), threads,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(h->sp.real_coef, h->sp.fixed_point), threads,
                                                           fused_smem_bytes(h->nth)) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
@@ -306,6 +306,7 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     p.nr = nr; p.nth = nth; p.dt = h->dt; p.q = 0.25 * h->dt; p.half_dt = 0.5 * h->dt;
     p.one = 1.0; p.nzero = -0.0;
     p.real_coef = su.real_coef;
+    p.fixed_point = 1;
     h->su = su;
     p.pred = PredPlanes{su.pa, su.pb, su.eb, su.KAp, su.KCp, su.P1, su.Q1, su.Q2};
     p.corr = CorrPlanes{su.tb, su.nt2, su.KAc, su.KCc, su.R1, su.R3, su.R4};
@@ -598,6 +599,13 @@ extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
         CU(cudaStreamSynchronize(h->stream));
         destroy_graphs(h);
         h->split_rows = (int)value;
+        return TEUK_OK;
+    case TEUK_OPT_FIXED_POINT:
+        if (value != 0 && value != 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: fixed point is 0 or 1");
+        CU(cudaStreamSynchronize(h->stream));
+        destroy_graphs(h);
+        h->sp.fixed_point = (int)value;
+        if (h->variant == 0) choose_launch(h, h->rows_per_block);  // the fused kernel's occupancy depends on it
         return TEUK_OK;
     case TEUK_OPT_REAL_PATH: {
         if (value != 0 && value != 1) return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: real path is 0 or 1");

@@ -80,6 +80,7 @@ struct StepParams {
     double dt, q, half_dt; // dt, dt/4, dt/2
     double one, nzero;     // 1 and -0: operands that turn FP64 adds and multiplies into FMAs
     int real_coef;         // 1: P1, Q1, Q2, R1, R3, R4 are packed real planes (no imaginary parts)
+    int fixed_point;       // 1: Pi rows as fixed-point sums (teuk_fixed.h); 0: FP64 FMA chains
     PredPlanes pred;
     CorrPlanes corr;
     SourceWindow src;
@@ -161,11 +162,11 @@ const void *batch_kernel_ptr(int which);
 
 int fused_block_threads(int nth);
 size_t fused_smem_bytes(int nth);
-const void *fused_kernel_ptr(int real);
+const void *fused_kernel_ptr(int real, int fixed_point);
 int split_tile_width(int nth);
 int split_theta_tiles(int nth);
-int split_rows_per_block(int nth);
+int split_rows_per_block(int nth, int fixed_point);
 size_t split_smem_bytes(int nth, int rows = 0);
-const void *split_kernel_ptr(int which, int real);
+const void *split_kernel_ptr(int which, int real, int fixed_point);
 
 }  // namespace teuk

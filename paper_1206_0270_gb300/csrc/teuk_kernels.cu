@@ -275,17 +275,14 @@ __device__ __forceinline__ double2 pred_pi_fp64(const PredCoef &c, const Ops ops
     return o;
 }
 
-// TEUK_FIXED_POINT 0 builds all-FP64 kernels (the Pi rows as FMA chains),
-// for comparison; the default evaluates the Pi rows in fixed point.
-#ifndef TEUK_FIXED_POINT
-#define TEUK_FIXED_POINT 1
-#endif
+// FX: the Pi rows as fixed-point sums (StepParams::fixed_point, the default)
+// or as FP64 FMA chains.
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __device__ __forceinline__ double2 pred_pi(const PredCoef &c, const Ops ops, double2 tau, double2 phi0,
                                            double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
-    if (!TEUK_FIXED_POINT) return pred_pi_fp64<REAL>(c, ops, tau, phi0, phi1, pi1, sup, sdn);
+    if (!FX) return pred_pi_fp64<REAL>(c, ops, tau, phi0, phi1, pi1, sup, sdn);
     const Fx tr = fx_unpack(tau.x), ti = fx_unpack(tau.y), pr = fx_unpack(pi1.x), pim = fx_unpack(pi1.y);
     const Fx ar = fx_unpack(phi0.x), ai = fx_unpack(phi0.y), br = fx_unpack(phi1.x), bi = fx_unpack(phi1.y);
     const Fx ur = fx_unpack(sup.x), ui = fx_unpack(sup.y), dr = fx_unpack(sdn.x), di = fx_unpack(sdn.y);
@@ -315,7 +312,7 @@ __device__ __forceinline__ double2 pred_pi(const PredCoef &c, const Ops ops, dou
     return o;
 }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, const Ops ops, double2 phi0,
                                               double2 pi0, double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
@@ -324,17 +321,17 @@ __device__ __forceinline__ HalfStep predict_c(const PredCoef &c, double q, const
     o.phi = make_double2(fma_rn(c.pa, phi0.x, ops.nzero), fma_rn(c.pa, phi0.y, ops.nzero));
     rfma(o.phi, c.pb, phi1);
     rfma(o.phi, q, tau);
-    o.pi = pred_pi<REAL>(c, ops, tau, phi0, phi1, pi1, sup, sdn);
+    o.pi = pred_pi<REAL, FX>(c, ops, tau, phi0, phi1, pi1, sup, sdn);
     return o;
 }
 
 __device__ __forceinline__ Ops ops_of(const StepParams &p) { return Ops{p.one, p.nzero}; }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __device__ __forceinline__ HalfStep predict(const StepParams &p, size_t k, double2 phi0, double2 pi0,
                                             double2 phi1, double2 pi1, double2 sup, double2 sdn)
 {
-    return predict_c<REAL>(load_pred<REAL>(p, k), p.q, ops_of(p), phi0, pi0, phi1, pi1, sup, sdn);
+    return predict_c<REAL, FX>(load_pred<REAL>(p, k), p.q, ops_of(p), phi0, pi0, phi1, pi1, sup, sdn);
 }
 
 // Corrector (Eq. 4) at one node.  hp: half step at i + 1/2, hm: at i - 1/2,
@@ -355,11 +352,11 @@ __device__ __forceinline__ double2 corr_pi_fp64(const CorrCoef &c, const Ops ops
     return npi;
 }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, double2 pi, double2 tau,
                                            const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn)
 {
-    if (!TEUK_FIXED_POINT) return corr_pi_fp64<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
+    if (!FX) return corr_pi_fp64<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
     const Fx one = fx_unpack_coef(1.0);
     const Fx pr = fx_unpack(pi.x), pim = fx_unpack(pi.y), tr = fx_unpack(tau.x), ti = fx_unpack(tau.y);
     const Fx mr = fx_unpack(hm.pi.x), mi = fx_unpack(hm.pi.y);
@@ -391,7 +388,7 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
     return o;
 }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, const Ops ops, double2 phi,
                                           double2 pi, const HalfStep &hp, const HalfStep &hm, double2 sup,
                                           double2 sdn, double2 *phi_out, double2 *pi_out)
@@ -402,15 +399,15 @@ __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, con
     rfma(nphi, c.tb, hm.phi);
     rfma(nphi, half_dt, tau);
     *phi_out = nphi;
-    *pi_out = corr_pi<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
+    *pi_out = corr_pi<REAL, FX>(c, ops, pi, tau, hp, hm, sup, sdn);
 }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 phi, double2 pi,
                                         const HalfStep &hp, const HalfStep &hm, double2 sup,
                                         double2 sdn, double2 *phi_out, double2 *pi_out)
 {
-    correct_c<REAL>(load_corr<REAL>(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
+    correct_c<REAL, FX>(load_corr<REAL>(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -422,7 +419,7 @@ __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 p
 size_t fused_smem_bytes(int nth) { return sizeof(double2) * 4 * (size_t)(nth + 2); }
 int fused_block_threads(int nth) { return ((nth + 31) / 32) * 32; }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, const double2 *__restrict__ Phi,
                                                       const double2 *__restrict__ Pi,
                                                       double2 *__restrict__ PhiO,
@@ -464,7 +461,7 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
     double2 phn = Phi[(size_t)i0 * nth + jj], pin = Pi[(size_t)i0 * nth + jj];
     if (act) s_sig[j + 1] = add2(phc, phn, ops_of(p));
     __syncthreads();
-    HalfStep hm = predict<REAL>(p, (size_t)(i0 - 1) * nth + jj, phc, pic, phn, pin, s_sig[jj + 2], s_sig[jj]);
+    HalfStep hm = predict<REAL, FX>(p, (size_t)(i0 - 1) * nth + jj, phc, pic, phn, pin, s_sig[jj + 2], s_sig[jj]);
     if (src_mid && i0 - 1 >= sw.mid_lo && i0 - 1 <= sw.mid_hi)
         rfma(hm.pi, ldg(sw.gP + (size_t)(i0 - 1 - sw.mid_lo) * nth + jj), s_phase[0]);
     phc = phn;
@@ -492,7 +489,7 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
         double2 *sg = s_sig + buf * W;
         if (act) sg[j + 1] = add2(phc, phn, ops_of(p));
         __syncthreads();
-        HalfStep hp = predict_c<REAL>(pc, p.q, ops_of(p), phc, pic, phn, pin, sg[jj + 2], sg[jj]);
+        HalfStep hp = predict_c<REAL, FX>(pc, p.q, ops_of(p), phc, pic, phn, pin, sg[jj + 2], sg[jj]);
         if (src_mid && i >= sw.mid_lo && i <= sw.mid_hi)
             rfma(hp.pi, ldg(sw.gP + (size_t)(i - sw.mid_lo) * nth + jj), s_phase[0]);
 
@@ -501,7 +498,7 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
         __syncthreads();
         const size_t kc = (size_t)i * nth + jj;
         double2 nphi, npi;
-        correct_c<REAL>(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
+        correct_c<REAL, FX>(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
         if (src_node && i >= sw.node_lo && i <= sw.node_hi)
             rfma(npi, ldg(sw.gC + (size_t)(i - sw.node_lo) * nth + jj), s_phase[1]);
         if (act) {
@@ -519,17 +516,19 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
     }
 }
 
-const void *fused_kernel_ptr(int real) { return real ? (const void *)lw_step_fused<true> : (const void *)lw_step_fused<false>; }
+// The four instantiations of a step kernel (real or complex coefficient
+// planes, fixed-point or FP64 Pi rows) share one signature.
+#define TEUK_PICK(K, real, fx) ((real) ? ((fx) ? K<true, true> : K<true, false>) : ((fx) ? K<false, true> : K<false, false>))
+
+const void *fused_kernel_ptr(int real, int fixed_point) { return (const void *)TEUK_PICK(lw_step_fused, real, fixed_point); }
 
 cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const double2 *Pi,
                               double2 *PhiO, double2 *PiO, int k, int rows_per_block, int nblocks,
                               cudaStream_t st)
 {
     const int threads = fused_block_threads(p.nth);
-    if (p.real_coef)
-        lw_step_fused<true><<<nblocks, threads, fused_smem_bytes(p.nth), st>>>(p, Phi, Pi, PhiO, PiO, k, rows_per_block);
-    else
-        lw_step_fused<false><<<nblocks, threads, fused_smem_bytes(p.nth), st>>>(p, Phi, Pi, PhiO, PiO, k, rows_per_block);
+    TEUK_PICK(lw_step_fused, p.real_coef, p.fixed_point)<<<nblocks, threads, fused_smem_bytes(p.nth), st>>>(
+        p, Phi, Pi, PhiO, PiO, k, rows_per_block);
     return cudaGetLastError();
 }
 
@@ -537,7 +536,7 @@ cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const dou
 // Two-kernel variant: predictor writes the half-step fields to device memory
 // ---------------------------------------------------------------------------
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
                                   const double2 *__restrict__ Pi, double2 *__restrict__ PhiH,
                                   double2 *__restrict__ PiH, int k)
@@ -553,7 +552,7 @@ __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
     const size_t r0 = (size_t)hp * nth, r1 = r0 + nth;
     const double2 sup = add2(Phi[r0 + ju], Phi[r1 + ju], ops_of(p));
     const double2 sdn = add2(Phi[r0 + jd], Phi[r1 + jd], ops_of(p));
-    HalfStep o = predict<REAL>(p, k0, phi0, pi0, phi1, pi1, sup, sdn);
+    HalfStep o = predict<REAL, FX>(p, k0, phi0, pi0, phi1, pi1, sup, sdn);
     const SourceWindow &sw = p.src;
     if (sw.active && hp >= sw.mid_lo && hp <= sw.mid_hi) {
         const long long n = *p.step_base + k;
@@ -563,7 +562,7 @@ __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
     PiH[k0] = o.pi;
 }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
                                   const double2 *__restrict__ Pi, const double2 *__restrict__ PhiH,
                                   const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
@@ -585,7 +584,7 @@ __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
     const double2 sup = add2(PhiH[kp - j + ju], PhiH[km - j + ju], ops_of(p));
     const double2 sdn = add2(PhiH[kp - j + jd], PhiH[km - j + jd], ops_of(p));
     double2 nphi, npi;
-    correct<REAL>(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, &nphi, &npi);
+    correct<REAL, FX>(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, &nphi, &npi);
     const long long n = *p.step_base + k;
     const SourceWindow &sw = p.src;
     if (sw.active && i >= sw.node_lo && i <= sw.node_hi)
@@ -605,16 +604,12 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
 {
     const int threads = 256;
     const long long np = (long long)(p.nr - 1) * p.nth, nc = (long long)(p.nr - 2) * p.nth;
-    if (part != 1) {
-        if (p.real_coef) lw_predict_kernel<true><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
-        else lw_predict_kernel<false><<<(unsigned)((np + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH, k);
-    }
-    if (part != 0) {
-        if (p.real_coef) lw_correct_kernel<true><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
-                                                                                  PhiO, PiO, k);
-        else lw_correct_kernel<false><<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
-                                                                                  PhiO, PiO, k);
-    }
+    if (part != 1)
+        TEUK_PICK(lw_predict_kernel, p.real_coef, p.fixed_point)<<<(unsigned)((np + threads - 1) / threads), threads,
+                                                                    0, st>>>(p, Phi, Pi, PhiH, PiH, k);
+    if (part != 0)
+        TEUK_PICK(lw_correct_kernel, p.real_coef, p.fixed_point)<<<(unsigned)((nc + threads - 1) / threads), threads,
+                                                                    0, st>>>(p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);
     return cudaGetLastError();
 }
 
@@ -645,10 +640,13 @@ int split_theta_tiles(int nth)
     const int tw = split_tile_width(nth);
     return (nth + tw - 1) / tw;
 }
-int split_rows_per_block(int nth)
+// Default tile height: 128-thread CTAs for the fixed-point kernels (up to 128
+// registers per thread: many small CTAs), 256-thread CTAs for the FP64 ones.
+int split_rows_per_block(int nth, int fixed_point)
 {
     const int tw = split_tile_width(nth);
-    return tw >= TEUK_SPLIT_TILE_MAX ? 1 : TEUK_SPLIT_TILE_MAX / tw;
+    const int threads = fixed_point ? TEUK_SPLIT_TILE_MAX : 2 * TEUK_SPLIT_TILE_MAX;
+    return tw >= threads ? 1 : threads / tw;
 }
 
 // Launch bounds of the split kernels.  The single-argument form leaves ptxas
@@ -659,13 +657,15 @@ int split_rows_per_block(int nth)
 #ifndef TEUK_SPLIT_THREADS
 #define TEUK_SPLIT_THREADS kTileMaxThreads
 #endif
+// The FP64 instantiations (FX = false) need far fewer registers; their
+// 1024-thread bound lets ptxas keep them at about 50.
 #ifdef TEUK_SPLIT_MINB
-#define TEUK_SPLIT_BOUNDS __launch_bounds__(TEUK_SPLIT_THREADS, TEUK_SPLIT_MINB)
+#define TEUK_SPLIT_BOUNDS __launch_bounds__(FX ? TEUK_SPLIT_THREADS : 1024, TEUK_SPLIT_MINB)
 #else
-#define TEUK_SPLIT_BOUNDS __launch_bounds__(TEUK_SPLIT_THREADS)
+#define TEUK_SPLIT_BOUNDS __launch_bounds__(FX ? TEUK_SPLIT_THREADS : 1024)
 #endif
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __global__ void TEUK_SPLIT_BOUNDS lw_predict_split(StepParams p, const double2 *__restrict__ Phi,
                                                    const double2 *__restrict__ Pi, double2 *__restrict__ PhiH,
                                                    double2 *__restrict__ PiH, int k)
@@ -694,7 +694,7 @@ __global__ void TEUK_SPLIT_BOUNDS lw_predict_split(StepParams p, const double2 *
         row[TW + 1] = j0 + TW < nth ? add2(ldcg(Phi + kr + j0 + TW), ldcg(Phi + kr + nth + j0 + TW), ops)
                                     : make_double2(0.0, 0.0);
     __syncthreads();
-    HalfStep o = predict_c<REAL>(c, p.q, ops, phi0, pi0, phi1, pi1, row[tx + 2], row[tx]);
+    HalfStep o = predict_c<REAL, FX>(c, p.q, ops, phi0, pi0, phi1, pi1, row[tx + 2], row[tx]);
     const SourceWindow &sw = p.src;
     if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
         const long long n = ldcg(p.step_base) + k;
@@ -707,7 +707,7 @@ __global__ void TEUK_SPLIT_BOUNDS lw_predict_split(StepParams p, const double2 *
     allow_dependents();  // after the last store: the dependent sees only writes made before it
 }
 
-template <bool REAL>
+template <bool REAL, bool FX>
 __global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *__restrict__ Phi,
                                                    const double2 *__restrict__ Pi, const double2 *__restrict__ PhiH,
                                                    const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
@@ -741,7 +741,7 @@ __global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *
                                     : make_double2(0.0, 0.0);
     __syncthreads();
     double2 nphi, npi;
-    correct_c<REAL>(c, p.half_dt, ops, phi, pi, hp, hm, row[tx + 2], row[tx], &nphi, &npi);
+    correct_c<REAL, FX>(c, p.half_dt, ops, phi, pi, hp, hm, row[tx + 2], row[tx], &nphi, &npi);
     const long long n = ldcg(p.step_base) + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
@@ -760,12 +760,12 @@ __global__ void TEUK_SPLIT_BOUNDS lw_correct_split(StepParams p, const double2 *
 
 size_t split_smem_bytes(int nth, int rows)
 {
-    return sizeof(double2) * (size_t)(rows > 0 ? rows : split_rows_per_block(nth)) * (split_tile_width(nth) + 2);
+    return sizeof(double2) * (size_t)(rows > 0 ? rows : split_rows_per_block(nth, 1)) * (split_tile_width(nth) + 2);
 }
-const void *split_kernel_ptr(int which, int real)
+const void *split_kernel_ptr(int which, int real, int fixed_point)
 {
-    if (real) return which ? (const void *)lw_correct_split<true> : (const void *)lw_predict_split<true>;
-    return which ? (const void *)lw_correct_split<false> : (const void *)lw_predict_split<false>;
+    return which ? (const void *)TEUK_PICK(lw_correct_split, real, fixed_point)
+                 : (const void *)TEUK_PICK(lw_predict_split, real, fixed_point);
 }
 
 // part: 0 = predictor only, 1 = corrector only, 2 = both.  rows: r* rows per
@@ -774,7 +774,7 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
                               double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl,
                               int part, int rows)
 {
-    const int R = rows > 0 ? rows : split_rows_per_block(p.nth);
+    const int R = rows > 0 ? rows : split_rows_per_block(p.nth, p.fixed_point);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -788,16 +788,14 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     cudaError_t e = cudaSuccess;
     if (part != 1) {
         cfg.gridDim = dim3((p.nr - 1 + R - 1) / R, tiles);
-        e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_predict_split<true>, p, Phi, Pi, PhiH, PiH, k)
-                        : cudaLaunchKernelEx(&cfg, lw_predict_split<false>, p, Phi, Pi, PhiH, PiH, k);
+        e = cudaLaunchKernelEx(&cfg, TEUK_PICK(lw_predict_split, p.real_coef, p.fixed_point), p, Phi, Pi, PhiH, PiH,
+                               k);
         if (e != cudaSuccess) return e;
     }
     if (part != 0) {
         cfg.gridDim = dim3((p.nr - 2 + R - 1) / R, tiles);
-        e = p.real_coef ? cudaLaunchKernelEx(&cfg, lw_correct_split<true>, p, Phi, Pi, (const double2 *)PhiH,
-                                             (const double2 *)PiH, PhiO, PiO, k)
-                        : cudaLaunchKernelEx(&cfg, lw_correct_split<false>, p, Phi, Pi, (const double2 *)PhiH,
-                                             (const double2 *)PiH, PhiO, PiO, k);
+        e = cudaLaunchKernelEx(&cfg, TEUK_PICK(lw_correct_split, p.real_coef, p.fixed_point), p, Phi, Pi,
+                               (const double2 *)PhiH, (const double2 *)PiH, PhiO, PiO, k);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -886,10 +884,6 @@ __device__ __forceinline__ BatchTile batch_tile(const JobDesc &J, const BatchCur
     return t;
 }
 
-#ifndef TEUK_BATCH_REAL_BRANCH
-#define TEUK_BATCH_REAL_BRANCH 1
-#endif
-
 // Row buffer words (double2) per buffer for a CTA of `block` threads: R rows
 // of tw + 2 with R tw <= block and R <= block / 32.
 __host__ __device__ __forceinline__ int batch_row_words(int block) { return block + 2 * (block / 32); }
@@ -915,7 +909,7 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_predict_batch(const JobDes
         const int hq = min(hp, p.nr - 2);
         double2 *row = rowbuf + (tile & 1) * bw + t.tyc * (tw + 2);
         const size_t k0 = (size_t)hq * nth + t.jj;
-        const bool real = TEUK_BATCH_REAL_BRANCH && p.real_coef != 0;  // uniform over the CTA
+        const bool real = p.real_coef != 0;  // uniform over the CTA
         const PredCoef c = real ? load_pred<true>(p, k0) : load_pred<false>(p, k0);
         if (tile == t0) grid_dependency_wait();
         const int from = J.cur ^ (k & 1);
@@ -934,8 +928,11 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_predict_batch(const JobDes
                                   : make_double2(0.0, 0.0);
         }
         __syncthreads();
-        HalfStep o = real ? predict_c<true>(c, p.q, ops, phi0, pi0, phi1, pi1, row[t.tx + 2], row[t.tx])
-                          : predict_c<false>(c, p.q, ops, phi0, pi0, phi1, pi1, row[t.tx + 2], row[t.tx]);
+        const double2 sup = row[t.tx + 2], sdn = row[t.tx];
+        HalfStep o = real ? (p.fixed_point ? predict_c<true, true>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn)
+                                           : predict_c<true, false>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn))
+                          : (p.fixed_point ? predict_c<false, true>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn)
+                                           : predict_c<false, false>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn));
         const SourceWindow &sw = p.src;
         if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
             const long long n = ldcg(p.step_base) + k;
@@ -972,7 +969,7 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDes
         const int iq = min(i, p.nr - 2);
         double2 *row = rowbuf + (tile & 1) * bw + t.tyc * (tw + 2);
         const size_t kc = (size_t)iq * nth + t.jj;
-        const bool real = TEUK_BATCH_REAL_BRANCH && p.real_coef != 0;
+        const bool real = p.real_coef != 0;
         const CorrCoef c = real ? load_corr<true>(p, kc) : load_corr<false>(p, kc);
         if (tile == t0) grid_dependency_wait();
         const int from = J.cur ^ (k & 1);
@@ -997,10 +994,14 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDes
         }
         __syncthreads();
         double2 nphi, npi;
-        if (real)
-            correct_c<true>(c, p.half_dt, ops, phi, pi, hp, hm, row[t.tx + 2], row[t.tx], &nphi, &npi);
-        else
-            correct_c<false>(c, p.half_dt, ops, phi, pi, hp, hm, row[t.tx + 2], row[t.tx], &nphi, &npi);
+        const double2 sup = row[t.tx + 2], sdn = row[t.tx];
+        if (real) {
+            if (p.fixed_point) correct_c<true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
+            else correct_c<true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
+        } else {
+            if (p.fixed_point) correct_c<false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
+            else correct_c<false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
+        }
         const long long n = ldcg(p.step_base) + k;
         const SourceWindow &sw = p.src;
         if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)

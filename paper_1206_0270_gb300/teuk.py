@@ -33,6 +33,7 @@ TEUK_OPT_BLOCK_THREADS = 3
 TEUK_OPT_REAL_PATH = 4
 TEUK_OPT_SPLIT_ROWS = 5
 TEUK_OPT_BATCH_MODE = 6
+TEUK_OPT_FIXED_POINT = 7
 ERRORS = {-1: "TEUK_ERR_BAD_ARG", -2: "TEUK_ERR_OOM", -3: "TEUK_ERR_CUDA", -4: "TEUK_ERR_NONFINITE",
           -5: "TEUK_ERR_STATE", -6: "TEUK_ERR_OVERFLOW"}
 

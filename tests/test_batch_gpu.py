@@ -167,3 +167,35 @@ def test_batch_bad_arguments(teuk):
         B.set_option(teuk.TEUK_OPT_BLOCK_THREADS, 100)
     assert B.step(0) == 0
     B.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_mixes_fixed_point_and_fp64_jobs(teuk, mode):
+    # jobs with the fixed-point and with the FP64 Pi rows in one batch: each
+    # equals the same job stepped alone with its own setting
+    picks = [0, 2, 3, 5]
+    def build(q):
+        j = JOBS[q]
+        g, _ = make(teuk, j, q)
+        if q % 2 == 0:
+            g.set_option(teuk.TEUK_OPT_FIXED_POINT, 0)
+        return g, j
+    alone = []
+    for q in picks:
+        g, j = build(q)
+        g.step(j["steps"])
+        alone.append(collect(g, j))
+        g.close()
+    B = teuk.Batch()
+    B.set_option(teuk.TEUK_OPT_BATCH_MODE, mode)
+    solvers = []
+    for q in picks:
+        g, j = build(q)
+        solvers.append((g, j))
+        B.add(g, j["steps"])
+    B.step(10 ** 6)
+    B.sync()
+    for (g, j), ref in zip(solvers, alone):
+        for x, y in zip(collect(g, j), ref):
+            np.testing.assert_array_equal(x, y)
+    B.close()

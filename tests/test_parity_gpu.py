@@ -501,3 +501,42 @@ def test_set_stream_keeps_results(teuk):
     b.close()
     np.testing.assert_array_equal(st[0], ref[0])
     np.testing.assert_array_equal(st[1], ref[1])
+
+
+@pytest.mark.parametrize("nr,nth,a,s,m", [(120, 48, 0.9, -2, 2), (90, 300, 0.6, 2, -1), (64, 32, 0.0, -2, 2)])
+def test_all_fp64_option(teuk, nr, nth, a, s, m):
+    # TEUK_OPT_FIXED_POINT 0: every product of the Pi rows as an FP64 FMA.
+    # The kernel variants agree bit for bit among themselves, both settings
+    # agree with the oracle, and they differ from each other only by rounding.
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, a, s, m)
+    u = inputs.random_fields(nr, nth, seed=nr + nth)
+    src = dict(r0=6.0, sigma=1.0)
+    ora = O.Solver(nr, nth, -20.0, 40.0, dt, a, s, m)
+    ora.set_initial(*u)
+    ora.set_source(**src)
+    ora.step(80)
+    ref = ora.state()
+    out = {}
+    for fx in (0, 1):
+        kernels = (0, 1, 2) if nth <= 256 else (1, 2)
+        for kern in kernels:
+            g = teuk.Solver(nr, nth, -20.0, 40.0, dt, a, s, m, kernel=kern)
+            g.set_option(teuk.TEUK_OPT_FIXED_POINT, fx)
+            g.set_initial(*u)
+            g.set_source(**src)
+            g.step(80)
+            st = g.state()
+            g.close()
+            if fx in out:
+                np.testing.assert_array_equal(st[0], out[fx][0])
+                np.testing.assert_array_equal(st[1], out[fx][1])
+            else:
+                out[fx] = st
+        assert rel(out[fx][0], ref[0]) <= TOL and rel(out[fx][1], ref[1]) <= TOL
+    assert rel(out[0][0], out[1][0]) <= TOL
+    with pytest.raises(teuk.TeukError):
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, a, s, m)
+        try:
+            g.set_option(teuk.TEUK_OPT_FIXED_POINT, 2)
+        finally:
+            g.close()
