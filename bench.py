@@ -58,8 +58,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
 # sources whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(predictor=125.86e6 + 16.36e6, corrector=151.01e6 + 19.77e6,
-                   sources_sha256="db3abb72fbb3c38d0846a9076d0760e19620ce393b4391a8c9968c7bee996eb6")
+NCU_TRAFFIC = dict(predictor=125.87e6 + 16.21e6, corrector=151.02e6 + 19.45e6,
+                   sources_sha256="a0da3c9cefd1fca2d8c1b9b72660ed95b45ada4be3af79f67e1da8cd2e4e5c69")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits
