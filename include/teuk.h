@@ -256,20 +256,25 @@ int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in,
  * A template bank is many independent (a, r0, m) evolutions of uneven grid
  * size and length (the paper's motivation for fast waveform generation; its
  * temporal segments are independent evolutions too).  A batch groups
- * existing handles on one device and advances all of its jobs by one time
- * step with one predictor launch and one corrector launch, each CTA working on
- * one tile of one job; the arithmetic per point is that of teuk_step (results
- * are bit-identical to stepping each handle alone).  Jobs advance in slices of
- * min(graph chunk, smallest remaining step count) steps; a job that has taken
- * its steps leaves at the next slice boundary.  Full slices replay a CUDA
- * graph captured for the current set of jobs.
+ * existing handles on one device and advances them together; the arithmetic
+ * per point is that of teuk_step, so results are bit-identical to stepping
+ * each handle alone.  Two modes (TEUK_OPT_BATCH_MODE):
+ *   1 (default): every job advances with its own kernels on its own stream
+ *     (graph replay per chunk), all jobs concurrently and independently;
+ *   0: one persistent predictor and one persistent corrector launch per time
+ *     step work through the theta tiles of every job; jobs advance in slices
+ *     of min(graph chunk, smallest remaining step count) steps, a job that
+ *     has taken its steps leaves at the next slice boundary, and full slices
+ *     replay a CUDA graph captured for the current set of jobs.
+ * teuk_batch_autotune picks the mode (and the persistent launch's CTA size).
  *
- * Rules: a handle in a batch is driven by the batch only -- teuk_step,
- * teuk_set_* , teuk_step_noalloc and teuk_destroy on it return
- * TEUK_ERR_STATE until it is removed (or the batch destroyed); call
- * teuk_batch_sync() before reading a job's results through its handle
- * (teuk_extract, teuk_get_state).  Jobs need nth <= 512.  A batch allocates its job table (and a job's
- * half-step buffer if the handle has none).
+ * Rules: a handle in a batch is driven by the batch only -- teuk_step, the
+ * other teuk_set_* calls (teuk_set_stream excepted), teuk_step_noalloc and
+ * teuk_destroy on it return TEUK_ERR_STATE until it is removed (or the batch
+ * destroyed); call teuk_batch_sync() before reading a job's results through
+ * its handle (teuk_extract, teuk_get_state).  Jobs need nth <= 512.  A batch
+ * allocates its job table (and a job's half-step buffer if the handle has
+ * none).
  * ------------------------------------------------------------------------ */
 typedef struct teuk_batch teuk_batch;
 

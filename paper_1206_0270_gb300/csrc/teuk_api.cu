@@ -167,9 +167,9 @@ struct Arena {
 };
 }  // namespace
 
-// Automatic launch shape: about 16 resident warps per SM (enough to hide
-// the load latency behind the FP64 pipe), in as few, long strips as that
-// allows, since every strip recomputes one predictor row.
+// Automatic launch shape of the fused kernel: about 16 resident warps per SM
+// (enough to hide the load latency), in as few, long strips as that allows,
+// since every strip recomputes one predictor row.
 static void choose_launch(teuk_handle *h, int rows_per_block)
 {
     const int rows = h->nr - 2;

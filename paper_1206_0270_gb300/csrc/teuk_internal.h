@@ -88,11 +88,11 @@ struct StepParams {
     const long long *step_base;  // device: steps completed before this chunk
 };
 
-// One job of a batch: its step parameters and buffers.  A batch advances all
-// of its jobs by one time step with one predictor and one corrector launch;
-// CTA b works on tile b - tile_off[job] of the job with the largest
-// tile_off[job] <= b.  A tile is `rows` consecutive rows of nth values, one
-// thread per value (colpad = nth rounded up to a warp).
+// One job of a batch, as the persistent batch kernels see it: its step
+// parameters and buffers and its tile geometry.  The kernels work through
+// the tiles of all jobs (tile_off[job] is the job's first tile); a tile is
+// `rows` r* rows by `tw` theta columns, one thread per point, and a row has
+// `tiles` theta tiles.
 struct JobDesc {
     StepParams p;
     double2 *phi[2], *pi[2];  // state, ping-pong
