@@ -540,3 +540,16 @@ def test_all_fp64_option(teuk, nr, nth, a, s, m):
             g.set_option(teuk.TEUK_OPT_FIXED_POINT, 2)
         finally:
             g.close()
+
+
+def test_device_allocation_failure_is_reported(teuk):
+    # 2^21 x 4096 points need about 2.3 TB of coefficient planes and state:
+    # creation fails with TEUK_ERR_OOM and the context stays usable
+    with pytest.raises(teuk.TeukError) as err:
+        teuk.Solver(1 << 21, 4096, -100.0, 600.0, 1e-3, 0.5, -2, 2)
+    assert err.value.code == -2  # TEUK_ERR_OOM
+    g = teuk.Solver(64, 32, -20.0, 40.0, 1e-3, 0.5, -2, 2)
+    g.set_initial(*inputs.random_fields(64, 32, seed=3))
+    g.step(4)
+    assert g.check_finite()
+    g.close()
