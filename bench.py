@@ -81,6 +81,16 @@ def sources_sha256():
     return h.hexdigest()
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine's GPUs (MEASURED_PEAKS.json),
+    else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback: 6.8 TB/s, one earlier GB300 measurement"
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -294,6 +304,14 @@ def run_gpu(args):
                     step_in_graph=dict(ms=per_launch_s * 1e3,
                                        tflops=FLOPS_PER_UPDATE * upd_per_launch / per_launch_s / 1e12),
                     hbm_alg_gbs=BYTES_PER_UPDATE_ALG * upd_per_launch / per_launch_s / 1e9)
+    # secondary roof: HBM (not binding here), against the measured copy bandwidth
+    hbm_peak, hbm_src = measured_hbm_gbs()
+    dram_step = (NCU_TRAFFIC["predictor"] + NCU_TRAFFIC["corrector"]) if same_src else None
+    roofline["hbm"] = dict(
+        peak_gbs=hbm_peak, peak_source=hbm_src,
+        algorithmic_gbs=roofline["hbm_alg_gbs"], frac_algorithmic=roofline["hbm_alg_gbs"] / hbm_peak,
+        dram_gbs=None if dram_step is None else dram_step / per_launch_s / 1e9,
+        frac_dram=None if dram_step is None else dram_step / per_launch_s / 1e9 / hbm_peak)
 
     # ---- end to end through the C ABI with host buffers ------------------------------
     pin = lambda: torch.zeros((nr, nth), dtype=torch.complex128, pin_memory=True).numpy()
