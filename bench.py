@@ -519,7 +519,7 @@ def run_serving(args):
     budget = int(args.memory_gb * 2 ** 30)
     # continuous batching, the three scheduling policies
     per_policy = {}
-    for policy in ("fill", "share", "priority"):
+    for policy in ("fill", "share", "priority", "async"):
         svc = S.WaveformService(memory_budget=budget, slice_steps=args.slice, policy=policy)
         for r in reqs:
             svc.submit(r)
@@ -559,6 +559,10 @@ def run_serving(args):
                 share_policy=dict(value=n / per_policy["share"][0], unit="waveforms/s",
                                   latency_s=dict(p50=per_policy["share"][1]["p50"], p99=per_policy["share"][1]["p99"],
                                                  mean=per_policy["share"][1]["mean"])),
+                async_policy=dict(value=n / per_policy["async"][0], unit="waveforms/s",
+                                  latency_s=dict(p50=per_policy["async"][1]["p50"],
+                                                 p99=per_policy["async"][1]["p99"],
+                                                 mean=per_policy["async"][1]["mean"])),
                 priority_policy=dict(value=n / per_policy["priority"][0], unit="waveforms/s",
                                      latency_s=dict(p50=per_policy["priority"][1]["p50"],
                                                     p99=per_policy["priority"][1]["p99"],

@@ -86,15 +86,20 @@ class WaveformService:
     jobs that "fill" would run (the oldest, up to `fill_points`) run on
     high-priority CUDA streams and the others on low-priority ones, so the
     younger jobs take only what the older ones leave of the GPU (the batch's
-    per-job launches run each job on its own stream)."""
+    per-job launches run each job on its own stream).
+    policy="async": no common slices.  Every admitted job runs on its own
+    CUDA stream; the oldest jobs (up to `fill_points`) each get their next
+    slice as soon as their previous one has finished (polled with CUDA
+    events, never waited for), so a small job's samples are streamed and the
+    job retired as soon as it is done, not when the largest job's slice ends."""
 
     def __init__(self, memory_budget: int, slice_steps: int = 640, max_jobs: int = 4096,
                  stream=None, clock: Callable[[], float] = time.perf_counter, policy: str = "fill",
                  fill_points: int = 2_000_000):
         if slice_steps < 2 or slice_steps % 2:
             raise ValueError("slice_steps must be even and >= 2")
-        if policy not in ("share", "fill", "priority"):
-            raise ValueError("policy is 'share', 'fill' or 'priority'")
+        if policy not in ("share", "fill", "priority", "async"):
+            raise ValueError("policy is 'share', 'fill', 'priority' or 'async'")
         self.policy = policy
         self.fill_points = int(fill_points)
         self.budget = int(memory_budget)
@@ -176,12 +181,15 @@ class WaveformService:
             if self._prio is not None:
                 import torch
                 low_stream = torch.cuda.Stream(priority=self._prio[0])
+            elif self.policy == "async":
+                import torch
+                low_stream = torch.cuda.Stream()  # the job's own stream
             g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, self._dt(r), r.a, r.s, r.m, stream=low_stream)
             g.set_source(r0=r.r0, sigma=r.sigma)
             g.set_extraction(r.rstar_ext, r.every, capacity=self.slice // r.every + 2)
             self._used += need
             self._running[rid] = dict(solver=g, job=None, remaining=r.steps, admitted=self.now(), t=[], phi=[],
-                                      need=need, high=False)
+                                      need=need, high=False, stream=low_stream, event=None, inflight=0)
 
     def _schedule(self):
         """Choose the jobs that advance in the next slice and make the batch
@@ -213,6 +221,17 @@ class WaveformService:
             elif st["job"] is None and rid in want:
                 st["job"] = self.batch.add(st["solver"], st["remaining"])
 
+    def _retire(self, rid, fin):
+        st = self._running.pop(rid)
+        if st["job"] is not None:
+            self.batch.remove(st["job"])
+        st["solver"].close()
+        self._used -= st["need"]
+        r = self._requests[rid]
+        t = np.concatenate(st["t"]) if st["t"] else np.zeros(0)
+        phi = np.concatenate(st["phi"]) if st["phi"] else np.zeros((0, r.nth), complex)
+        self.results[rid] = Result(rid, r, t, phi, self._submitted[rid], st["admitted"], fin)
+
     def _drain(self):
         """Stream every running job's new samples; retire finished jobs."""
         self.batch.sync()
@@ -231,22 +250,58 @@ class WaveformService:
                 done.append(rid)
         fin = self.now()
         for rid in done:
-            st = self._running.pop(rid)
-            if st["job"] is not None:
-                self.batch.remove(st["job"])
-            st["solver"].close()
-            self._used -= st["need"]
+            self._retire(rid, fin)
+
+    def _step_async(self) -> bool:
+        """One iteration of the event-driven loop: harvest the jobs whose
+        slice has finished, admit arrivals, give idle jobs of the running set
+        their next slice.  Never blocks on the GPU."""
+        import torch
+        progressed = False
+        for rid in list(self._running):
+            st = self._running[rid]
+            ev = st["event"]
+            if ev is not None and ev.query():
+                t, w = st["solver"].extract(cap=self.slice // self._requests[rid].every + 2)
+                if len(t):
+                    st["t"].append(t)
+                    st["phi"].append(w)
+                st["remaining"] -= st["inflight"]
+                st["inflight"], st["event"] = 0, None
+                progressed = True
+            if st["event"] is None and st["remaining"] == 0:
+                self._retire(rid, self.now())
+                progressed = True
+        self._admit()
+        pts = 0
+        for rid in sorted(self._running, key=lambda q: (self._submitted[q], q)):
+            st = self._running[rid]
+            if pts and pts >= self.fill_points:
+                break
             r = self._requests[rid]
-            nth = r.nth
-            t = np.concatenate(st["t"]) if st["t"] else np.zeros(0)
-            phi = np.concatenate(st["phi"]) if st["phi"] else np.zeros((0, nth), complex)
-            self.results[rid] = Result(rid, r, t, phi, self._submitted[rid], st["admitted"], fin)
+            pts += r.nr * r.nth
+            if st["event"] is None and st["remaining"] > 0:
+                n = min(self.slice, st["remaining"])
+                st["solver"].step(n)
+                ev = torch.cuda.Event()
+                ev.record(st["stream"])
+                st["event"], st["inflight"] = ev, n
+                self.slices += 1
+                progressed = True
+        if not progressed:
+            if not self._running and not self._queue:
+                return False
+            wait = self._queue[0][0] - self.now() if (self._queue and not self._running) else 0.0
+            time.sleep(min(max(wait, 0.0005), 0.01))
+        return True
 
     def step(self) -> bool:
         """One service iteration: launch a slice for the admitted jobs, admit
         arrivals (their set-up overlaps the slice), then stream samples and
         retire finished jobs.  New jobs join the batch at the next slice.
         Returns False when nothing is queued or running."""
+        if self.policy == "async":
+            return self._step_async()
         had_jobs = bool(self._running)
         if had_jobs:
             self._schedule()

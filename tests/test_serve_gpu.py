@@ -37,7 +37,8 @@ def run_alone(S, r):
     return res[rid]
 
 
-@pytest.mark.parametrize("policy,fill", [("share", 0), ("fill", 60000), ("fill", 1), ("priority", 60000)])
+@pytest.mark.parametrize("policy,fill", [("share", 0), ("fill", 60000), ("fill", 1), ("priority", 60000),
+                                         ("async", 60000), ("async", 1)])
 def test_results_same_alone_and_in_the_mix(serve, policy, fill):
     S = serve
     rs = reqs(S) + [S.Request(a=0.2, s=-2, m=2, nr=100, nth=8, steps=0, sigma=3.0, rstar_ext=10.0)]
