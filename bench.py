@@ -517,36 +517,53 @@ def run_serving(args):
     reqs = [request(d) for d in raw]
     upd = sum((r.nr - 2) * r.nth * r.steps for r in reqs)
     budget = int(args.memory_gb * 2 ** 30)
-    # continuous batching, the three scheduling policies
-    per_policy = {}
-    for policy in ("fill", "share", "priority", "async"):
+
+    def served(reqs, policy):
         svc = S.WaveformService(memory_budget=budget, slice_steps=args.slice, policy=policy)
         for r in reqs:
             svc.submit(r)
         torch.cuda.synchronize()
         t0 = svc.now()
         res = svc.run()
-        per_policy[policy] = (svc.now() - t0, S.latency_stats(res))
+        out = (svc.now() - t0, S.latency_stats(res))
         svc.close()
+        return out
+
+    def one_at_a_time(reqs):
+        """Same kernels, no batching: each job runs alone, in arrival order."""
+        t_start = time.perf_counter()
+        lat = []
+        for r in reqs:
+            now = time.perf_counter() - t_start
+            if now < r.arrival:
+                time.sleep(r.arrival - now)
+            dt = T.stable_dt(r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m, r.c_r, r.c_theta)
+            g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, dt, r.a, r.s, r.m)
+            g.set_source(r0=r.r0, sigma=r.sigma)
+            g.set_extraction(r.rstar_ext, r.every, capacity=r.steps // r.every + 1)
+            g.step(r.steps)
+            g.extract()
+            g.close()
+            lat.append(time.perf_counter() - t_start - r.arrival)
+        return time.perf_counter() - t_start, np.array(lat)
+
+    # continuous batching, the four scheduling policies
+    per_policy = {policy: served(reqs, policy) for policy in ("fill", "share", "priority", "async")}
     wall, st = per_policy["fill"]
-    # one job at a time, arrival order (same kernels, no batching)
-    t_start = time.perf_counter()
-    lat1, clock = [], 0.0
-    for r in reqs:
-        now = time.perf_counter() - t_start
-        if now < r.arrival:
-            time.sleep(r.arrival - now)
-        dt = T.stable_dt(r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m, r.c_r, r.c_theta)
-        g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, dt, r.a, r.s, r.m)
-        g.set_source(r0=r.r0, sigma=r.sigma)
-        g.set_extraction(r.rstar_ext, r.every, capacity=r.steps // r.every + 1)
-        g.step(r.steps)
-        g.extract()
-        g.close()
-        lat1.append(time.perf_counter() - t_start - r.arrival)
-    wall1 = time.perf_counter() - t_start
-    lat1 = np.array(lat1)
+    wall1, lat1 = one_at_a_time(reqs)
     n = len(reqs)
+    # arrival-rate sweep in multiples of the one-at-a-time capacity (the same
+    # jobs; only the arrival times scale)
+    sweep = []
+    for mult in [float(x) for x in args.rate_sweep.split(",") if x.strip()]:
+        rate = mult * n / wall1
+        rq = [request(d) for d in inputs.serving_requests(args.requests, rate)]
+        w_f, st_f = served(rq, "fill")
+        w_1, l_1 = one_at_a_time(rq)
+        sweep.append(dict(rate_per_s=rate, load=mult,
+                          fill=dict(value=n / w_f, p50=st_f["p50"], p99=st_f["p99"], mean=st_f["mean"]),
+                          one_by_one=dict(value=n / w_1, p50=float(np.percentile(l_1, 50)),
+                                          p99=float(np.percentile(l_1, 99)), mean=float(l_1.mean()))))
     line = dict(metric="served waveforms/s", value=n / wall, unit="waveforms/s", n_gpus=1, steps=1, warmup=0,
                 ms_per_step=1e3 * wall, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic",
@@ -569,7 +586,8 @@ def run_serving(args):
                                                     mean=per_policy["priority"][1]["mean"])),
                 one_by_one=dict(value=n / wall1, unit="waveforms/s",
                                 latency_s=dict(p50=float(np.percentile(lat1, 50)),
-                                               p99=float(np.percentile(lat1, 99)), mean=float(lat1.mean()))))
+                                               p99=float(np.percentile(lat1, 99)), mean=float(lat1.mean()))),
+                rate_sweep=sweep)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -597,6 +615,9 @@ def main():
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--slice", type=int, default=640, help="serving: time steps per batch slice")
+    ap.add_argument("--rate-sweep", default="0.5,1,2",
+                    help="serving: arrival rates to sweep, as multiples of the measured one-at-a-time capacity "
+                         "('' to skip)")
     ap.add_argument("--memory-gb", type=float, default=200.0, help="serving: device memory budget (GiB)")
     args = ap.parse_args()
     if args.workload == "serving":
