@@ -1,0 +1,206 @@
+"""Host logic of the waveform service (paper_1206_0270_gb300/serve.py) on the
+CPU: admission by device-memory footprint in arrival order, arrivals not
+admitted early, the "fill" and "share" scheduling policies, waveform
+assembly across slices, retirement and the argument checks.  The library's
+Solver and Batch are replaced by fakes that count time steps and produce
+samples exactly where the real extraction would (every `every` steps), and
+the service runs on a fake clock; nothing here touches a GPU."""
+import numpy as np
+import pytest
+
+from paper_1206_0270_gb300 import serve as S
+
+
+class FakeSolver:
+    def __init__(self, nr, nth, rstar_min, rstar_max, dt, a, s, m, stream=None):
+        self.nr, self.nth, self.dt = nr, nth, dt
+        self.n = 0
+        self.every = None
+        self.pending = []
+        self.closed = False
+        self.advanced_at = []      # batch slice index of every advance
+
+    def set_source(self, **kw):
+        pass
+
+    def set_extraction(self, rstar_ext, every, capacity):
+        self.every, self.capacity = every, capacity
+
+    def advance(self, n, tick):
+        for _ in range(n):
+            self.n += 1
+            if self.n % self.every == 0:
+                self.pending.append(self.n)
+        assert len(self.pending) <= self.capacity, "ring buffer would have overflowed"
+        if n:
+            self.advanced_at.append(tick)
+
+    def extract(self, cap):
+        k, self.pending = self.pending[:cap], self.pending[cap:]
+        t = np.array(k, dtype=float) * self.dt
+        return t, np.outer(t, np.arange(1, self.nth + 1)).astype(complex)
+
+    def close(self):
+        self.closed = True
+
+
+class FakeBatch:
+    def __init__(self, stream=None):
+        self.jobs, self.next, self.ticks = {}, 0, 0
+
+    def set_option(self, option, value):
+        pass
+
+    def add(self, solver, steps):
+        jid = self.next
+        self.next += 1
+        self.jobs[jid] = [solver, int(steps)]
+        return jid
+
+    def remove(self, jid):
+        del self.jobs[jid]
+
+    def step(self, max_steps):
+        # each job advances min(max_steps, its remaining steps)
+        for job in self.jobs.values():
+            n = min(max_steps, job[1])
+            job[0].advance(n, self.ticks)
+            job[1] -= n
+        self.ticks += 1
+
+    def remaining(self, jid):
+        return self.jobs[jid][1]
+
+    def sync(self):
+        pass
+
+    def close(self):
+        pass
+
+
+class FakeLib:
+    TEUK_OPT_GRAPH_CHUNK = 4
+    Solver = FakeSolver
+    Batch = FakeBatch
+    made = []
+
+    @staticmethod
+    def stable_dt(nr, nth, rmin, rmax, a, s, m, c_r=0.5, c_theta=0.1):
+        return 0.25
+
+
+class Clock:
+    """Advances by `tick` seconds per reading: the loop always makes progress."""
+    def __init__(self, tick=1e-3):
+        self.t, self.tick = 0.0, tick
+
+    def __call__(self):
+        self.t += self.tick
+        return self.t
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    made = []
+
+    class Tracking(FakeSolver):
+        def __init__(self, *args, **kw):
+            super().__init__(*args, **kw)
+            made.append(self)
+    lib = type("Lib", (FakeLib,), {"Solver": Tracking})
+    monkeypatch.setattr(S, "T", lib)
+    monkeypatch.setattr(S.time, "sleep", lambda s: None)
+    return made
+
+
+def request(nr=64, nth=8, steps=100, arrival=0.0, every=10):
+    return S.Request(a=0.5, s=-2, m=2, nr=nr, nth=nth, steps=steps, arrival=arrival, every=every)
+
+
+def run(svc, watch=None):
+    while svc.step():
+        assert svc.memory_in_use() <= svc.budget
+        if watch is not None:
+            watch(svc)
+    return svc.results
+
+
+def test_admission_by_footprint_in_arrival_order(fake):
+    slice_steps = 20
+    need = S.footprint_bytes(request(), slice_steps)
+    svc = S.WaveformService(memory_budget=2 * need + need // 2, slice_steps=slice_steps,
+                            clock=Clock(), policy="share")
+    rids = [svc.submit(request(steps=40 + 20 * k)) for k in range(5)]
+    seen = []
+    res = run(svc, lambda s: seen.append(s.running()))
+    assert max(seen) == 2                       # two fit the budget, never three
+    assert sorted(res) == rids
+    adm = [res[r].admitted for r in rids]
+    assert adm == sorted(adm)                   # first come, first served
+    assert all(s.closed for s in fake) and svc.memory_in_use() == 0
+    svc.close()
+
+
+def test_waveform_samples_are_complete_and_ordered(fake):
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), policy="share")
+    steps = [0, 7, 20, 55, 130]
+    rids = [svc.submit(request(steps=n, every=5)) for n in steps]
+    res = run(svc)
+    for rid, n in zip(rids, steps):
+        r = res[rid]
+        expect = np.arange(5, n + 1, 5) * 0.25
+        np.testing.assert_array_equal(r.t, expect)
+        np.testing.assert_array_equal(r.phi, np.outer(expect, np.arange(1, 9)).astype(complex))
+        assert r.finished >= r.admitted >= r.submitted
+    svc.close()
+
+
+def test_arrivals_are_not_admitted_early(fake):
+    clock = Clock(tick=1e-3)
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=clock, policy="share")
+    early = svc.submit(request(steps=20, arrival=0.0))
+    late = svc.submit(request(steps=20, arrival=0.5))
+    res = run(svc)
+    assert res[late].admitted >= 0.5 and res[late].submitted == 0.5
+    assert res[early].admitted < 0.5
+    svc.close()
+
+
+def test_fill_runs_the_oldest_jobs_first(fake):
+    # fill_points = one job's grid: the jobs run one after another, in arrival order
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), policy="fill",
+                            fill_points=64 * 8)
+    for _ in range(3):
+        svc.submit(request(steps=60))
+    run(svc)
+    spans = [(min(s.advanced_at), max(s.advanced_at)) for s in fake]
+    assert spans[0][1] < spans[1][0] and spans[1][1] < spans[2][0], spans
+    svc.close()
+
+
+def test_share_advances_every_admitted_job(fake):
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), policy="share")
+    for _ in range(3):
+        svc.submit(request(steps=60))
+    run(svc)
+    ticks = [s.advanced_at for s in fake]
+    assert ticks[0] == ticks[1] == ticks[2] and len(ticks[0]) == 3
+    svc.close()
+
+
+def test_argument_checks(fake):
+    with pytest.raises(ValueError):
+        S.WaveformService(memory_budget=1 << 30, slice_steps=7)
+    with pytest.raises(ValueError):
+        S.WaveformService(memory_budget=1 << 30, policy="lifo")
+    svc = S.WaveformService(memory_budget=1 << 20, slice_steps=20, clock=Clock())
+    with pytest.raises(ValueError):
+        svc.submit(request(nr=4096, nth=256))   # larger than the whole budget
+    svc.close()
+
+
+def test_latency_stats():
+    assert S.latency_stats({})["n"] == 0
+    res = {i: S.Result(i, request(), np.zeros(0), np.zeros((0, 8)), 0.0, 0.0, float(i + 1)) for i in range(100)}
+    st = S.latency_stats(res)
+    assert st["p50"] == pytest.approx(50.5) and st["mean"] == pytest.approx(50.5)
