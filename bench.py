@@ -33,6 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "kerr_a0.9_s-2_m2_8192x128_r0_10"
+HBM_PROBE = "kerr_a0.9_s-2_m2_32768x512_r0_10"   # state far beyond L2: where "% of HBM roof" is quoted
 METRIC = "FP64 grid-pt updates/s"
 UNIT = "grid-pt updates/s"
 # FP64 work of one interior point update in the folded formulation of
@@ -365,6 +366,7 @@ def run_gpu(args):
     all_fp64 = dict(value=whole_job_rate(ws, upd_per_step * n_fp64, fp64_ms / 1e3), unit=UNIT, steps=n_fp64,
                     arithmetic="every Pi-row product as an FP64 FMA (TEUK_OPT_FIXED_POINT 0)")
     F.close()
+    hbm_probe = run_hbm_probe(T, stream, ws, hbm_peak, hbm_src, same_src) if args.hbm_probe else None
 
     if rank != 0:
         S.close()
@@ -380,7 +382,7 @@ def run_gpu(args):
                                        "rounded once to FP64 (error <= n 2^-57 max|c x| + 2^-53 |sum|)",
                             l2="inputs larger than L2 (state 2x33.5 MB + coefficients 193 MB per time step)",
                             parallelism="replicas" if ws > 1 else "single GPU"),
-                roofline=roofline, e2e=e2e, gpu_launches=int(launches), all_fp64=all_fp64,
+                roofline=roofline, e2e=e2e, gpu_launches=int(launches), all_fp64=all_fp64, hbm_probe=hbm_probe,
                 step_ms_min=min(step_ms), step_ms_median=statistics.median(step_ms))
     clocks = clk.summary()
     if clocks:
@@ -399,6 +401,49 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     S.close()
     return 0
+
+
+def run_hbm_probe(T, stream, ws, hbm_peak, hbm_src, same_src, chunk=64, reps=6):
+    """The same physics on 32768 x 512 (state 2 x 537 MB, planes 2.8 GB per
+    time step: far beyond L2): point updates/s and the HBM figures on a grid
+    where every time step must stream its whole working set from DRAM."""
+    import torch
+    from paper_1206_0270_gb300 import inputs
+    w = dict(inputs.WORKLOADS[HBM_PROBE])
+    nr, nth = w["nr"], w["nth"]
+    dt = T.stable_dt(nr, nth, w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], w["c_r"], w["c_theta"])
+    P = T.Solver(nr, nth, w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"], stream=stream)
+    try:
+        P.set_initial(np.zeros((nr, nth), complex), np.zeros((nr, nth), complex))
+        P.set_source(**w["source"])
+        ex = w["extraction"]
+        P.set_extraction(ex["rstar"], ex["every"], capacity=chunk * (reps + 3) // ex["every"] + 16)
+        for _ in range(2):
+            P.step(chunk)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            P.step(chunk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = reduce_max(e0.elapsed_time(e1), "cuda")
+        assert P.check_finite(), "state became non-finite"
+    finally:
+        P.close()
+    upd = (nr - 2) * nth * chunk * reps
+    rate = upd / (ms / 1e3)
+    alg = BYTES_PER_UPDATE_ALG * rate / 1e9
+    # DRAM bytes per point update from the 8192 x 128 capture, scaled by the
+    # points processed (traffic is proportional to the grid: planes, state and
+    # half step are each read or written once per step)
+    dram_per_upd = (NCU_TRAFFIC["predictor"] + NCU_TRAFFIC["corrector"]) / (8190 * 128) if same_src else None
+    return dict(workload=HBM_PROBE, nr=nr, nth=nth, time_steps=chunk * reps,
+                value=whole_job_rate(ws, upd, ms / 1e3), unit=UNIT, peak_gbs=hbm_peak, peak_source=hbm_src,
+                algorithmic_gbs=alg, frac_algorithmic=alg / hbm_peak,
+                dram_gbs=None if dram_per_upd is None else dram_per_upd * rate / 1e9,
+                frac_dram=None if dram_per_upd is None else dram_per_upd * rate / 1e9 / hbm_peak,
+                dram_source="ncu bytes per point update on 8192 x 128, scaled to this grid")
 
 
 # ---------------------------------------------------------------------------
@@ -604,6 +649,8 @@ def main():
     ap.add_argument("--kernel-timing-steps", type=int, default=64,
                     help="steps timed kernel by kernel (after the timed region) for the roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm-probe", dest="hbm_probe", action="store_false",
+                    help="skip the 32768 x 512 HBM-roof probe")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batch_modes", "template_bank", "serving"],
                     help="single: the Kerr 8192x128 step (default); batch_modes / template_bank: batched "
