@@ -459,6 +459,12 @@ def batch_jobs(kind, scale):
         for m, nth in w["modes"]:
             jobs.append(dict(a=w["a"], s=w["s"], m=m, nr=w["nr"], nth=nth, r0=w["r0"], sigma=w["sigma"],
                              steps=max(2, int(round(w["steps"] * scale)))))
+    elif kind == "small_bank":
+        for j in inputs.small_bank(128):
+            j = dict(j)
+            j["sigma"] = max(0.05, 2.0 * 700.0 / (j["nr"] - 1))
+            j["steps"] = max(2, int(round(j["steps"] * scale)))
+            jobs.append(j)
     else:
         for j in inputs.template_bank(256):
             j = dict(j)
@@ -652,7 +658,7 @@ def main():
     ap.add_argument("--no-hbm-probe", dest="hbm_probe", action="store_false",
                     help="skip the 32768 x 512 HBM-roof probe")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batch_modes", "template_bank", "serving"],
+                    choices=["single", "batch_modes", "template_bank", "small_bank", "serving"],
                     help="single: the Kerr 8192x128 step (default); batch_modes / template_bank: batched "
                          "waveforms/s against one job at a time")
     ap.add_argument("--steps-scale", type=float, default=0.2,

@@ -118,6 +118,19 @@ def template_bank(n_jobs: int, seed: int = 20120603):
     return jobs
 
 
+def small_bank(n_jobs: int = 128, seed: int = 20120605):
+    """A bank of small evolutions (the regime in which a single job cannot
+    fill the GPU): a ~ U[0, 0.95], r0 ~ U[6, 20] M, m ~ U{1..4}, s = -2,
+    nr ~ U{256, 512}, nth ~ U{16, 32}, steps ~ logU[1e4, 4e4]."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for _ in range(n_jobs):
+        jobs.append(dict(a=float(rng.uniform(0.0, 0.95)), r0=float(rng.uniform(6.0, 20.0)), m=int(rng.integers(1, 5)),
+                         s=-2, nr=int(rng.choice([256, 512])), nth=int(rng.choice([16, 32])),
+                         steps=int(round(10 ** rng.uniform(4.0, np.log10(4e4))))))
+    return jobs
+
+
 def serving_requests(n: int, rate: float, seed: int = 20120604, step_range=(1e3, 1e4),
                      grids=((2048, 64), (4096, 64), (4096, 128), (8192, 128), (16384, 256), (32768, 512)),
                      grid_weights=(0.25, 0.25, 0.2, 0.2, 0.08, 0.02)):
