@@ -138,6 +138,36 @@ def test_parity_kerr_8192x128_full_grid(teuk):
     assert_parity(out)
 
 
+def test_parity_32768x512_sampled_rows(teuk):
+    """The largest grid of the workloads (32768 x 512: four theta tiles per
+    row) in the benchmark's launch configuration, one graph chunk of 64 steps
+    from random smooth data, no source.  After N steps a node depends only on
+    rows i - N .. i + N, so the oracle computes sampled rows exactly on a strip
+    of 2N + 3 rows with the same spacing and time step (whose edge rows, N + 1
+    away, cannot reach the sampled row); strips that touch the true radial
+    boundaries keep them."""
+    nr, nth, rmin, rmax, a, s, m, N = 32768, 512, -100.0, 600.0, 0.9, -2, 2, 64
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
+    h = (rmax - rmin) / (nr - 1)
+    phi0, pi0 = inputs.random_fields(nr, nth, seed=11)
+    g = teuk.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    g.set_initial(phi0, pi0)
+    g.step(N)
+    pg, qg = g.state()
+    g.close()
+    assert np.all(np.isfinite(pg)) and np.all(np.isfinite(qg))
+    for i in (1, 40, 9000, 20011, 32727, nr - 2):
+        lo, hi = max(0, i - N - 1), min(nr - 1, i + N + 1)
+        ora = O.Solver(hi - lo + 1, nth, rmin + lo * h, rmin + hi * h, dt, a, s, m)
+        ora.set_initial(phi0[lo:hi + 1], pi0[lo:hi + 1])
+        ora.step(N)
+        po, qo = ora.state()
+        assert rel(pg[i], po[i - lo]) <= TOL, (i, rel(pg[i], po[i - lo]))
+        assert rel(qg[i], qo[i - lo]) <= TOL, (i, rel(qg[i], qo[i - lo]))
+    # the radial boundary rows stay exactly zero
+    assert not pg[0].any() and not pg[-1].any() and not qg[0].any() and not qg[-1].any()
+
+
 def test_graph_and_direct_launches_agree_bitwise(teuk):
     kw = dict(source=SRC, ext=(10.0, 5), seed=2)
     a = run_pair(teuk, 120, 40, -20.0, 40.0, 0.8, -2, 2, 200, chunks=[200], **kw)
