@@ -2,13 +2,14 @@
 
 Requests (one (a, s, m) evolution each) queue up; the service admits them
 while their device footprint fits in a memory budget, keeps every admitted
-job's state resident on the device, advances all admitted jobs together in
-slices of time steps (one teuk_batch: shared predictor/corrector launches),
-streams each job's waveform samples to the host after every slice, and
+job's state resident on the device, advances admitted jobs in slices of time
+steps, streams each job's waveform samples to the host after every slice, and
 retires finished jobs so that their memory and slot admit the next requests.
-Requests that arrive while others are running join at the next slice
-boundary.  Results do not depend on the mix: a job's arithmetic is the same
-alone and in any batch (bit-identical).
+Requests that arrive while others are running join without waiting for them.
+The scheduling policies are described on WaveformService; the default
+("async") gives every job its own CUDA stream with a priority by age.
+Results do not depend on the mix: a job's arithmetic is the same alone and
+in any batch (bit-identical).
 
 All device work runs in libteuk (teuk_create / teuk_batch_* / teuk_extract);
 this module only schedules.
@@ -74,7 +75,7 @@ class Result:
 
 
 class WaveformService:
-    """Continuous batching over teuk_batch with admission by device memory.
+    """Continuous batching with admission by device memory.
 
     policy="share": every admitted job advances in every slice (processor
     sharing: short jobs finish early, long ones stretch).
@@ -87,15 +88,20 @@ class WaveformService:
     high-priority CUDA streams and the others on low-priority ones, so the
     younger jobs take only what the older ones leave of the GPU (the batch's
     per-job launches run each job on its own stream).
-    policy="async": no common slices.  Every admitted job runs on its own
+    policy="async" (default): no common slices.  Every admitted job runs on its own
     CUDA stream; the oldest jobs (up to `fill_points`) each get their next
     slice as soon as their previous one has finished (polled with CUDA
     events, never waited for), so a small job's samples are streamed and the
-    job retired as soon as it is done, not when the largest job's slice ends."""
+    job retired as soon as it is done, not when the largest job's slice ends.
+    With `age_priority` (default) the streams carry CUDA priorities by age
+    rank among the running jobs (the oldest highest, promoted as older jobs
+    retire): a younger job's kernels then take only the SMs an older job's
+    kernels leave free, as in first-come first-served order, instead of
+    slowing a small older job down to the pace of a large younger one."""
 
     def __init__(self, memory_budget: int, slice_steps: int = 640, max_jobs: int = 4096,
-                 stream=None, clock: Callable[[], float] = time.perf_counter, policy: str = "fill",
-                 fill_points: int = 2_000_000):
+                 stream=None, clock: Callable[[], float] = time.perf_counter, policy: str = "async",
+                 fill_points: int = 2_000_000, age_priority: bool = True):
         if slice_steps < 2 or slice_steps % 2:
             raise ValueError("slice_steps must be even and >= 2")
         if policy not in ("share", "fill", "priority", "async"):
@@ -122,11 +128,8 @@ class WaveformService:
         # (teuk_stable_dt scans the whole grid; the ctypes call releases the GIL)
         self._pool = cf.ThreadPoolExecutor(max_workers=4)
         self.slices = 0
-        self._prio = None
-        if policy == "priority":
-            import torch
-            low, high = torch.cuda.Stream.priority_range()  # least and greatest priority
-            self._prio = (low, high)
+        self.age_priority = bool(age_priority) and policy == "async"
+        self._prio = None           # (least, greatest) CUDA stream priority, read at the first admission
 
     # -- clock -------------------------------------------------------------
     def now(self) -> float:
@@ -176,6 +179,9 @@ class WaveformService:
             if r.dt is None and not self._dt_cache[self._dt_future(r)].done() and self._running:
                 break                      # its time step is still being prepared; others keep running
             heapq.heappop(self._queue)
+            if self._prio is None and (self.policy == "priority" or self.age_priority):
+                import torch
+                self._prio = torch.cuda.Stream.priority_range()  # least and greatest priority
             # each handle sets up on its own stream, concurrently with the running slice
             low_stream = None
             if self._prio is not None:
@@ -189,7 +195,8 @@ class WaveformService:
             g.set_extraction(r.rstar_ext, r.every, capacity=self.slice // r.every + 2)
             self._used += need
             self._running[rid] = dict(solver=g, job=None, remaining=r.steps, admitted=self.now(), t=[], phi=[],
-                                      need=need, high=False, stream=low_stream, event=None, inflight=0)
+                                      need=need, high=False, stream=low_stream, event=None, inflight=0,
+                                      level=None if self._prio is None else self._prio[0])
 
     def _schedule(self):
         """Choose the jobs that advance in the next slice and make the batch
@@ -274,13 +281,21 @@ class WaveformService:
                 progressed = True
         self._admit()
         pts = 0
-        for rid in sorted(self._running, key=lambda q: (self._submitted[q], q)):
+        for rank, rid in enumerate(sorted(self._running, key=lambda q: (self._submitted[q], q))):
             st = self._running[rid]
             if pts and pts >= self.fill_points:
                 break
             r = self._requests[rid]
             pts += r.nr * r.nth
             if st["event"] is None and st["remaining"] > 0:
+                if self.age_priority:
+                    # CUDA priorities: smaller numbers are higher, from high (greatest)
+                    # up to low (least); the oldest job gets the greatest
+                    want = min(self._prio[1] + rank, self._prio[0])
+                    if want < st["level"]:     # promote, never demote
+                        st["stream"] = torch.cuda.Stream(priority=want)
+                        st["solver"].set_stream(st["stream"])
+                        st["level"] = want
                 n = min(self.slice, st["remaining"])
                 st["solver"].step(n)
                 ev = torch.cuda.Event()
