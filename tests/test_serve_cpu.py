@@ -1,10 +1,13 @@
 """Host logic of the waveform service (paper_1206_0270_gb300/serve.py) on the
 CPU: admission by device-memory footprint in arrival order, arrivals not
-admitted early, the "fill" and "share" scheduling policies, waveform
-assembly across slices, retirement and the argument checks.  The library's
-Solver and Batch are replaced by fakes that count time steps and produce
-samples exactly where the real extraction would (every `every` steps), and
-the service runs on a fake clock; nothing here touches a GPU."""
+admitted early, the "fill" and "share" scheduling policies, the default
+"async" policy (per-job streams, completion events, priorities by age rank
+and their promotion), waveform assembly across slices, retirement and the
+argument checks.  The library's Solver and Batch are replaced by fakes that
+count time steps and produce samples exactly where the real extraction
+would (every `every` steps), CUDA events and streams by fakes whose work
+completes when recorded, and the service runs on a fake clock; nothing here
+touches a GPU."""
 import numpy as np
 import pytest
 
@@ -19,6 +22,16 @@ class FakeSolver:
         self.pending = []
         self.closed = False
         self.advanced_at = []      # batch slice index of every advance
+        self.priorities = [getattr(stream, "priority", None)]
+        self.ticks = None          # shared step log of the async loop
+
+    def set_stream(self, stream=None):
+        self.priorities.append(stream.priority)
+
+    def step(self, n):             # the async policy steps handles directly
+        self.advance(n, None)
+        if self.ticks is not None:
+            self.ticks.append(self)
 
     def set_source(self, **kw):
         pass
@@ -204,3 +217,90 @@ def test_latency_stats():
     res = {i: S.Result(i, request(), np.zeros(0), np.zeros((0, 8)), 0.0, 0.0, float(i + 1)) for i in range(100)}
     st = S.latency_stats(res)
     assert st["p50"] == pytest.approx(50.5) and st["mean"] == pytest.approx(50.5)
+
+
+# ---------------------------------------------------------------------------
+# The async policy (default): per-job streams, events, priorities by age
+# ---------------------------------------------------------------------------
+
+class FakeEvent:
+    """Work on the fake streams completes as soon as it is recorded."""
+    def __init__(self):
+        self.recorded = False
+
+    def record(self, stream):
+        self.recorded = True
+
+    def query(self):
+        return self.recorded
+
+
+class FakeStream:
+    def __init__(self, priority=0):
+        self.priority = priority
+
+    @staticmethod
+    def priority_range():
+        return (0, -5)             # least, greatest
+
+
+@pytest.fixture
+def fake_cuda(monkeypatch, fake):
+    import sys
+    import types
+    torch = types.SimpleNamespace(cuda=types.SimpleNamespace(Event=FakeEvent, Stream=FakeStream,
+                                                             synchronize=lambda: None))
+    monkeypatch.setitem(sys.modules, "torch", torch)
+    return fake
+
+
+def test_async_policy_completes_every_job(fake_cuda):
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock())
+    assert svc.policy == "async"
+    steps = [0, 7, 45, 130]
+    rids = [svc.submit(request(steps=n, every=5)) for n in steps]
+    res = run(svc)
+    for rid, n in zip(rids, steps):
+        np.testing.assert_array_equal(res[rid].t, np.arange(5, n + 1, 5) * 0.25)
+    assert all(s.closed for s in fake_cuda) and svc.memory_in_use() == 0
+    svc.close()
+
+
+def test_async_priorities_follow_age_and_promote(fake_cuda):
+    # four equal jobs admitted at once: the oldest runs at the greatest
+    # priority (-5), the next at -4, ...; as older jobs retire the younger are
+    # promoted, never demoted
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock())
+    for k in range(4):
+        svc.submit(request(steps=40 + 20 * k))
+    run(svc)
+    first = [s.priorities[1] for s in fake_cuda]
+    assert first == [-5, -4, -3, -2], first
+    for s in fake_cuda:
+        assert s.priorities[0] == 0                                  # admitted at the least priority
+        assert all(b < a for a, b in zip(s.priorities[1:], s.priorities[2:]))  # only promotions
+    assert fake_cuda[3].priorities[-1] == -5                          # the last job ends up oldest
+    svc.close()
+
+
+def test_async_runs_oldest_jobs_up_to_fill_points(fake_cuda):
+    log = []
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), fill_points=64 * 8)
+    for _ in range(3):
+        svc.submit(request(steps=60))
+    svc._admit()
+    for s in fake_cuda:
+        s.ticks = log
+    run(svc)
+    order = [fake_cuda.index(s) for s in log]
+    assert order == sorted(order), order      # one job at a time, in arrival order
+    svc.close()
+
+
+def test_age_priority_can_be_switched_off(fake_cuda):
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), age_priority=False)
+    for _ in range(2):
+        svc.submit(request(steps=40))
+    run(svc)
+    assert all(s.priorities == [0] for s in fake_cuda)   # default-priority streams, never moved
+    svc.close()
