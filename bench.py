@@ -654,8 +654,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=640, help="time steps per benchmark step")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--ref-steps", type=int, default=10, help="oracle time steps per reference step")
-    ap.add_argument("--cpu-sample-steps", type=int, default=200)
+    ap.add_argument("--ref-steps", type=int, default=100,
+                    help="oracle time steps per reference step (~0.2 s of host work each)")
+    ap.add_argument("--cpu-sample-steps", type=int, default=4000,
+                    help="oracle time steps of the cpu_baseline sample (~10 s of host work)")
     ap.add_argument("--kernel-timing-steps", type=int, default=64,
                     help="steps timed kernel by kernel (after the timed region) for the roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
