@@ -125,6 +125,35 @@ def test_fallback_conditions():
         T.fixed_dot(np.ones((2, 17)), np.ones((2, 17)))
 
 
+def test_bound_and_fallbacks_for_arbitrary_fp64_operands():
+    """Property test over arbitrary finite FP64 operands (any exponent,
+    subnormals and signed zeros included): wherever the sum reports success
+    it meets the bound; it falls back only where the exact sum lies below
+    2^-820 or above 2^1020 (the tiny-result and overflow rules)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    finite = st.floats(allow_nan=False, allow_infinity=False, width=64)
+    # coefficients as the kernels see them: normal numbers or exact zeros
+    coef = st.one_of(st.just(0.0), st.floats(min_value=2.0 ** -60, max_value=2.0 ** 60).map(float),
+                     st.floats(min_value=-2.0 ** 60, max_value=-2.0 ** -60).map(float))
+
+    @hyp.settings(max_examples=400, deadline=None, derandomize=True)
+    @hyp.given(st.integers(1, 16).flatmap(lambda n: st.tuples(
+        st.lists(coef, min_size=n, max_size=n), st.lists(finite, min_size=n, max_size=n),
+        st.lists(st.integers(0, 1), min_size=n, max_size=n))))
+    def check(case):
+        c, x, f = (np.array([v], dtype=t) for v, t in zip(case, (np.float64, np.float64, np.uint32)))
+        out, ok = T.fixed_dot(c, x, f)
+        ex = exact_sum(c[0], x[0], f[0])
+        if ok[0]:
+            check_bound(c, x, f, out, ok)
+        else:
+            assert abs(ex) < Fraction(2) ** -820 or abs(ex) > Fraction(2) ** 1020, (case, float(ex))
+
+    check()
+
+
 @pytest.mark.gpu
 def test_device_build_equals_host_build():
     rng = np.random.default_rng(2026)
