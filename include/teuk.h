@@ -14,7 +14,11 @@
  *   - The point particle is a narrow Gaussian ("Mathematical Advances",
  *     item 1) moving on a circular equatorial orbit; the waveform is Phi
  *     sampled at an extraction radius.
- * Units: black-hole mass M = 1.  All arithmetic is IEEE FP64.
+ * Units: black-hole mass M = 1.  Fields and coefficients are IEEE FP64.  By
+ * default the Pi-row sums of each update are formed from exact integer
+ * products in 64-bit fixed point and rounded once to FP64, which is at least
+ * as accurate as the same sums in FP64 arithmetic (TEUK_OPT_FIXED_POINT,
+ * teuk_fixed_dot); everything else is FP64 arithmetic.
  *
  * Grid: r*_i = rstar_min + i h, h = (rstar_max - rstar_min)/(nr - 1),
  * i = 0..nr-1; theta_j = (j + 1/2) pi / nth, j = 0..nth-1 (the poles are not
