@@ -98,9 +98,10 @@ def test_parity_ragged_and_tiny(teuk, nr, nth):
 
 
 def test_parity_wide_theta_kernel_limits(teuk):
-    # nth = 256 is the widest fused block, 512 the widest split tile; wider
-    # rows run the two-kernel variant.
-    for nth, kern in [(256, 0), (257, 2), (512, 2), (513, 1), (1030, 1)]:
+    # nth = 256 is the widest fused block, 512 the widest split row; wider
+    # rows run the two-kernel variant.  304 (the paper's theta resolution)
+    # and 448 are cut into 64-column tiles, 304 with a ragged last tile.
+    for nth, kern in [(256, 0), (257, 2), (304, 2), (448, 2), (512, 2), (513, 1), (1030, 1)]:
         out = run_pair(teuk, 40, nth, -10.0, 30.0, 0.9, -2, 2, 6, source=dict(r0=5.0, sigma=1.0), kernel=kern,
                        seed=1)
         assert_parity(out)
