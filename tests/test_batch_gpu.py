@@ -199,3 +199,52 @@ def test_batch_mixes_fixed_point_and_fp64_jobs(teuk, mode):
         for x, y in zip(collect(g, j), ref):
             np.testing.assert_array_equal(x, y)
     B.close()
+
+
+@pytest.mark.parametrize("mode", ["auto", 0])
+def test_mode_batch_at_full_size_equals_individual_runs(teuk, mode):
+    """The batched-modes workload at its own sizes: a = 0.7, r0 = 8, m = 1..8
+    on 4096 x {32, 32, 64, 64, 128, 128, 256, 256}, r* in [-100, 600], with
+    the source and waveform extraction, in the benchmark's launch
+    configuration (autotuned) and in one persistent launch per step.  Uneven
+    step counts (640 .. 1200) must give each job the same bits as stepping
+    its handle alone; the single-job path is held to the oracle by the
+    parity tests."""
+    w = inputs.MODE_BATCH
+    rmin, rmax = w["rstar_min"], w["rstar_max"]
+    jobs = []
+    for q, (m, nth) in enumerate(w["modes"]):
+        jobs.append(dict(m=m, nth=nth, steps=640 + 80 * q))
+
+    def make_job(q, j):
+        dt = O.stable_dt(w["nr"], j["nth"], rmin, rmax, w["a"], w["s"], j["m"])
+        g = teuk.Solver(w["nr"], j["nth"], rmin, rmax, dt, w["a"], w["s"], j["m"])
+        g.set_initial(*inputs.random_fields(w["nr"], j["nth"], seed=100 + q))
+        g.set_source(r0=w["r0"], sigma=w["sigma"])
+        g.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"], capacity=j["steps"] // 10 + 2)
+        return g
+
+    alone = []
+    for q, j in enumerate(jobs):
+        g = make_job(q, j)
+        g.step(j["steps"])
+        alone.append(list(g.state()) + [g.extract()[1]])
+        g.close()
+    B = teuk.Batch()
+    solvers = [make_job(q, j) for q, j in enumerate(jobs)]
+    for g, j in zip(solvers, jobs):
+        B.add(g, j["steps"])
+    if mode == "auto":
+        B.autotune()
+    else:
+        B.set_option(teuk.TEUK_OPT_BATCH_MODE, mode)
+    while B.step(10 ** 6):
+        pass
+    B.sync()
+    for q, (g, j) in enumerate(zip(solvers, jobs)):
+        assert g.step_count == j["steps"]
+        for x, y in zip(list(g.state()) + [g.extract()[1]], alone[q]):
+            np.testing.assert_array_equal(x, y)
+    B.close()
+    for g in solvers:
+        g.close()
