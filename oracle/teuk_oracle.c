@@ -44,6 +44,14 @@
  *     Gershgorin bound of the discrete angular-plus-potential operator.
  *   - time-symmetric initial data: Pi_i = b_i (Phi_{i+1} - Phi_{i-1}) / (2h).
  *
+ * Parity unpinned: the amplitude and phase of the waveform relative to a
+ * physical h_22.  The paper does not give the true source T or its
+ * normalisation, so the Gaussian's strength A is a reading.  It is pinned
+ * only through its discrete normalisation, linearity and the forced
+ * frequency m Omega.  Everything else above is pinned by the tests against
+ * Eq. (1), exact amplification factors, convergence and published
+ * quasinormal frequencies.
+ *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no FMA contraction,
  * so every product is rounded on its own).  Arrays of complex numbers are
  * interleaved (re, im) doubles, row-major [i][j] with theta (j) fastest.
