@@ -1,0 +1,81 @@
+"""Host logic of bench.py that the measurement depends on, without a GPU:
+the clock record's throttle detection, the source hash that keeps the DRAM
+traffic figure tied to the kernels it was captured for, the HBM peak lookup,
+and the algorithmic flop counts behind the roofline."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+class _Proc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _summary_of(tmp_path, lines):
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(lines) + "\n")
+    c = bench.ClockSampler(0)
+    c.proc, c.path = _Proc(), str(path)
+    return c.summary()
+
+
+def test_clock_summary_median_max_and_reasons(tmp_path):
+    ok = "0, {sm}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {cap}"
+    lines = [ok.format(sm=sm, cap="Not Active") for sm in (2070, 2055, 1995)]
+    lines.append(ok.format(sm=1980, cap="Active"))
+    lines.append("garbage line")
+    s = _summary_of(tmp_path, lines)
+    assert s["sm_mhz"] == pytest.approx((2055 + 1995) / 2) and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+
+
+def test_clock_summary_reports_thermal_and_hw_slowdown(tmp_path):
+    line = "0, 1500, 2070, 1300.0, 0x48, Active, Not Active, Active, Not Active"
+    s = _summary_of(tmp_path, [line, line])
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_samples_is_none(tmp_path):
+    assert _summary_of(tmp_path, ["not, a, number"]) is None
+
+
+def test_traffic_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("// a kernel\n__global__ void f(int *x) { x[0] = 1; } /* done */\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES", ["k.cu"])
+    h0 = bench.sources_sha256()
+    src.write_text("// the same kernel, reworded comment\n__global__ void f(int *x)\n{ x[0] = 1; }\n")
+    assert bench.sources_sha256() == h0
+    src.write_text("__global__ void f(int *x) { x[0] = 2; }\n")
+    assert bench.sources_sha256() != h0
+
+
+def test_hbm_peak_from_measured_file_or_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_hbm_gbs()[0] == 6800.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6783.1}))
+    v, src = bench.measured_hbm_gbs()
+    assert v == 6783.1 and "MEASURED_PEAKS" in src
+
+
+def test_flop_and_instruction_counts_are_consistent():
+    # 100 algorithmic flops per update, split 48 / 52 between the kernels.
+    # With every Pi-row product an FP64 FMA an update takes 56 FP64
+    # instructions: the 20 that stay on the FP64 pipe plus one per
+    # fixed-point product, less the corrector's two unit-coefficient terms
+    # (Pi itself, real and imaginary part), which an FMA chain takes as its
+    # starting value
+    assert bench.FLOPS_PREDICTOR_POINT + bench.FLOPS_CORRECTOR_POINT == bench.FLOPS_PER_UPDATE == 100
+    assert bench.BYTES_PER_UPDATE_ALG == 64
+    assert bench.FP64_INSTR_PER_UPDATE + bench.FIXED_POINT_PRODUCTS_PER_UPDATE - 2 == 56
