@@ -339,6 +339,25 @@ def test_orbit_frequency():
     assert O.orbit_omega(1e6, 0.9, True) * 1e9 == pytest.approx(1.0, rel=1e-8)
 
 
+@pytest.mark.parametrize("a", [-0.9, 0.0, 0.3, 0.9])
+def test_orbit_frequency_from_circular_geodesics(a):
+    """Independent of the orbit formula: on a circular equatorial geodesic
+    of the Kerr metric (Boyer-Lindquist, theta = pi/2, M = 1) the angular
+    velocity solves d_r g_tt + 2 Omega d_r g_tphi + Omega^2 d_r g_phiphi = 0.
+    The metric is written out below and differentiated numerically; the
+    larger root is the orbit the oracle calls prograde, the smaller the
+    retrograde one."""
+    def g(r):
+        return (-(1.0 - 2.0 / r), -2.0 * a / r, r * r + a * a + 2.0 * a * a / r)
+    for r0 in [6.0, 10.0, 37.5]:
+        e = 1e-4 * r0
+        (tt_p, tp_p, pp_p), (tt_m, tp_m, pp_m) = g(r0 + e), g(r0 - e)
+        d_tt, d_tp, d_pp = (tt_p - tt_m) / (2 * e), (tp_p - tp_m) / (2 * e), (pp_p - pp_m) / (2 * e)
+        lo, hi = sorted(np.roots([d_pp, 2.0 * d_tp, d_tt]).real)
+        assert O.orbit_omega(r0, a, True) == pytest.approx(hi, rel=1e-7)
+        assert O.orbit_omega(r0, a, False) == pytest.approx(lo, rel=1e-7)
+
+
 def test_source_normalisation_and_support():
     nr, nth = 401, 64
     S = O.Solver(nr, nth, -50.0, 150.0, 0.01, 0.9, -2, 2)
@@ -355,24 +374,27 @@ def test_source_normalisation_and_support():
     assert np.count_nonzero(G) < 0.05 * G.size
 
 
-def test_forced_steady_state_frequency():
+@pytest.mark.parametrize("prograde", [True, False])
+def test_forced_steady_state_frequency(prograde):
     # Once the switch-on transients have left, the field oscillates as
     # e^{-i m Omega t}.  s = 0 settles within ~40M; the outer-boundary
-    # reflection reaches the observer after ~110M.
+    # reflection reaches the observer after ~110M.  A retrograde orbit turns
+    # the pattern the other way (Omega < 0) at a lower rate.
     a, s, m, r0 = 0.5, 0, 2, 6.0
     nr, nth = 481, 16
     rmin, rmax = -40.0, 80.0
     dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
     S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
     S.set_initial(np.zeros((nr, nth), complex))
-    S.set_source(r0=r0, sigma=1.0)
+    S.set_source(r0=r0, sigma=1.0, prograde=prograde)
     every = 20
     S.set_extraction(20.0, every)
     S.step(int(105.0 / dt))
     t, phi = S.samples()
     late = (t > 55.0) & (t < 105.0)
     z = phi[late, nth // 2 - 1]
-    Om = O.orbit_omega(r0, a, True)
+    Om = O.orbit_omega(r0, a, prograde)
+    assert (Om > 0) == prograde
     # the phase advances at -m Omega
     slope = np.polyfit(t[late], np.unwrap(np.angle(z)), 1)[0]
     assert slope == pytest.approx(-m * Om, rel=2e-3)
