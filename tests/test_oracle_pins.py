@@ -469,6 +469,28 @@ def test_kerr_terms_switch_off_continuously():
     assert 1e-12 < rel < 1e-5
 
 
+def test_time_symmetric_initial_data_start_at_rest():
+    """Reading 10: without Pi the initial data are time-symmetric,
+    Pi = b dPhi/dr* (centred difference), so that d_t Phi = Pi - b dPhi/dr*
+    vanishes and one step changes Phi only at second order in dt.  The same
+    Phi with Pi = 0 moves at first order (d_t Phi = -b dPhi/dr*).  A wrong
+    sign or factor in the constructed Pi leaves a first-order change."""
+    nr, nth, rmin, rmax, a, s, m = 801, 16, -50.0, 150.0, 0.5, -2, 2
+    phi0 = inputs.gaussian_pulse(nr, nth, rmin, rmax, s, m, center=30.0, width=5.0)
+    change = {}
+    for dt in (0.08, 0.04, 0.02):
+        for label, pi in (("symmetric", None), ("pi0", np.zeros((nr, nth), complex))):
+            S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+            S.set_initial(phi0, pi)
+            S.step(1)
+            change[label, dt] = abs(S.state()[0] - phi0).max()
+    for dt in (0.08, 0.04):
+        # observed 4.07, 3.97 (second order) against 2.00, 2.00 (first order)
+        assert change["symmetric", dt] / change["symmetric", dt / 2] == pytest.approx(4.0, rel=0.1)
+        assert change["pi0", dt] / change["pi0", dt / 2] == pytest.approx(2.0, rel=0.05)
+    assert change["symmetric", 0.08] < 0.03 * change["pi0", 0.08]
+
+
 def test_radial_boundary_rows_stay_zero():
     nr, nth = 64, 8
     dt = O.stable_dt(nr, nth, -10.0, 20.0, 0.5, 2, 3)
