@@ -491,6 +491,29 @@ def test_time_symmetric_initial_data_start_at_rest():
     assert change["symmetric", 0.08] < 0.03 * change["pi0", 0.08]
 
 
+@pytest.mark.parametrize("rstar_ext", [10.0, 10.0 + 0.49 * 0.25, 10.0 + 0.51 * 0.25, -20.0])
+def test_extraction_samples_nearest_node_after_every_steps(rstar_ext):
+    """Reading 11: a sample is the whole theta row of Phi at the node nearest
+    to r*_ext, taken after each step n with n % every == 0, at t = n dt.
+    Checked against the state read back at those step counts."""
+    nr, nth, rmin, rmax, a, s, m, dt, every = 161, 8, -20.0, 20.0, 0.7, -2, 1, 0.01, 3
+    h = (rmax - rmin) / (nr - 1)                      # 0.25
+    S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    S.set_initial(*inputs.random_fields(nr, nth, seed=5))
+    S.set_extraction(rstar_ext, every)
+    rows, times = [], []
+    i_ext = int(np.argmin(abs(inputs.rstar_grid(nr, rmin, rmax) - rstar_ext)))
+    for n in range(1, 11):
+        S.step(1)
+        if n % every == 0:
+            rows.append(S.state()[0][i_ext].copy())
+            times.append(n * dt)
+    t, phi = S.samples()
+    np.testing.assert_array_equal(t, np.array(times))
+    np.testing.assert_array_equal(phi, np.array(rows))
+    assert round((rstar_ext - rmin) / h) == i_ext
+
+
 def test_radial_boundary_rows_stay_zero():
     nr, nth = 64, 8
     dt = O.stable_dt(nr, nth, -10.0, 20.0, 0.5, 2, 3)
