@@ -59,8 +59,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
 # sources whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(predictor=125.88e6 + 15.75e6, corrector=151.02e6 + 16.90e6,
-                   sources_sha256="cb5dd95f5fd19ae1d5aad44543ea33534bd362b750601cb39d3e6d2c6fe7d893")
+NCU_TRAFFIC = dict(predictor=125.87e6 + 15.97e6, corrector=151.01e6 + 16.74e6,
+                   sources_sha256="0e90dd64ec9b435947cc1f85a10f9ace89c5a6ef1d14570db7fd9f8c82fe9dee")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits

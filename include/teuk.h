@@ -194,10 +194,13 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  * s = m = 0: 6 and 7 instead of 9 and 10 products per Pi row); 0 keeps the
  * complex planes.  Both give the same numbers. */
 #define TEUK_OPT_REAL_PATH 4
-/* TEUK_OPT_SPLIT_ROWS: r* rows per CTA tile of the split kernels, 1..512 /
- * (tile width); a tile is up to 128 theta columns (rows wider than 128 are
- * cut into equal tiles, a multiple of 32 wide), one thread per point.  0
- * (default) picks 128 / tile width, at least 1. */
+/* TEUK_OPT_SPLIT_ROWS: r* rows per CTA tile of the split kernels; a tile is
+ * up to 128 theta columns (a multiple of 32; wider rows are cut into tiles,
+ * the last one ragged), one thread per point.  1..128 / (tile width) with
+ * the fixed-point Pi rows (their kernels launch at most 128 threads per CTA;
+ * a larger height set earlier for FP64 is reduced to that), 1..512 / (tile
+ * width) with FP64 Pi rows.  0 (default) picks 128 / tile width (256 / tile
+ * width for FP64), at least 1. */
 #define TEUK_OPT_SPLIT_ROWS 5
 /* TEUK_OPT_BATCH_MODE (batches only): 1 (default) advances every job with its
  * own kernels on its own stream (graph replay per chunk), the jobs running

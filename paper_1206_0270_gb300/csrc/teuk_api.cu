@@ -594,8 +594,9 @@ extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
         h->chunk = (int)value;
         return TEUK_OK;
     case TEUK_OPT_SPLIT_ROWS:
-        if (value < 0 || value * split_tile_width(h->nth) > kTileMaxThreads)
-            return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_option: split rows must be 0 or 1..512 / (split tile width)");
+        if (value < 0 || value * split_tile_width(h->nth) > (h->sp.fixed_point ? kFxTileThreads : kTileMaxThreads))
+            return fail(h, TEUK_ERR_BAD_ARG,
+                        "teuk_set_option: split rows must be 0 or 1..(128 fixed point, 512 FP64) / (split tile width)");
         CU(cudaStreamSynchronize(h->stream));
         destroy_graphs(h);
         h->split_rows = (int)value;

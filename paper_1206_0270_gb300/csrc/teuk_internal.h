@@ -44,6 +44,8 @@ namespace teuk {
 // loads), so their launch bounds admit 512 and 256 threads per CTA.  One
 // thread covers one theta point of a tile row.
 constexpr int kTileMaxThreads = 512;  // split and batch tiles: nth <= 512
+constexpr int kFxTileThreads = 128;   // fixed-point split kernels: threads per CTA at most
+constexpr int kFxTileMinBlocks = 5;   // ... and CTAs kept resident per SM (96 registers)
 constexpr int kFusedMaxNth = 256;     // fused kernel: nth <= 256
 
 // Predictor planes: rows hp = 0 .. nr-2 (mid-point r*_{hp+1/2}), nth values each.

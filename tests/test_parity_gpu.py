@@ -227,12 +227,19 @@ def test_tuning_options_agree_bitwise(teuk):
     dt = O.stable_dt(nr, nth, -20.0, 40.0, 0.9, -2, 2)
     u = inputs.random_fields(nr, nth, seed=13)
     ref = None
-    for pdl, chunk, rows in [(1, 64, 0), (0, 64, 0), (1, 2, 0), (1, 128, 0), (0, 6, 0), (1, 64, 1), (1, 6, 3),
-                             (0, 64, 8)]:
+    # (fixed point, ...): fixed-point tiles hold at most 128 threads (2 rows of
+    # 64 here); a height set under FP64 and kept when switching back to fixed
+    # point (the last case, 8 x 64) is reduced at launch
+    for fx, pdl, chunk, rows in [(1, 1, 64, 0), (1, 0, 64, 0), (1, 1, 2, 0), (1, 1, 128, 0), (1, 0, 6, 0),
+                                 (1, 1, 64, 1), (1, 1, 6, 2), ("fp64 rows 8, then fixed point", 0, 64, 8)]:
         g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
         g.set_option(teuk.TEUK_OPT_PDL, pdl)
         g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, chunk)
+        if fx != 1:
+            g.set_option(teuk.TEUK_OPT_FIXED_POINT, 0)
         g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, rows)
+        if fx != 1:
+            g.set_option(teuk.TEUK_OPT_FIXED_POINT, 1)
         g.set_initial(*u)
         g.set_source(**SRC)
         g.set_extraction(10.0, 3, capacity=200)
@@ -249,6 +256,10 @@ def test_tuning_options_agree_bitwise(teuk):
     g = teuk.Solver(nr, nth, -20.0, 40.0, dt, 0.9, -2, 2)
     with pytest.raises(teuk.TeukError):
         g.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, 3)
+    with pytest.raises(teuk.TeukError):
+        g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, 3)    # 3 x 64 threads > 128 (fixed point)
+    g.set_option(teuk.TEUK_OPT_FIXED_POINT, 0)
+    g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, 8)        # 8 x 64 = 512: allowed for FP64
     with pytest.raises(teuk.TeukError):
         g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, 9)    # 9 x 64 threads > 512
     with pytest.raises(teuk.TeukError):
