@@ -56,7 +56,9 @@ def lib():
             L.oracle_angular_op.argtypes = [C.c_int, C.c_int, dp, dp]
             L.oracle_lw_step_generic.restype = None
             L.oracle_lw_step_generic.argtypes = ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]
-                                                 + [dp] * 13 + [C.c_double] * 4 + [dp] * 4)
+                                                 + [dp] * 13 + [C.c_double] * 5 + [dp] * 4)
+            L.oracle_set_dissipation.restype = C.c_int
+            L.oracle_set_dissipation.argtypes = [vp, C.c_double]
             L.oracle_create.restype = vp
             L.oracle_create.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_double, C.c_int, C.c_int]
@@ -138,8 +140,9 @@ def stable_dt(nr, nth, rstar_min, rstar_max, a, s, m, c_r=0.5, c_theta=0.1) -> f
 
 def lw_step_generic(Phi, Pi, *, h, dt, parity, b_node, b_mid, d_node, d_mid, ct_node, ct_mid,
                     W_node, W_mid, kap_node, kap_mid, cot, G_node=None, G_mid=None,
-                    phase_n=0j, phase_half=0j):
-    """One Lax-Wendroff step with caller-supplied coefficient fields."""
+                    phase_n=0j, phase_half=0j, eps=0.0):
+    """One Lax-Wendroff step with caller-supplied coefficient fields and
+    Kreiss-Oliger strength eps."""
     nr, nth = Phi.shape
     f = lambda x, dt_=np.float64: np.ascontiguousarray(x, dtype=dt_)
     c = lambda x: f(x, np.complex128).view(np.float64)
@@ -153,7 +156,7 @@ def lw_step_generic(Phi, Pi, *, h, dt, parity, b_node, b_mid, d_node, d_mid, ct_
     Gm = None if G_mid is None else f(G_mid)
     lib().oracle_lw_step_generic(nr, nth, int(parity), float(h), float(dt), *[_p(a) for a in args],
                                  _p(Gn), _p(Gm), phase_n.real, phase_n.imag, phase_half.real,
-                                 phase_half.imag, _p(Phi.view(np.float64)), _p(Pi.view(np.float64)),
+                                 phase_half.imag, float(eps), _p(Phi.view(np.float64)), _p(Pi.view(np.float64)),
                                  _p(Po.view(np.float64)), _p(Qo.view(np.float64)))
     return Po, Qo
 
@@ -194,6 +197,10 @@ class Solver:
                                      1 if prograde else 0)
         if rc:
             raise ValueError("oracle_set_source: bad argument")
+
+    def set_dissipation(self, eps):
+        if lib().oracle_set_dissipation(self._h, float(eps)):
+            raise ValueError("oracle_set_dissipation: eps outside [0, 2)")
 
     def clear_source(self):
         lib().oracle_clear_source(self._h)

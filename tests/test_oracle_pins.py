@@ -173,7 +173,6 @@ def test_angular_operator_exact_on_quadratics(nth):
 def _angular_part(S, r, s, m, nth):
     """kappa L_theta S - W S on the theta grid at radius r (a = 0): the theta
     derivatives of the Pi row of S in Eq. (1), discretised as the oracle does."""
-    from paper_1206_0270_gb300 import richardson  # noqa: F401  (host numpy only)
     th = inputs.theta_grid(nth)
     D = r * r - 2.0 * r
     co = [O.coefficients(r, D, t, 0.0, s, m) for t in th]
@@ -196,8 +195,9 @@ def test_spin_weighted_harmonics_are_discrete_eigenfunctions(s, m):
       * the Rayleigh quotients of two l's differ by -kappa [l2(l2+1) - l1(l1+1)]
         (the theta-independent part of W cancels), kappa = Delta / r^4.
     Catches a wrong sign or index in the angular stencil, the cot term, the
-    (m + s cos theta)^2 / sin^2 theta term or the ghost parity."""
-    from paper_1206_0270_gb300.richardson import swsh_theta
+    (m + s cos theta)^2 / sin^2 theta term or the ghost parity.  The
+    harmonics come from the test suite's own Jacobi-polynomial form
+    (qnm_leaver.swsh_basis), not from the package."""
     r = 12.0
     kappa_exact = (r * r - 2.0 * r) / r ** 4
     l1 = max(2, abs(m), abs(s))
@@ -207,8 +207,9 @@ def test_spin_weighted_harmonics_are_discrete_eigenfunctions(s, m):
         th = inputs.theta_grid(nth)
         w = np.sin(th)
         lam = {}
+        Y, ls = Q.swsh_basis(s, m, l2, np.cos(th))
         for l in (l1, l2):
-            S = swsh_theta(s, l, m, th)
+            S = Y[ls.index(l)]
             op, kap = _angular_part(S, r, s, m, nth)
             np.testing.assert_allclose(kap, kappa_exact, rtol=1e-13)
             lam[l] = np.sum(w * S * op) / np.sum(w * S * S)
@@ -273,6 +274,81 @@ def test_lax_wendroff_exact_fourier_amplification(seed):
         np.testing.assert_allclose(Pi[sel, j], expect[1] * ph, rtol=1e-12, atol=1e-12 * abs(expect).max())
     # radial boundary rows are exactly zero
     assert np.all(Phi[0] == 0) and np.all(Phi[-1] == 0) and np.all(Pi[0] == 0) and np.all(Pi[-1] == 0)
+
+
+# ---------------------------------------------------------------------------
+# Angular Kreiss-Oliger dissipation (sixth order): closed-form Fourier symbol
+# ---------------------------------------------------------------------------
+
+def _zero_fields(nr, nth):
+    z = lambda rows: np.zeros((rows, nth))
+    zc = lambda rows: np.zeros((rows, nth), complex)
+    return dict(b_node=z(nr), b_mid=z(nr - 1), d_node=zc(nr), d_mid=zc(nr - 1), ct_node=zc(nr),
+                ct_mid=zc(nr - 1), W_node=zc(nr), W_mid=zc(nr - 1), kap_node=z(nr), kap_mid=z(nr - 1),
+                cot=np.ones(nth))
+
+
+@pytest.mark.parametrize("nth", [2, 3, 5, 16, 61])
+@pytest.mark.parametrize("parity", [1, -1])
+@pytest.mark.parametrize("eps", [0.37, 1.0])
+def test_kreiss_oliger_fourier_symbol(nth, parity, eps):
+    # With every coefficient zero and dt = 0 the step is the dissipation alone:
+    # u -> u - (eps/64) D6 u.  The ghost rule extends a row to a 2 nth-periodic
+    # sequence, even (p = +1) or odd (p = -1) about both poles, on which
+    # cos(k theta) (p = +1) and sin(k theta) (p = -1) are exact eigenvectors of
+    # the seven-point difference, with eigenvalue 64 sin^6(k dtheta / 2) (the
+    # third power of the second difference's -4 sin^2).  Different k in every
+    # row and in Phi and Pi; rows shorter than the stencil reflect twice.
+    rng = np.random.default_rng(nth * 7 + (parity > 0))
+    ks = np.arange(0, nth + 1)
+    nr = len(ks) + 2
+    th = inputs.theta_grid(nth)
+    dth = math.pi / nth
+    shape = np.cos if parity > 0 else np.sin
+    Phi = np.zeros((nr, nth), complex)
+    Pi = np.zeros((nr, nth), complex)
+    ePhi = np.zeros((nr, nth), complex)
+    ePi = np.zeros((nr, nth), complex)
+    for row, k in enumerate(ks, start=1):
+        kq = ks[(row * 3) % len(ks)]
+        for X, E, kk in ((Phi, ePhi, k), (Pi, ePi, kq)):
+            amp = complex(rng.normal(), rng.normal())
+            X[row] = amp * shape(kk * th)
+            E[row] = (1.0 - eps * math.sin(kk * dth / 2) ** 6) * X[row]
+    P, Q = O.lw_step_generic(Phi, Pi, h=0.1, dt=0.0, parity=parity, eps=eps, **_zero_fields(nr, nth))
+    tol = 1e-14 * max(abs(Phi).max(), abs(Pi).max(), 1.0) * 4
+    np.testing.assert_allclose(P[1:-1], ePhi[1:-1], rtol=0, atol=tol)
+    np.testing.assert_allclose(Q[1:-1], ePi[1:-1], rtol=0, atol=tol)
+    assert np.all(P[0] == 0) and np.all(P[-1] == 0) and np.all(Q[0] == 0) and np.all(Q[-1] == 0)
+
+
+def test_kreiss_oliger_adds_to_the_scheme_and_is_linear_in_eps():
+    # The dissipated step equals the bare step minus eps times the pure
+    # dissipation of u^n: the term acts on the old state of the same row, not
+    # on the half step or the new state.
+    nr, nth = 40, 12
+    rmin, rmax, a, s, m = -20.0, 30.0, 0.7, -2, 2
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
+    Phi0, Pi0 = inputs.random_fields(nr, nth, seed=11, smooth=False)
+    Phi0[0] = Phi0[-1] = Pi0[0] = Pi0[-1] = 0
+    out = {}
+    for eps in (0.0, 0.5, 1.0):
+        S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+        S.set_dissipation(eps)
+        S.set_initial(Phi0, Pi0)
+        S.step(1)
+        out[eps] = S.state()
+    D = {}
+    for eps in (0.5, 1.0):
+        D[eps] = O.lw_step_generic(Phi0, Pi0, h=0.1, dt=0.0, parity=1, eps=eps, **_zero_fields(nr, nth))
+    for eps in (0.5, 1.0):
+        for c in (0, 1):
+            X0 = (Phi0, Pi0)[c]
+            expect = out[0.0][c] + (D[eps][c] - X0)
+            expect[0] = expect[-1] = 0
+            np.testing.assert_allclose(out[eps][c], expect, rtol=0, atol=1e-13 * abs(X0).max())
+    with pytest.raises(ValueError):
+        O.Solver(nr, nth, rmin, rmax, dt, a, s, m).set_dissipation(2.0)
 
 
 def test_lax_wendroff_source_enters_pi_row():
@@ -554,6 +630,85 @@ def test_bounded_evolution_with_source():
     assert np.isfinite(p2) and p2 < 1.5 * p1
 
 
+def test_schwarzschild_workload_bounded_over_a_ringdown_length_run():
+    """The Schwarzschild workload's grid (1024 x 64, r* in [-100, 300]) with
+    its time-step rule (c_theta = 0.8) and dissipation (eps = 1), run to
+    t = 450 M: the pulse's outgoing half passes the observer at r* = 100
+    (t ~ 50 M), the half that falls in scatters off the potential and its
+    ringdown passes the observer (t ~ 150 M).
+      * The solution stays bounded by the level its r^-4 infall sets: for
+        s = -2 the ingoing part of Phi = psi / r^3 grows like r^-4 towards
+        the hole (psi ~ r^-1 there against r^3 outgoing), which lifts a pulse
+        of height 1 at r* = 50 to about 3.6e3; no value may exceed 4e3 at any
+        checkpoint, and after the outgoing wave has left through the outer
+        boundary (t = 450 M) the maximum is below 1e3.
+      * The waveform at the observer equals, to the scheme's truncation
+        error, that of the bare scheme (eps = 0) at an eight times smaller
+        step over the first 160 M (relative 2e-3; observed 4e-4): the
+        dissipation changes no physics at the resolved scales."""
+    w = inputs.WORKLOADS["schwarzschild_s-2_m2_1024x64"]
+    nr, nth, rmin, rmax, a, s, m = w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"]
+    phi0 = inputs.gaussian_pulse(nr, nth, rmin, rmax, s, m, w["pulse"]["center"], w["pulse"]["width"], seed=0)
+    ex = w["extraction"]
+
+    def solver(c_theta, eps):
+        dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m, w["c_r"], c_theta)
+        S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+        S.set_dissipation(eps)
+        S.set_initial(phi0)
+        S.set_extraction(ex["rstar"], ex["every"])
+        return S, dt
+    S, dt = solver(w["c_theta"], w["eps"])
+    peaks = []
+    for k in range(9):
+        S.step(int(round(50.0 / dt)))
+        peaks.append(abs(S.state()[0]).max())
+    assert all(np.isfinite(peaks)) and max(peaks) < 4.0e3, peaks
+    assert max(peaks) > 3.0e3, peaks          # the r^-4 infall transient itself
+    assert peaks[-1] < 1.0e3, peaks
+    t, wf = S.samples()
+    B, dtb = solver(0.1, 0.0)
+    B.step(int(round(160.0 / dtb)))
+    tb, wb = B.samples()
+    sel = t <= tb[-1]
+    wb_i = np.array([np.interp(t[sel], tb, wb[:, j].real) + 1j * np.interp(t[sel], tb, wb[:, j].imag)
+                     for j in range(nth)]).T
+    assert abs(wf[sel] - wb_i).max() <= 2e-3 * abs(wb_i).max()
+
+
+def test_kerr_workload_full_length_stays_bounded_and_radiates_at_m_omega():
+    """The Kerr workload in full (8192 x 128, r* in [-100, 1000], 1e5 steps,
+    t = 1170 M) as the oracle ran it (tests/golden/make_kerr_full_fixture.py):
+      * max |Phi| and max |Pi| over the grid every 1000 steps stay below 300
+        (the switch-on burst of the source is the largest feature); at the end,
+        after the burst has left through the outer boundary, max |Phi| < 10;
+      * the observer at r* = 500 M receives the orbit's radiation: once the
+        burst has passed (t > 700 M) the projected waveform turns with
+        exp(-i m Omega t), Omega = 1/(r0^{3/2} + a) (closed form for the
+        circular equatorial orbit), to 1e-4, at an amplitude constant to 3%."""
+    path = os.path.join(GOLDEN, "kerr_a0.9_8192x128_1e5.txt")
+    W, H = [], []
+    for line in open(path):
+        if line.startswith("W "):
+            W.append([float(x) for x in line.split()[1:]])
+        elif line.startswith("H "):
+            H.append([float(x) for x in line.split()[1:]])
+    W, H = np.array(W), np.array(H)
+    assert len(H) == 100 and H[-1, 0] == 100000
+    assert np.all(np.isfinite(H)) and H[:, 1:].max() < 300.0, H[:, 1:].max()
+    assert H[-1, 1] < 10.0
+    t, z = W[:, 0], W[:, 1] + 1j * W[:, 2]
+    late = t > 700.0
+    assert late.sum() > 300
+    phase = np.unwrap(np.angle(z[late]))
+    omega = np.polyfit(t[late], phase, 1)[0]
+    w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
+    m_omega = w["m"] / (w["source"]["r0"] ** 1.5 + w["a"])
+    assert omega == pytest.approx(-m_omega, rel=1e-4)
+    amp = abs(z[late])
+    assert amp.max() <= 1.03 * amp.min() and amp.min() > 0
+
+
 # ---------------------------------------------------------------------------
 # Convergence and physics
 # ---------------------------------------------------------------------------
@@ -619,12 +774,16 @@ def _fit_damped(t, y):
     return best.x[2], best.x[1]
 
 
-def test_schwarzschild_l2_quasinormal_ringdown():
+@pytest.mark.parametrize("rule", [(0.1, 0.0), (0.8, 1.0)])
+def test_schwarzschild_l2_quasinormal_ringdown(rule):
+    # rule = (c_theta, eps): the bare scheme, and the larger step with the
+    # angular dissipation; both must ring down at Leaver's frequency
     re_w, im_w = np.loadtxt(os.path.join(GOLDEN, "qnm_schwarzschild_l2.txt"))
     s, m = -2, 2
     nr, nth, rmin, rmax = 1301, 16, -60.0, 200.0
-    dt = O.stable_dt(nr, nth, rmin, rmax, 0.0, s, m)
+    dt = O.stable_dt(nr, nth, rmin, rmax, 0.0, s, m, 0.5, rule[0])
     S = O.Solver(nr, nth, rmin, rmax, dt, 0.0, s, m)
+    S.set_dissipation(rule[1])
     S.set_initial(inputs.gaussian_pulse(nr, nth, rmin, rmax, s, m, center=10.0, width=2.0))
     S.set_extraction(50.0, max(1, int(round(0.5 / dt))))
     S.step(int(145.0 / dt))
@@ -733,13 +892,15 @@ def test_leaver_reference_against_published_value_and_two_angular_solvers():
     assert abs(Q.kerr_qnm(0.9, -2, 2, 2, 0.5 - 0.08j, "cf") - Q.kerr_qnm(0.9, -2, 2, 2, 0.5 - 0.08j)) < 1e-10
 
 
-@pytest.mark.parametrize("a,s,m,window,next_l", [
-    (0.5, -2, 2, (140.0, 190.0), True),
-    (0.9, -2, 2, (140.0, 190.0), True),
-    (0.7, -2, 1, (140.0, 190.0), True),
-    (0.9, 0, 2, (120.0, 170.0), False),
+@pytest.mark.parametrize("a,s,m,window,next_l,rule", [
+    (0.5, -2, 2, (140.0, 190.0), True, (0.1, 0.0)),
+    (0.9, -2, 2, (140.0, 190.0), True, (0.1, 0.0)),
+    (0.7, -2, 1, (140.0, 190.0), True, (0.1, 0.0)),
+    (0.9, 0, 2, (120.0, 170.0), False, (0.1, 0.0)),
+    (0.9, -2, 2, (140.0, 190.0), True, (0.8, 1.0)),
+    (0.7, -2, 1, (140.0, 190.0), True, (0.8, 1.0)),
 ])
-def test_kerr_quasinormal_spectrum(a, s, m, window, next_l):
+def test_kerr_quasinormal_spectrum(a, s, m, window, next_l, rule):
     """The oracle's Kerr evolution of a pulse rings down in the Kerr
     quasinormal modes.  A damped-exponential fit to all theta rows of the
     extracted waveform late in the ringdown must find, within the scheme's
@@ -756,10 +917,14 @@ def test_kerr_quasinormal_spectrum(a, s, m, window, next_l):
     tolerances (dRe(omega)/da ~ 0.7 at a = 0.9).  The scalar case is fitted
     earlier: its ingoing wave is not suppressed near the horizon as the
     s = -2 field's is (~Delta^2), so the part reflected by the inner boundary
-    row (r* = -60) is strong and reaches the extraction radius at t ~ 170 M."""
+    row (r* = -60) is strong and reaches the extraction radius at t ~ 170 M.
+    rule = (c_theta, eps): the bare scheme at c_theta = 0.1, and the
+    eight-times larger step that the angular dissipation at eps = 1 allows,
+    which must ring down in the same modes."""
     nr, nth, rmin, rmax = 1301, 16, -60.0, 200.0
-    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m, 0.5, rule[0])
     S = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    S.set_dissipation(rule[1])
     S.set_initial(inputs.gaussian_pulse(nr, nth, rmin, rmax, s, m, center=10.0, width=2.0))
     S.set_extraction(50.0, max(1, int(round(0.5 / dt))))
     S.step(int(window[1] / dt))
