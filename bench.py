@@ -1,11 +1,15 @@
 """Benchmark: FP64 grid-point updates/s of the time-domain Teukolsky step on GB300.
 
 Workload: Kerr a = 0.9M, s = -2, m = 2, grid 8192 r* x 128 theta,
-r* in [-100M, 600M], circular equatorial orbit r0 = 10M with a Gaussian source
-of width 0.05M, waveform sampled at r* = 500M every 10 steps, FP64.  One
+r* in [-100M, 1000M], circular equatorial orbit r0 = 10M with a Gaussian source
+of width 0.05M, waveform sampled at r* = 500M every 10 steps, FP64, time step
+c_theta = 0.8 with the angular Kreiss-Oliger dissipation at eps = 1.  One
 benchmark step = `--chunk` time steps of Eqs. (3)-(4) (graph replays of the
-fused kernel), on inputs resident in HBM.  The per-step working set (state
-2 x 33.5 MB + coefficient planes 193 MB) is larger than the 129 MB L2.
+split kernels), on inputs resident in HBM.  The per-step working set (state
+2 x 33.5 MB + coefficient planes 193 MB) is larger than the 129 MB L2.  The
+default run also reports the batched workloads (waveforms/s batched against
+one job at a time) and the serving stream (p50/p99 latency), each on a stated
+fraction of its step counts.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--chunk C] [--impl reference]
 
@@ -39,10 +43,15 @@ UNIT = "grid-pt updates/s"
 # FP64 work of one interior point update in the folded formulation of
 # Eqs. (3)-(4): 8 adds + 4 multiplies + 44 FMAs = 100 flops (algorithmic);
 # per kernel: predictor (one mid-point) 4 adds + 4 multiplies + 20 FMAs = 48 flops,
-# corrector (one node) 4 adds + 24 FMAs = 52 flops.
+# corrector (one node) 4 adds + 24 FMAs = 52 flops.  The angular dissipation
+# adds to the corrector, per real component of Phi and Pi, 3 pair sums and the
+# weighted sum k1 s1 + k2 s2 + k3 s3 (1 multiply + 2 FMAs), and applies it with
+# the central weight (1 FMA for Phi, 1 multiply for Pi): 10 + 9 flops per
+# complex component pair, 38 per node.
 FLOPS_PER_UPDATE = 100
 FLOPS_PREDICTOR_POINT = 48
 FLOPS_CORRECTOR_POINT = 52
+FLOPS_DISSIPATION_POINT = 38
 # Algorithmic HBM bytes of one point update: read u^n, write u^{n+1} (4 doubles each).
 BYTES_PER_UPDATE_ALG = 64
 # Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
@@ -50,15 +59,18 @@ FP64_PEAK_FLOPS = 1.25e12
 # How the kernels execute that work: the Phi rows and the sums tau, sigma on
 # the FP64 pipe (20 instructions per update, adds and multiplies issued as
 # FMAs), the Pi rows as fixed-point sums of 38 exact integer products per
-# update on the integer pipes.  Measured FP64 issue rate on GB300
-# (FMA-chain probe): 1.906 per clock per SM.
+# update on the integer pipes; the dissipation adds 26 FP64 instructions and
+# 2 products.  Measured FP64 issue rate on GB300 (FMA-chain probe): 1.906 per
+# clock per SM.
 FP64_INSTR_PER_UPDATE = 20
 FIXED_POINT_PRODUCTS_PER_UPDATE = 38
+FP64_INSTR_DISSIPATION = 26
+FIXED_POINT_PRODUCTS_DISSIPATION = 2
 FP64_FMA_PER_CLK_SM = 1.906
 NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
-# (profiles/lw_split_kerr_a0.9_8192x128_ncu.md), valid for the kernel and launch
-# sources whose SHA-256 is recorded here; reported as null otherwise.
+# of the split kernels on 8192 x 128, valid for the kernel and launch sources
+# whose SHA-256 is recorded here; reported as null otherwise.
 NCU_TRAFFIC = dict(predictor=125.87e6 + 15.97e6, corrector=151.01e6 + 16.74e6,
                    sources_sha256="0e90dd64ec9b435947cc1f85a10f9ace89c5a6ef1d14570db7fd9f8c82fe9dee")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
@@ -133,6 +145,7 @@ def oracle_rate(steps_per_sample: int, samples: int, warmup: int = 0):
     dt = O.stable_dt(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"],
                      w["c_r"], w["c_theta"])
     S = O.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+    S.set_dissipation(w["eps"])
     S.set_initial(np.zeros((w["nr"], w["nth"]), complex))
     S.set_source(**w["source"])
     S.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"])
@@ -253,6 +266,7 @@ def run_gpu(args):
     dt = T.stable_dt(nr, nth, w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], w["c_r"], w["c_theta"])
     stream = torch.cuda.Stream()
     S = T.Solver(nr, nth, w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"], stream=stream)
+    S.set_dissipation(w["eps"])
     S.set_initial(np.zeros((nr, nth), complex), np.zeros((nr, nth), complex))
     S.set_source(**w["source"])
     ex = w["extraction"]
@@ -264,6 +278,12 @@ def run_gpu(args):
     for _ in range(args.warmup):
         S.step(args.chunk)
     torch.cuda.synchronize()
+    # the state where the timed region starts: the end-to-end leg below times
+    # the same time steps, resumed from it through the C ABI
+    pin = lambda: torch.zeros((nr, nth), dtype=torch.complex128, pin_memory=True).numpy()
+    phi_h, pi_h = pin(), pin()
+    T._check(T.teuk_get_state(S.h, phi_h.ctypes.data_as(T._dp), pi_h.ctypes.data_as(T._dp)), S.h, "teuk_get_state")
+    n_start = S.step_count
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     if ws > 1:
         torch.distributed.barrier()
@@ -280,6 +300,7 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.barrier()
     assert S.check_finite(), "state became non-finite"
+    S.state_at_end = S.state()
     launches = args.steps * S.launches_for(args.chunk)
     value = whole_job_rate(ws, upd_per_step * args.steps, total_ms / 1e3)
 
@@ -290,20 +311,27 @@ def run_gpu(args):
     per_launch_s = (total_ms / 1e3) / (args.steps * args.chunk)     # one step, inside the graph replay
     upd_per_launch = (nr - 2) * nth
     ms_pred, ms_corr = S.time_kernels(args.kernel_timing_steps)
+    ko = w["eps"] > 0
+    flops_corr = FLOPS_CORRECTOR_POINT + (FLOPS_DISSIPATION_POINT if ko else 0)
+    flops_update = FLOPS_PER_UPDATE + (FLOPS_DISSIPATION_POINT if ko else 0)
     kern = dict(lw_predict_split=(FLOPS_PREDICTOR_POINT * (nr - 1) * nth, ms_pred, "predictor"),
-                lw_correct_split=(FLOPS_CORRECTOR_POINT * (nr - 2) * nth, ms_corr, "corrector"))
+                lw_correct_split=(flops_corr * (nr - 2) * nth, ms_corr, "corrector"))
     dom = max(kern, key=lambda k: kern[k][1])
     flops, ms, key = kern[dom]
     achieved = flops / (ms / 1e3)
     same_src = NCU_TRAFFIC["sources_sha256"] == sources_sha256()
+    measured_fp64 = NUM_SMS * FP64_FMA_PER_CLK_SM * 2 * 2.07e9     # the DFMA probe's rate at 2070 MHz
     roofline = dict(bound="alu", achieved=achieved / 1e12, peak=FP64_PEAK_FLOPS / 1e12, unit="TFLOP/s",
                     frac=achieved / FP64_PEAK_FLOPS, traffic=NCU_TRAFFIC[key] if same_src else None,
                     kernel=dom, launch_ms=ms,
                     peak_source="nominal FP64 (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz); achieved counts the "
                                 "algorithmic FP64 flops, of which the Pi-row products run on the integer pipes",
+                    frac_of_measured_dfma=achieved / measured_fp64,
+                    measured_dfma_tflops=measured_fp64 / 1e12,
+                    flops_per_launch=flops, flops_per_node=flops_corr if key == "corrector" else FLOPS_PREDICTOR_POINT,
                     kernels={k: dict(ms=v[1], tflops=v[0] / (v[1] / 1e3) / 1e12) for k, v in kern.items()},
                     step_in_graph=dict(ms=per_launch_s * 1e3,
-                                       tflops=FLOPS_PER_UPDATE * upd_per_launch / per_launch_s / 1e12),
+                                       tflops=flops_update * upd_per_launch / per_launch_s / 1e12),
                     hbm_alg_gbs=BYTES_PER_UPDATE_ALG * upd_per_launch / per_launch_s / 1e9)
     # secondary roof: HBM (not binding here), against the measured copy bandwidth
     hbm_peak, hbm_src = measured_hbm_gbs()
@@ -315,25 +343,37 @@ def run_gpu(args):
         frac_dram=None if dram_step is None else dram_step / per_launch_s / 1e9 / hbm_peak)
 
     # ---- end to end through the C ABI with host buffers ------------------------------
-    pin = lambda: torch.zeros((nr, nth), dtype=torch.complex128, pin_memory=True).numpy()
-    phi_h, pi_h = pin(), pin()
+    # Every step uploads the state from pinned host memory (teuk_set_state at
+    # the current step count, so the evolution resumes where it stood), runs
+    # the chunk, reads the waveform samples back and downloads the new state:
+    # the same time steps as the device-resident region, plus the copies.
     t_buf = np.zeros(samples_per_step + 1)
     w_buf = torch.zeros((samples_per_step + 1, nth), dtype=torch.complex128, pin_memory=True).numpy()
     E = T.Solver(nr, nth, w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"], stream=stream)
+    E.set_dissipation(w["eps"])
     E.set_source(**w["source"])
     E.set_extraction(ex["rstar"], ex["every"], capacity=samples_per_step + 1)
     import ctypes as C
+    dp = lambda a: a.ctypes.data_as(T._dp)
+    e2e_at = [n_start]
 
     def e2e_step():
-        E.set_initial(phi_h, pi_h)           # H2D of the step's input state (pinned)
+        T._check(T.teuk_set_state(E.h, dp(phi_h), dp(pi_h), e2e_at[0]), E.h, "teuk_set_state")   # H2D
         E.step(args.chunk)
         n = C.c_long()
-        rc = T.teuk_extract(E.h, t_buf.ctypes.data_as(T._dp), w_buf.ctypes.data_as(T._dp), len(t_buf),
-                            C.byref(n))      # D2H of the step's waveform samples (synchronises)
+        rc = T.teuk_extract(E.h, dp(t_buf), dp(w_buf), len(t_buf), C.byref(n))    # D2H waveform (synchronises)
         T._check(rc, E.h, "teuk_extract")
+        T._check(T.teuk_get_state(E.h, dp(phi_h), dp(pi_h)), E.h, "teuk_get_state")  # D2H state
+        e2e_at[0] += args.chunk
         return n.value
+    # one untimed step (graph capture, first-touch of the pinned buffers), then
+    # back to the snapshot where the device-resident timed region started
+    snap = (phi_h.copy(), pi_h.copy())
     for _ in range(max(1, args.warmup)):
         e2e_step()
+    np.copyto(phi_h, snap[0])
+    np.copyto(pi_h, snap[1])
+    e2e_at[0] = n_start
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -342,12 +382,17 @@ def run_gpu(args):
     for _ in range(args.steps):
         nsamp = e2e_step()
     e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
+    # the resumed run reproduces the device-resident one: same steps, same bits
+    e2e_same = bool(np.array_equal(phi_h, S.state_at_end[0])) if hasattr(S, "state_at_end") else None
     e2e = dict(value=whole_job_rate(ws, upd_per_step * args.steps, e2e_s), unit=UNIT,
-               h2d_bytes_per_step=2 * nr * nth * 16, d2h_bytes_per_step=nsamp * (nth * 16 + 8))
+               h2d_bytes_per_step=2 * nr * nth * 16,
+               d2h_bytes_per_step=2 * nr * nth * 16 + nsamp * (nth * 16 + 8),
+               time_steps=[n_start, e2e_at[0]], same_steps_as_value=True, bitwise_equal_to_value=e2e_same)
     E.close()
 
     # ---- the same workload with every Pi-row product as an FP64 FMA ------------------
     F = T.Solver(nr, nth, w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"], stream=stream)
+    F.set_dissipation(w["eps"])
     F.set_option(T.TEUK_OPT_FIXED_POINT, 0)
     F.set_initial(np.zeros((nr, nth), complex), np.zeros((nr, nth), complex))
     F.set_source(**w["source"])
@@ -375,8 +420,11 @@ def run_gpu(args):
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
                 ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic",
+                evolved_M_per_s=value / ((nr - 2) * nth) * dt,
                 config=dict(workload=WORKLOAD, nr=nr, nth=nth, a=w["a"], s=w["s"], m=w["m"],
-                            rstar=[w["rstar_min"], w["rstar_max"]], dt=dt, time_steps_per_step=args.chunk,
+                            rstar=[w["rstar_min"], w["rstar_max"]], dt=dt, c_r=w["c_r"], c_theta=w["c_theta"],
+                            eps=w["eps"], time_steps_per_step=args.chunk,
+                            evolved_M_per_step=args.chunk * dt,
                             kernel="split predictor/corrector tiles, CUDA-graph replay",
                             arithmetic="FP64; Pi-row sums as exact integer products in 64-bit fixed point, "
                                        "rounded once to FP64 (error <= n 2^-57 max|c x| + 2^-53 |sum|)",
@@ -389,9 +437,21 @@ def run_gpu(args):
         line["clocks"] = clocks
         # FP64 pipe occupancy at the clock seen during the timed region
         pipe = NUM_SMS * FP64_FMA_PER_CLK_SM * clocks["sm_mhz"] * 1e6
-        roofline["fp64_instr_per_update"] = FP64_INSTR_PER_UPDATE
-        roofline["fixed_point_products_per_update"] = FIXED_POINT_PRODUCTS_PER_UPDATE
-        roofline["fp64_pipe_frac"] = FP64_INSTR_PER_UPDATE * upd_per_launch / per_launch_s / pipe
+        fp64_instr = FP64_INSTR_PER_UPDATE + (FP64_INSTR_DISSIPATION if ko else 0)
+        roofline["fp64_instr_per_update"] = fp64_instr
+        roofline["fixed_point_products_per_update"] = (FIXED_POINT_PRODUCTS_PER_UPDATE +
+                                                       (FIXED_POINT_PRODUCTS_DISSIPATION if ko else 0))
+        roofline["fp64_pipe_frac"] = fp64_instr * upd_per_launch / per_launch_s / pipe
+    if ws == 1 and args.batched:
+        # the other parts of the workload metric, on stated fractions of their
+        # step counts: batched waveforms/s against one job at a time, and the
+        # serving stream's latency
+        from paper_1206_0270_gb300 import inputs, serve as SV
+        line["batched"] = [batch_result(T, "batch_modes", 0.2), batch_result(T, "template_bank", 0.01),
+                           batch_result(T, "small_bank", 0.2)]
+        line["serving"] = serving_result(T, SV, inputs.serving_requests(64, 4.0), slice_steps=640,
+                                         fill_points=2_000_000, memory_gb=200.0, policies=("async",))
+        line["serving"].update(rate_per_s=4.0, step_fraction=1.0, steps="logU[1e3, 1e4]")
     if ws == 1 and not args.no_cpu_baseline:
         per = args.cpu_sample_steps
         upd, times = oracle_rate(per, 1)
@@ -475,27 +535,29 @@ def batch_jobs(kind, scale):
     return jobs
 
 
-def run_batch_workload(args):
+def batch_result(T, kind, scale, batch_mode="auto"):
+    """Waveforms/s of a batched workload against the same jobs one at a time
+    (each job's own graph-replayed steps, jobs in sequence)."""
     import torch
-    from paper_1206_0270_gb300 import build
-    build.build()
-    from paper_1206_0270_gb300 import teuk as T
+    from paper_1206_0270_gb300 import inputs
+    rule = inputs.STEP_RULE
     rmin, rmax, ext = -100.0, 600.0, dict(rstar=500.0, every=10)
-    jobs = batch_jobs(args.workload, args.steps_scale)
+    jobs = batch_jobs(kind, scale)
     stream = torch.cuda.Stream()
     dts = {}
     for j in jobs:
         key = (j["nr"], j["nth"], j["a"], j["s"], j["m"])
         if key not in dts:
-            dts[key] = T.stable_dt(j["nr"], j["nth"], rmin, rmax, j["a"], j["s"], j["m"])
+            dts[key] = T.stable_dt(j["nr"], j["nth"], rmin, rmax, j["a"], j["s"], j["m"], rule["c_r"],
+                                   rule["c_theta"])
         j["dt"] = dts[key]
 
     def make_all(own_streams=False):
         out = []
         for j in jobs:
-            dt = j["dt"]
-            g = T.Solver(j["nr"], j["nth"], rmin, rmax, dt, j["a"], j["s"], j["m"],
+            g = T.Solver(j["nr"], j["nth"], rmin, rmax, j["dt"], j["a"], j["s"], j["m"],
                          stream=None if own_streams else stream)
+            g.set_dissipation(rule["eps"])
             g.set_source(r0=j["r0"], sigma=j["sigma"])
             g.set_extraction(ext["rstar"], ext["every"], capacity=j["steps"] // ext["every"] + 1)
             out.append(g)
@@ -503,7 +565,6 @@ def run_batch_workload(args):
         return out
 
     upd = sum((j["nr"] - 2) * j["nth"] * j["steps"] for j in jobs)
-    # one at a time: each job's own graph-replayed steps, jobs in sequence
     solvers = make_all()
     t0 = time.perf_counter()
     for g, j in zip(solvers, jobs):
@@ -512,6 +573,7 @@ def run_batch_workload(args):
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
     launches_single = sum(g.launches_for(j["steps"]) for g, j in zip(solvers, jobs))
+    finite = all(g.check_finite() for g in solvers)
     for g in solvers:
         g.close()
     # batched: every job in one batch (each job on its own stream, so that
@@ -522,67 +584,77 @@ def run_batch_workload(args):
     for g, j in zip(solvers, jobs):
         B.add(g, j["steps"])
     t0 = time.perf_counter()
-    if args.batch_mode == "auto":
+    if batch_mode == "auto":
         best = B.autotune()
     else:
-        B.set_option(T.TEUK_OPT_BATCH_MODE, int(args.batch_mode))
-        best = 0 if args.batch_mode == "1" else 128
+        B.set_option(T.TEUK_OPT_BATCH_MODE, int(batch_mode))
+        best = 0 if batch_mode == "1" else 128
     B.step(10 ** 9)
     B.sync()
     for g in solvers:
         g.extract()
     t_batch = time.perf_counter() - t0
     B.close()
+    finite = finite and all(g.check_finite() for g in solvers)
     for g in solvers:
         g.close()
     n = len(jobs)
-    line = dict(metric="batched waveforms/s", value=n / t_batch, unit="waveforms/s", n_gpus=1,
-                steps=1, warmup=0, ms_per_step=1e3 * t_batch, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=args.workload, jobs=n, steps_scale=args.steps_scale,
-                            point_updates=upd, block_threads=best,
-                            batch_mode="per-job launches" if best == 0 else "one persistent launch per step"),
+    return dict(workload=kind, jobs=n, step_fraction=scale, point_updates=upd,
+                value=n / t_batch, unit="waveforms/s", seconds=t_batch, grid_pt_updates_per_s=upd / t_batch,
+                block_threads=best,
+                batch_mode="per-job launches" if best == 0 else "one persistent launch per step",
                 one_by_one=dict(value=n / t_single, unit="waveforms/s", seconds=t_single,
-                                gpu_launches=int(launches_single)),
-                batched=dict(seconds=t_batch, grid_pt_updates_per_s=upd / t_batch),
-                speedup=t_single / t_batch)
+                                gpu_launches=int(launches_single), grid_pt_updates_per_s=upd / t_single),
+                speedup=t_single / t_batch, finite=finite)
+
+
+def run_batch_workload(args):
+    from paper_1206_0270_gb300 import build
+    build.build()
+    from paper_1206_0270_gb300 import teuk as T
+    r = batch_result(T, args.workload, args.steps_scale, args.batch_mode)
+    line = dict(metric="batched waveforms/s", value=r["value"], unit="waveforms/s", n_gpus=1,
+                steps=1, warmup=0, ms_per_step=1e3 * r["seconds"], higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, jobs=r["jobs"], steps_scale=args.steps_scale,
+                            point_updates=r["point_updates"], block_threads=r["block_threads"],
+                            batch_mode=r["batch_mode"]),
+                one_by_one=r["one_by_one"], batched=dict(seconds=r["seconds"],
+                                                         grid_pt_updates_per_s=r["grid_pt_updates_per_s"]),
+                speedup=r["speedup"])
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args):
-    """Poisson stream of requests through the continuous-batching service:
-    p50/p99 latency and waveforms/s, beside the same stream served one job at
-    a time in arrival order."""
+def serving_result(T, S, raw, *, slice_steps, fill_points, memory_gb, policies=("async",), sweep=(), n_requests=None,
+                   rate=None):
+    """A Poisson stream of requests through the continuous-batching service:
+    p50/p99 latency and waveforms/s for each policy, beside the same stream
+    served one job at a time in arrival order (same kernels, no batching)."""
     import torch
-    from paper_1206_0270_gb300 import build
-    build.build()
-    from paper_1206_0270_gb300 import inputs, serve as S
-    from paper_1206_0270_gb300 import teuk as T
-    raw = inputs.serving_requests(args.requests, args.rate)
+    from paper_1206_0270_gb300 import inputs
 
     def request(d):
         sigma = max(0.05, 2.0 * 700.0 / (d["nr"] - 1))
         return S.Request(a=d["a"], s=d["s"], m=d["m"], nr=d["nr"], nth=d["nth"], steps=d["steps"], r0=d["r0"],
-                         sigma=sigma, arrival=d["arrival"])
+                         sigma=sigma, arrival=d["arrival"], **inputs.STEP_RULE)
     reqs = [request(d) for d in raw]
     upd = sum((r.nr - 2) * r.nth * r.steps for r in reqs)
-    budget = int(args.memory_gb * 2 ** 30)
+    budget = int(memory_gb * 2 ** 30)
 
     def served(reqs, policy):
-        svc = S.WaveformService(memory_budget=budget, slice_steps=args.slice, policy=policy,
-                                fill_points=args.fill_points)
+        svc = S.WaveformService(memory_budget=budget, slice_steps=slice_steps, policy=policy,
+                                fill_points=fill_points)
         for r in reqs:
             svc.submit(r)
         torch.cuda.synchronize()
         t0 = svc.now()
         res = svc.run()
-        out = (svc.now() - t0, S.latency_stats(res))
+        out = (svc.now() - t0, S.latency_stats(res), res)
         svc.close()
         return out
 
     def one_at_a_time(reqs):
-        """Same kernels, no batching: each job runs alone, in arrival order."""
         t_start = time.perf_counter()
         lat = []
         for r in reqs:
@@ -591,6 +663,7 @@ def run_serving(args):
                 time.sleep(r.arrival - now)
             dt = T.stable_dt(r.nr, r.nth, r.rstar_min, r.rstar_max, r.a, r.s, r.m, r.c_r, r.c_theta)
             g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, dt, r.a, r.s, r.m)
+            g.set_dissipation(r.eps)
             g.set_source(r0=r.r0, sigma=r.sigma)
             g.set_extraction(r.rstar_ext, r.every, capacity=r.steps // r.every + 1)
             g.step(r.steps)
@@ -599,50 +672,66 @@ def run_serving(args):
             lat.append(time.perf_counter() - t_start - r.arrival)
         return time.perf_counter() - t_start, np.array(lat)
 
-    # continuous batching, the four scheduling policies
-    per_policy = {policy: served(reqs, policy) for policy in ("fill", "share", "priority", "async")}
-    wall, st = per_policy["async"]          # the service's default policy
-    wall1, lat1 = one_at_a_time(reqs)
+    def stats(st):
+        return dict(p50=st["p50"], p99=st["p99"], mean=st["mean"])
+
     n = len(reqs)
-    # arrival-rate sweep in multiples of the one-at-a-time capacity (the same
-    # jobs; only the arrival times scale)
-    sweep = []
-    for mult in [float(x) for x in args.rate_sweep.split(",") if x.strip()]:
-        rate = mult * n / wall1
-        rq = [request(d) for d in inputs.serving_requests(args.requests, rate)]
-        w_f, st_f = served(rq, "fill")
-        w_a, st_a = served(rq, "async")
-        w_1, l_1 = one_at_a_time(rq)
-        sweep.append(dict(rate_per_s=rate, load=mult,
-                          fill=dict(value=n / w_f, p50=st_f["p50"], p99=st_f["p99"], mean=st_f["mean"]),
-                          async_policy=dict(value=n / w_a, p50=st_a["p50"], p99=st_a["p99"], mean=st_a["mean"]),
-                          one_by_one=dict(value=n / w_1, p50=float(np.percentile(l_1, 50)),
-                                          p99=float(np.percentile(l_1, 99)), mean=float(l_1.mean()))))
-    line = dict(metric="served waveforms/s", value=n / wall, unit="waveforms/s", n_gpus=1, steps=1, warmup=0,
-                ms_per_step=1e3 * wall, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                data="synthetic",
-                config=dict(workload="serving", requests=n, rate_per_s=args.rate, slice_steps=args.slice,
-                            fill_points=args.fill_points,
-                            memory_budget_gb=args.memory_gb, point_updates=upd,
-                            grids="2048x64..32768x512", steps="logU[1e3, 1e4]"),
-                policy="async",
-                latency_s=dict(p50=st["p50"], p99=st["p99"], mean=st["mean"]),
-                grid_pt_updates_per_s=upd / wall,
-                share_policy=dict(value=n / per_policy["share"][0], unit="waveforms/s",
-                                  latency_s=dict(p50=per_policy["share"][1]["p50"], p99=per_policy["share"][1]["p99"],
-                                                 mean=per_policy["share"][1]["mean"])),
-                fill_policy=dict(value=n / per_policy["fill"][0], unit="waveforms/s",
-                                 latency_s=dict(p50=per_policy["fill"][1]["p50"],
-                                                p99=per_policy["fill"][1]["p99"],
-                                                mean=per_policy["fill"][1]["mean"])),
-                priority_policy=dict(value=n / per_policy["priority"][0], unit="waveforms/s",
-                                     latency_s=dict(p50=per_policy["priority"][1]["p50"],
-                                                    p99=per_policy["priority"][1]["p99"],
-                                                    mean=per_policy["priority"][1]["mean"])),
-                one_by_one=dict(value=n / wall1, unit="waveforms/s",
-                                latency_s=dict(p50=float(np.percentile(lat1, 50)),
-                                               p99=float(np.percentile(lat1, 99)), mean=float(lat1.mean()))),
-                rate_sweep=sweep)
+    per_policy = {policy: served(reqs, policy) for policy in policies}
+    wall1, lat1 = one_at_a_time(reqs)
+    lat_1 = dict(p50=float(np.percentile(lat1, 50)), p99=float(np.percentile(lat1, 99)), mean=float(lat1.mean()))
+    out = dict(requests=n, point_updates=upd, slice_steps=slice_steps, fill_points=fill_points,
+               memory_budget_gb=memory_gb,
+               policies={p: dict(value=n / w, unit="waveforms/s", latency_s=stats(st), grid_pt_updates_per_s=upd / w)
+                         for p, (w, st, _) in per_policy.items()},
+               one_by_one=dict(value=n / wall1, unit="waveforms/s", latency_s=lat_1))
+    # latency by request size: the short jobs' tail beside the long ones
+    first = per_policy[policies[0]][2]
+    short = [x for x in first.values() if x.request.steps * x.request.nr * x.request.nth < np.median(
+        [r.steps * r.nr * r.nth for r in reqs])]
+    if short:
+        ls = np.array([x.latency for x in short])
+        ids = [x.rid for x in short]
+        l1s = lat1[ids]
+        out["short_half"] = dict(policy=policies[0], p50=float(np.percentile(ls, 50)), p99=float(np.percentile(ls, 99)),
+                                 one_by_one_p50=float(np.percentile(l1s, 50)),
+                                 one_by_one_p99=float(np.percentile(l1s, 99)))
+    if sweep:
+        rows = []
+        for mult in sweep:
+            r8 = mult * n / wall1
+            rq = [request(d) for d in inputs.serving_requests(n_requests, r8)]
+            w_f, st_f, _ = served(rq, "fill")
+            w_a, st_a, _ = served(rq, "async")
+            w_1, l_1 = one_at_a_time(rq)
+            rows.append(dict(rate_per_s=r8, load=mult,
+                             fill=dict(value=n / w_f, **stats(st_f)), async_policy=dict(value=n / w_a, **stats(st_a)),
+                             one_by_one=dict(value=n / w_1, p50=float(np.percentile(l_1, 50)),
+                                             p99=float(np.percentile(l_1, 99)), mean=float(l_1.mean()))))
+        out["rate_sweep"] = rows
+    return out
+
+
+def run_serving(args):
+    from paper_1206_0270_gb300 import build
+    build.build()
+    from paper_1206_0270_gb300 import inputs, serve as S
+    from paper_1206_0270_gb300 import teuk as T
+    raw = inputs.serving_requests(args.requests, args.rate, long_tail=args.long_tail)
+    sweep = [float(x) for x in args.rate_sweep.split(",") if x.strip()]
+    r = serving_result(T, S, raw, slice_steps=args.slice, fill_points=args.fill_points, memory_gb=args.memory_gb,
+                       policies=("async", "fill", "share", "priority"), sweep=sweep, n_requests=args.requests,
+                       rate=args.rate)
+    a = r["policies"]["async"]
+    line = dict(metric="served waveforms/s", value=a["value"], unit="waveforms/s", n_gpus=1, steps=1, warmup=0,
+                ms_per_step=1e3 * r["requests"] / a["value"], higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload="serving", requests=r["requests"], rate_per_s=args.rate,
+                            slice_steps=args.slice, fill_points=args.fill_points, memory_budget_gb=args.memory_gb,
+                            point_updates=r["point_updates"], grids="2048x64..32768x512",
+                            steps="logU[1e3, 1e4]", long_tail=args.long_tail),
+                policy="async", latency_s=a["latency_s"], grid_pt_updates_per_s=a["grid_pt_updates_per_s"],
+                policies=r["policies"], one_by_one=r["one_by_one"], short_half=r.get("short_half"),
+                rate_sweep=r.get("rate_sweep"))
     print(json.dumps(line), flush=True)
     return 0
 
@@ -680,6 +769,10 @@ def main():
                     help="serving: arrival rates to sweep, as multiples of the measured one-at-a-time capacity "
                          "('' to skip)")
     ap.add_argument("--memory-gb", type=float, default=200.0, help="serving: device memory budget (GiB)")
+    ap.add_argument("--long-tail", type=int, default=0,
+                    help="serving: number of long requests (1e5..1e6 steps, 8192x128..32768x512) in the stream")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the batched and serving blocks of the default run")
     args = ap.parse_args()
     if args.workload == "serving":
         return run_serving(args)

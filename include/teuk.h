@@ -88,9 +88,11 @@ typedef struct {
  * discrete angular-plus-potential operator over all nodes and mid-points.
  * The source terms of Eqs. (3)-(4) integrate oscillations of frequency omega
  * like explicit midpoint RK2, whose amplification per step is
- * sqrt(1 + (omega dt)^4 / 4); c_theta = 0.1 keeps the stiffest mode's growth
- * below e^{1.25} over 1e5 steps.  Uses g->nr, nth, rstar_min, rstar_max
- * (g->dt is ignored).  Host-only, no GPU needed. */
+ * sqrt(1 + (omega dt)^4 / 4): the stiffest modes, next to the poles, grow
+ * unless c_theta is small (0.1) or the angular dissipation of
+ * teuk_set_dissipation damps them (eps = 1 allows c_theta = 0.8).  Uses
+ * g->nr, nth, rstar_min, rstar_max (g->dt is ignored).  Host-only, no GPU
+ * needed. */
 int teuk_stable_dt(const teuk_grid *g, double a, int s, int m, double c_r, double c_theta,
                    double *dt_out);
 
@@ -102,7 +104,10 @@ int teuk_stable_dt(const teuk_grid *g, double a, int s, int m, double c_r, doubl
  * cuda_stream: a cudaStream_t (or NULL).  On success *out receives the handle. */
 int teuk_create(const teuk_grid *g, double a, int s, int m, void *cuda_stream, teuk_handle **out);
 
-/* Release all device memory of the handle (synchronises its stream). */
+/* Release all device memory of the handle: the state u = {Phi, Pi} of the
+ * first-order form of Eq. (2)'s mode equation (section "Teukolsky Code"),
+ * the coefficient planes and the waveform ring.  Synchronises its stream.
+ * TEUK_ERR_BAD_ARG for NULL, TEUK_ERR_STATE while a batch owns the handle. */
 int teuk_destroy(teuk_handle *h);
 
 /* Initial data from HOST arrays phi, pi (interleaved complex [nr][nth]).
@@ -119,10 +124,13 @@ int teuk_set_initial_device(teuk_handle *h, const double *phi_dev, const double 
  * the grid. */
 int teuk_set_source(teuk_handle *h, const teuk_orbit *orbit);
 
-/* Waveform sampling: after every step n (counted from the last
- * teuk_set_initial) with n % every == 0, Phi(r*_k, theta_j), j < nth, is copied
- * into a device ring buffer of `capacity` samples, k the node nearest to
- * rstar_ext.  Allocates the ring buffer; clears earlier samples. */
+/* Waveform sampling (the waveforms of the paper's results section, e.g.
+ * Fig. 1, are the field read at a distant observer): after every step n
+ * (counted from the last teuk_set_initial) with n % every == 0,
+ * Phi(r*_k, theta_j), j < nth, is copied into a device ring buffer of
+ * `capacity` samples, k the node nearest to rstar_ext.  Allocates the ring
+ * buffer; clears earlier samples.  TEUK_ERR_BAD_ARG if rstar_ext is off the
+ * grid, every < 1 or capacity < 1; TEUK_ERR_OOM if the ring does not fit. */
 int teuk_set_extraction(teuk_handle *h, double rstar_ext, int every, long capacity);
 
 /* Run the handle's future work on `cuda_stream` (a cudaStream_t owned by the
@@ -134,13 +142,33 @@ int teuk_set_extraction(teuk_handle *h, double rstar_ext, int every, long capaci
  * counterpart. */
 int teuk_set_stream(teuk_handle *h, void *cuda_stream);
 
-/* Advance n >= 0 time steps, asynchronously on the handle's stream.  Full
- * chunks of steps replay a captured CUDA graph. */
+/* Advance n >= 0 time steps of the two-step Lax-Wendroff scheme, Eqs. (3)
+ * and (4) (section "Teukolsky Code"): predictor to the radial mid-points at
+ * the half step, corrector to the nodes, angular derivatives and sources in
+ * S, Phi = Pi = 0 on the radial boundary rows, plus the angular dissipation
+ * if set.  Asynchronous on the handle's stream; full chunks of steps replay a
+ * captured CUDA graph.  TEUK_ERR_BAD_ARG for n < 0, TEUK_ERR_STATE while a
+ * batch owns the handle, TEUK_ERR_CUDA if a launch fails. */
 int teuk_step(teuk_handle *h, long n);
 
-/* Copy the waveform samples taken since the previous call (oldest first) to
- * the host: t_out[k] and phi_out[k][nth] (interleaved complex), at most cap
- * samples; *n_out receives the number copied.  Synchronises the stream.
+/* Angular Kreiss-Oliger dissipation (Kreiss & Oliger 1973, the sixth-order
+ * member of the family; the paper's scheme, Eqs. 3-4, has none, and this is
+ * the reading that lets the time step grow): each corrector subtracts
+ * (eps/64) D6 u^n from the new state of every interior row, for Phi and Pi,
+ *   D6 u_j = -(u_{j-3} + u_{j+3}) + 6 (u_{j-2} + u_{j+2})
+ *            - 15 (u_{j-1} + u_{j+1}) + 20 u_j,
+ * with the ghost values of the pole rule (reflection across the pole with
+ * the parity of |m|).  On cos(k theta) / sin(k theta) it multiplies by
+ * 1 - eps sin^6(k dtheta / 2).  eps = 0 (the default) is the bare scheme;
+ * otherwise 1e-9 <= eps < 2 (TEUK_ERR_BAD_ARG).  Synchronises the stream;
+ * TEUK_ERR_STATE while a batch owns the handle. */
+int teuk_set_dissipation(teuk_handle *h, double eps);
+
+/* Copy the waveform samples (see teuk_set_extraction; the observer's signal
+ * of the paper's results section) taken since the previous call (oldest
+ * first) to the host: t_out[k] and phi_out[k][nth] (interleaved complex), at
+ * most cap samples; *n_out receives the number copied.  Synchronises the
+ * stream.  TEUK_ERR_STATE if no extraction is set.
  * TEUK_ERR_OVERFLOW if more samples than the ring capacity were taken since
  * the previous call (the newest `capacity` samples are returned). */
 int teuk_extract(teuk_handle *h, double *t_out, double *phi_out, long cap, long *n_out);
@@ -153,7 +181,10 @@ int teuk_extract(teuk_handle *h, double *t_out, double *phi_out, long cap, long 
  * rows are forced to zero.  Synchronises. */
 int teuk_set_state(teuk_handle *h, const double *phi, const double *pi, long step);
 
-/* Copy the current state to HOST arrays (either may be NULL).  Synchronises. */
+/* Copy the current state u = {Phi, Pi} (the solution vector of Eq. (3),
+ * section "Teukolsky Code") to HOST arrays, layout as in teuk_set_initial
+ * (either pointer may be NULL).  Synchronises.  TEUK_ERR_CUDA if a copy
+ * fails. */
 int teuk_get_state(teuk_handle *h, double *phi, double *pi);
 
 /* Copy the current state to DEVICE arrays (stream-ordered, asynchronous). */
@@ -231,19 +262,23 @@ int teuk_time_kernels(teuk_handle *h, long n, double *ms_out);
 long teuk_launches_for(const teuk_handle *h, long n);
 
 /* One time step that allocates no device memory.  The paper has no
- * counterpart: this entry point serves callers that cannot allocate while
- * they step -- code running while a stream is being captured into a CUDA
- * graph (cudaMalloc is not permitted there), real-time loops that must not
- * block in the allocator, and processes whose device memory is owned by
- * another framework's pool.
+ * counterpart: this entry point serves callers that cannot call cudaMalloc
+ * while they step -- real-time loops that must not block in the allocator,
+ * and processes whose device memory is owned by another framework's pool
+ * (the library must not take memory behind that pool's back).
  *
- * Advances the DEVICE state (phi_in, pi_in) by one time step (Eqs. 3-4, split
- * kernels) into the DEVICE buffers (phi_out, pi_out), all interleaved complex
- * [nr][nth] and owned by the caller; outputs must not alias inputs.  Uses the
- * handle's coefficients and source (phase at t = step_index * dt), issues its
- * work on the handle's stream and returns without waiting.  No waveform is
- * sampled; the output boundary rows are set to zero.  The handle's own state,
- * step counter and ring buffer are neither read nor changed.
+ * Advances the DEVICE state (phi_in, pi_in) by one time step of the
+ * library's scheme (the split kernels, the handle's coefficients, source and
+ * dissipation) into the DEVICE buffers (phi_out, pi_out), all interleaved
+ * complex [nr][nth] and owned by the caller.  No output may overlap an input
+ * or the other output (checked by address range: TEUK_ERR_BAD_ARG).  Rows 0
+ * and nr-1 of the inputs must be zero, as in every state this library
+ * produces (the radial boundary rows; the kernels read them as they are);
+ * the output boundary rows are set to zero, so chained calls keep them so.
+ * step_index is passed by value to the kernels of this call: the source
+ * phase is that of t = step_index * dt.  Issues its work on the handle's
+ * stream and returns without waiting.  No waveform is sampled; the handle's
+ * own state, step counter and ring buffer are neither read nor changed.
  *
  * The half step is kept in a static device array of 32 MiB inside libteuk:
  * every GPU that loads the library holds it until the process exits, and it

@@ -176,8 +176,9 @@ static void choose_launch(teuk_handle *h, int rows_per_block)
     if (rows_per_block <= 0) {
         const int threads = fused_block_threads(h->nth);
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel_ptr(h->sp.real_coef, h->sp.fixed_point), threads,
-                                                          fused_smem_bytes(h->nth)) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
+                                                          fused_kernel_ptr(h->sp.real_coef, h->sp.fixed_point, h->sp.ko),
+                                                          threads, fused_smem_bytes(h->nth, h->sp.ko)) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         const int want = std::max(1, 16 / std::max(1, threads / 32));
@@ -307,6 +308,9 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     p.one = 1.0; p.nzero = -0.0;
     p.real_coef = su.real_coef;
     p.fixed_point = 1;
+    p.ko = 0;  // the bare scheme until teuk_set_dissipation
+    p.parity = h->parity;
+    p.k0 = 1.0; p.k1 = 0.0; p.k2 = 0.0; p.k3 = 0.0;
     h->su = su;
     p.pred = PredPlanes{su.pa, su.pb, su.eb, su.KAp, su.KCp, su.P1, su.Q1, su.Q2};
     p.corr = CorrPlanes{su.tb, su.nt2, su.KAc, su.KCc, su.R1, su.R3, su.R4};
@@ -315,7 +319,8 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     p.step_base = h->d_step;
     h->variant = nth <= kTileMaxThreads ? 2 : 1;
     // Shared memory stays below the 48 KB default: the fused kernel takes
-    // 64 (nth + 2) bytes <= 16.5 KB, a split tile 16 R (TW + 2) <= 8.3 KB.
+    // 64 (nth + 2) bytes, plus 64 (nth + 6) with the dissipation, <= 33 KB;
+    // a split tile 16 R (TW + 2), plus 32 R (TW + 6), <= 25 KB.
     if (nth <= kFusedMaxNth) choose_launch(h, 0);  // the fused kernel's shape, for when it is selected
     if (h->variant != 0) {  // the two-kernel variants keep the half step in device memory
         if (cudaMalloc(&h->phiH, 2 * Nm * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return bail(TEUK_ERR_OOM); }
@@ -625,6 +630,25 @@ extern "C" int teuk_set_option(teuk_handle *h, int option, long value)
     }
 }
 
+extern "C" int teuk_set_dissipation(teuk_handle *h, double eps)
+{
+    if (!h) return TEUK_ERR_BAD_ARG;
+    if (h->in_batch) return fail(h, TEUK_ERR_STATE, "teuk_set_dissipation: the handle belongs to a batch (remove it first)");
+    if (!(eps == 0.0 || (eps >= 1e-9 && eps < 2.0)))
+        return fail(h, TEUK_ERR_BAD_ARG, "teuk_set_dissipation: eps must be 0 or in [1e-9, 2)");
+    CU(cudaStreamSynchronize(h->stream));
+    destroy_graphs(h);  // the graphs hold the step parameters by value
+    StepParams &p = h->sp;
+    p.ko = eps > 0.0 ? 1 : 0;
+    p.k0 = 1.0 - 20.0 * eps / 64.0;
+    p.k1 = 15.0 * eps / 64.0;
+    p.k2 = -6.0 * eps / 64.0;
+    p.k3 = eps / 64.0;
+    h->eps = eps;
+    if (h->variant == 0 && h->nth <= kFusedMaxNth) choose_launch(h, h->rows_per_block);  // occupancy depends on it
+    return TEUK_OK;
+}
+
 extern "C" int teuk_get_launch(const teuk_handle *h, int *rows_per_block, int *nblocks)
 {
     if (!h || !rows_per_block || !nblocks) return TEUK_ERR_BAD_ARG;
@@ -716,13 +740,12 @@ extern "C" int teuk_set_kernel(teuk_handle *h, int variant)
 // One time step without any device allocation
 // ---------------------------------------------------------------------------
 //
-// For callers that cannot allocate device memory while they step: code that
-// runs while a stream is being captured into a CUDA graph (cudaMalloc is not
-// allowed there), real-time loops that must not block in the allocator, and
-// hosts whose device memory is owned by another framework's pool.  The half
-// step lives in the static array below instead of a per-handle buffer.  The
-// array (32 MiB) is part of the library image: every GPU that loads libteuk
-// holds it until the process exits.
+// For callers that cannot call cudaMalloc while they step: real-time loops
+// that must not block in the allocator, and processes whose device memory is
+// owned by another framework's pool (the library must not take memory behind
+// that pool's back).  The half step lives in the static array below instead
+// of a per-handle buffer.  The array (32 MiB) is part of the library image:
+// every GPU that loads libteuk holds it until the process exits.
 
 static const long long kNoAllocMaxMid = 1LL << 20;  // mid-point values: (nr - 1) * nth <= 1,048,576
 // Layout: Phi^{1/2} [kNoAllocMaxMid] double2, Pi^{1/2} [kNoAllocMaxMid] double2, then
@@ -747,8 +770,17 @@ extern "C" int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const dou
         return fail(h, TEUK_ERR_BAD_ARG,
                     "teuk_step_noalloc: (nr - 1) * nth = " + std::to_string(mids) +
                         " exceeds the static scratch of 1048576 mid-point values (32 MiB)");
-    if (phi_in == phi_out || pi_in == pi_out || (const double *)phi_out == pi_in || (const double *)pi_out == phi_in)
-        return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: output buffers must not alias the inputs");
+    // every buffer spans nr * nth complex values; no output may share a byte with
+    // an input or with the other output
+    {
+        const size_t span = (size_t)h->nr * h->nth * sizeof(double2);
+        const char *in[2] = {(const char *)phi_in, (const char *)pi_in};
+        const char *out[2] = {(const char *)phi_out, (const char *)pi_out};
+        auto overlap = [span](const char *x, const char *y) { return x < y + span && y < x + span; };
+        if (overlap(out[0], out[1]) || overlap(out[0], in[0]) || overlap(out[0], in[1]) || overlap(out[1], in[0]) ||
+            overlap(out[1], in[1]))
+            return fail(h, TEUK_ERR_BAD_ARG, "teuk_step_noalloc: an output buffer overlaps an input or the other output");
+    }
     int dev = -1;
     CU(cudaGetDevice(&dev));
     if (dev != h->device || dev < 0 || dev >= 128)

@@ -207,10 +207,12 @@ static int rebuild(teuk_batch *b)
     std::vector<int> off(2 * (size_t)(b->cap_jobs + 1), 0);
     int *poff = off.data(), *coff = off.data() + (b->cap_jobs + 1);
     size_t smem = 0;
+    int ko_any = 0;
     for (int q = 0; q < nj; ++q) {
         teuk_handle *h = b->jobs[b->active[q]].h;
         JobDesc &d = b->host_desc[q];
         d.p = h->sp;
+        ko_any |= h->sp.ko;
         d.phi[0] = h->phi[0]; d.phi[1] = h->phi[1];
         d.pi[0] = h->pi[0]; d.pi[1] = h->pi[1];
         d.phiH = h->phiH; d.piH = h->piH;
@@ -224,8 +226,9 @@ static int rebuild(teuk_batch *b)
     }
     b->pred_tiles = poff[nj];
     b->corr_tiles = coff[nj];
-    smem = batch_smem_bytes(b->block);
+    smem = batch_smem_bytes(b->block, ko_any);
     b->smem = smem;
+    BCU(batch_allow_smem(smem));
     int sms = 0, per_sm = 0;
     BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     for (int w = 0; w < 2; ++w) {

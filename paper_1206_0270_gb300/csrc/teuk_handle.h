@@ -10,6 +10,7 @@
 struct teuk_handle {
     int nr = 0, nth = 0, s = 0, m = 0, parity = 1;
     double a = 0, rstar_min = 0, rstar_max = 0, h = 0, dth = 0, dt = 0;
+    double eps = 0;  // strength of the angular Kreiss-Oliger dissipation (0: none)
     int device = 0, num_sms = 0;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     bool own_stream = false;

@@ -31,6 +31,14 @@
 //   tb = 2 beta, R1 = 2 beta - (dt/2) c_t, R2 = -2 beta - (dt/2) c_t, nt2 = -4 beta,
 //   R3 = 2 gamma - (dt/2)(W - kappa B), R4 = -2 gamma - (dt/2)(W - kappa B),
 //   KA' = (dt/2) kappa A, KC' = (dt/2) kappa C, gC = dt G        (node values)
+//
+// With the angular Kreiss-Oliger dissipation of strength eps the corrector
+// also subtracts (eps/64) D6 u^n, D6 u_j = 20 u_j - 15 s1 + 6 s2 - s3 with the
+// pair sums s_q = u_{j-q} + u_{j+q} of the same row (ghosts by reflection
+// across the pole with the parity of the pole rule), for Phi and Pi alike:
+//   Phi^{n+1} = k0 Phi_i + k1 s1 + k2 s2 + k3 s3 - tb Phi^{i+1/2} + ...
+//   Pi^{n+1}  = k0 Pi_i  + k1 s1' + k2 s2' + k3 s3' + R1 tau' + ...
+// k0 = 1 - 20 eps/64, k1 = 15 eps/64, k2 = -6 eps/64, k3 = eps/64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -83,6 +91,9 @@ struct StepParams {
     double one, nzero;     // 1 and -0: operands that turn FP64 adds and multiplies into FMAs
     int real_coef;         // 1: P1, Q1, Q2, R1, R3, R4 are packed real planes (no imaginary parts)
     int fixed_point;       // 1: Pi rows as fixed-point sums (teuk_fixed.h); 0: FP64 FMA chains
+    int ko;                // 1: angular Kreiss-Oliger dissipation on (coefficients k0..k3)
+    int parity;            // ghost parity of the pole rule (+1 even |m|, -1 odd |m|)
+    double k0, k1, k2, k3; // 1 - 20 eps/64, 15 eps/64, -6 eps/64, eps/64
     PredPlanes pred;
     CorrPlanes corr;
     SourceWindow src;
@@ -158,17 +169,18 @@ cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const in
 
 cudaError_t launch_advance_batch(const JobDesc *jobs, int njobs, long long by, cudaStream_t st);
 
-size_t batch_smem_bytes(int block);
+size_t batch_smem_bytes(int block, int ko);
+cudaError_t batch_allow_smem(size_t smem);
 int tile_width_for(int nth, int max_width);
 const void *batch_kernel_ptr(int which);
 
 int fused_block_threads(int nth);
-size_t fused_smem_bytes(int nth);
-const void *fused_kernel_ptr(int real, int fixed_point);
+size_t fused_smem_bytes(int nth, int ko);
+const void *fused_kernel_ptr(int real, int fixed_point, int ko);
 int split_tile_width(int nth);
 int split_theta_tiles(int nth);
 int split_rows_per_block(int nth, int fixed_point);
-size_t split_smem_bytes(int nth, int rows = 0);
-const void *split_kernel_ptr(int which, int real, int fixed_point);
+size_t split_smem_bytes(int nth, int rows = 0, int ko = 0);
+const void *split_kernel_ptr(int which, int real, int fixed_point, int ko = 0);
 
 }  // namespace teuk

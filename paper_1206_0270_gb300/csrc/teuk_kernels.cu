@@ -334,15 +334,62 @@ __device__ __forceinline__ HalfStep predict(const StepParams &p, size_t k, doubl
     return predict_c<REAL, FX>(load_pred<REAL>(p, k), p.q, ops_of(p), phi0, pi0, phi1, pi1, sup, sdn);
 }
 
+// Angular Kreiss-Oliger dissipation of the corrector: pair sums
+// s_q = u_{j-q} + u_{j+q} (q = 1, 2, 3) of the old state on the node's row and
+// the weights k0..k3 of StepParams (formulas in teuk_internal.h).
+struct KoSums {
+    double2 s1, s2, s3;
+};
+struct KoCoef {
+    double k0, k1, k2, k3;
+};
+__device__ __forceinline__ KoCoef ko_of(const StepParams &p) { return KoCoef{p.k0, p.k1, p.k2, p.k3}; }
+
+// Theta index j of a row continued past the poles by the ghost rule: the
+// reflection across theta = 0 maps j < 0 to -1 - j, the one across theta = pi
+// maps j >= nth to 2 nth - 1 - j, each with the factor `parity`; repeated for
+// rows shorter than the stencil (nth >= 2 and |offset| <= 3 need at most
+// two).  Returns the grid index and sets *sign.
+__device__ __forceinline__ int ko_fold(int j, int nth, int parity, double *sign)
+{
+    double sg = 1.0;
+    for (int it = 0; it < 4 && (j < 0 || j >= nth); ++it) {
+        j = j < 0 ? -1 - j : 2 * nth - 1 - j;
+        sg *= (double)parity;
+    }
+    *sign = sg;
+    return min(max(j, 0), nth - 1);
+}
+
+// Value of column j (any integer within 3 of the grid) of a row of a field
+// that another kernel writes, with the ghost rule applied.
+__device__ __forceinline__ double2 ko_load(const double2 *row, int j, int nth, int parity)
+{
+    double sg;
+    const int jj = ko_fold(j, nth, parity, &sg);
+    const double2 v = ldcg(row + jj);
+    return make_double2(sg * v.x, sg * v.y);
+}
+
+// Pair sums around entry c of a row staged in shared memory.
+__device__ __forceinline__ KoSums ko_sums(const double2 *u, int c, const Ops ops)
+{
+    return KoSums{add2(u[c - 1], u[c + 1], ops), add2(u[c - 2], u[c + 2], ops), add2(u[c - 3], u[c + 3], ops)};
+}
+
 // Corrector (Eq. 4) at one node.  hp: half step at i + 1/2, hm: at i - 1/2,
 // sup/sdn: sigma' = Phi^{i+1/2} + Phi^{i-1/2} at j+1, j-1.  As in the
-// predictor, the Pi row is a fixed-point sum with an FP64 fallback.
-template <bool REAL>
+// predictor, the Pi row is a fixed-point sum with an FP64 fallback.  KO adds
+// the dissipation: Pi^n enters with weight k0 and kdpi = k1 s1 + k2 s2 + k3 s3
+// (formed in FP64 from the pair sums of Pi^n) with weight one.
+template <bool REAL, bool KO>
 __device__ __forceinline__ double2 corr_pi_fp64(const CorrCoef &c, const Ops ops, double2 pi, double2 tau,
-                                                const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn)
+                                                const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn,
+                                                double k0, double2 kdpi)
 {
     // R1 Pi^{+} + R2 Pi^{-} = R1 tau' + (R2 - R1) Pi^{-}, tau' = Pi^{+} + Pi^{-}, R2 - R1 = -2 tb (nt2)
     double2 npi = pi;
+    if (KO) npi = make_double2(fma_rn(k0, pi.x, kdpi.x), fma_rn(k0, pi.y, kdpi.y));
     kfma<REAL>(npi, c.R1, tau);
     rfma(npi, c.nt2, hm.pi);
     kfma<REAL>(npi, c.R3, hp.phi);
@@ -352,12 +399,14 @@ __device__ __forceinline__ double2 corr_pi_fp64(const CorrCoef &c, const Ops ops
     return npi;
 }
 
-template <bool REAL, bool FX>
+template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, double2 pi, double2 tau,
-                                           const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn)
+                                           const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn,
+                                           double k0, double2 kdpi)
 {
-    if (!FX) return corr_pi_fp64<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
+    if (!FX) return corr_pi_fp64<REAL, KO>(c, ops, pi, tau, hp, hm, sup, sdn, k0, kdpi);
     const Fx one = fx_unpack_coef(1.0);
+    const Fx c0 = KO ? fx_unpack_coef(k0) : one;
     const Fx pr = fx_unpack(pi.x), pim = fx_unpack(pi.y), tr = fx_unpack(tau.x), ti = fx_unpack(tau.y);
     const Fx mr = fx_unpack(hm.pi.x), mi = fx_unpack(hm.pi.y);
     const Fx ar = fx_unpack(hp.phi.x), ai = fx_unpack(hp.phi.y), br = fx_unpack(hm.phi.x), bi = fx_unpack(hm.phi.y);
@@ -367,7 +416,26 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
     const Fx KA = fx_unpack_coef(c.KA), KC = fx_unpack_coef(c.KC);
     double2 o;
     bool ok;
-    if (REAL) {
+    if (KO) {
+        const Fx gr = fx_unpack(kdpi.x), gi = fx_unpack(kdpi.y);
+        if (REAL) {
+            const Fx C[8] = {c0, R1r, nt2, R3r, R4r, KA, KC, one};
+            const Fx Xr[8] = {pr, tr, mr, ar, br, ur, dr, gr};
+            const Fx Xi[8] = {pim, ti, mi, ai, bi, ui, di, gi};
+            const uint32_t F[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            ok = fx_dot<8>(C, Xr, F, &o.x);
+            ok &= fx_dot<8>(C, Xi, F, &o.y);
+        } else {
+            const Fx R1i = fx_unpack_coef(c.R1.y), R3i = fx_unpack_coef(c.R3.y), R4i = fx_unpack_coef(c.R4.y);
+            const Fx C[11] = {c0, R1r, R1i, nt2, R3r, R3i, R4r, R4i, KA, KC, one};
+            const Fx Xr[11] = {pr, tr, ti, mr, ar, ai, br, bi, ur, dr, gr};
+            const uint32_t Fr[11] = {0, 0, 1, 0, 0, 1, 0, 1, 0, 0, 0};
+            const Fx Xi[11] = {pim, ti, tr, mi, ai, ar, bi, br, ui, di, gi};
+            const uint32_t Fi[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            ok = fx_dot<11>(C, Xr, Fr, &o.x);
+            ok &= fx_dot<11>(C, Xi, Fi, &o.y);
+        }
+    } else if (REAL) {
         const Fx C[7] = {one, R1r, nt2, R3r, R4r, KA, KC};
         const Fx Xr[7] = {pr, tr, mr, ar, br, ur, dr};
         const Fx Xi[7] = {pim, ti, mi, ai, bi, ui, di};
@@ -384,30 +452,48 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
         ok = fx_dot<10>(C, Xr, Fr, &o.x);
         ok &= fx_dot<10>(C, Xi, Fi, &o.y);
     }
-    if (!ok) o = corr_pi_fp64<REAL>(c, ops, pi, tau, hp, hm, sup, sdn);
+    if (!ok) o = corr_pi_fp64<REAL, KO>(c, ops, pi, tau, hp, hm, sup, sdn, k0, kdpi);
     return o;
 }
 
-template <bool REAL, bool FX>
+// k1 s1 + k2 s2 + k3 s3 of a field's pair sums
+__device__ __forceinline__ double2 ko_combine(const KoCoef &kc, const KoSums &ks, const Ops ops)
+{
+    double2 d = make_double2(fma_rn(kc.k1, ks.s1.x, ops.nzero), fma_rn(kc.k1, ks.s1.y, ops.nzero));
+    rfma(d, kc.k2, ks.s2);
+    rfma(d, kc.k3, ks.s3);
+    return d;
+}
+
+template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, const Ops ops, double2 phi,
                                           double2 pi, const HalfStep &hp, const HalfStep &hm, double2 sup,
-                                          double2 sdn, double2 *phi_out, double2 *pi_out)
+                                          double2 sdn, const KoCoef &kc, const KoSums &kphi, const KoSums &kpi,
+                                          double2 *phi_out, double2 *pi_out)
 {
     const double2 tau = add2(hp.pi, hm.pi, ops);
     double2 nphi = phi;
+    double2 kdpi = make_double2(0.0, 0.0);
+    if (KO) {
+        const double2 kd = ko_combine(kc, kphi, ops);
+        nphi = make_double2(fma_rn(kc.k0, phi.x, kd.x), fma_rn(kc.k0, phi.y, kd.y));
+        kdpi = ko_combine(kc, kpi, ops);
+    }
     rfma(nphi, -c.tb, hp.phi);
     rfma(nphi, c.tb, hm.phi);
     rfma(nphi, half_dt, tau);
     *phi_out = nphi;
-    *pi_out = corr_pi<REAL, FX>(c, ops, pi, tau, hp, hm, sup, sdn);
+    *pi_out = corr_pi<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, kc.k0, kdpi);
 }
 
-template <bool REAL, bool FX>
+template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 phi, double2 pi,
                                         const HalfStep &hp, const HalfStep &hm, double2 sup,
-                                        double2 sdn, double2 *phi_out, double2 *pi_out)
+                                        double2 sdn, const KoSums &kphi, const KoSums &kpi, double2 *phi_out,
+                                        double2 *pi_out)
 {
-    correct_c<REAL, FX>(load_corr<REAL>(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, phi_out, pi_out);
+    correct_c<REAL, FX, KO>(load_corr<REAL>(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, ko_of(p), kphi,
+                            kpi, phi_out, pi_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,11 +501,16 @@ __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 p
 // ---------------------------------------------------------------------------
 
 // Shared memory: sigma and sigma' double buffers, each nth + 2 entries with
-// a zero ghost at both ends (their stencil weights are zero).
-size_t fused_smem_bytes(int nth) { return sizeof(double2) * 4 * (size_t)(nth + 2); }
+// a zero ghost at both ends (their stencil weights are zero); with the
+// dissipation also the row's old Phi and Pi, double-buffered, nth + 6 entries
+// each (three ghost columns past each pole).
+size_t fused_smem_bytes(int nth, int ko)
+{
+    return sizeof(double2) * (4 * (size_t)(nth + 2) + (ko ? 4 * (size_t)(nth + 6) : 0));
+}
 int fused_block_threads(int nth) { return ((nth + 31) / 32) * 32; }
 
-template <bool REAL, bool FX>
+template <bool REAL, bool FX, bool KO>
 __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, const double2 *__restrict__ Phi,
                                                       const double2 *__restrict__ Pi,
                                                       double2 *__restrict__ PhiO,
@@ -429,8 +520,10 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
     __shared__ double2 s_phase[2];
     const int nth = p.nth;
     const int W = nth + 2;
+    const int KW = nth + 6;
     double2 *s_sig = smem;          // [2][W]
     double2 *s_sgh = smem + 2 * W;  // [2][W]
+    double2 *s_u = smem + 4 * W;    // KO: [2][Phi, Pi][KW], entry c = column c - 3
     const int j = threadIdx.x;
     const bool act = j < nth;
     const int jj = act ? j : nth - 1;
@@ -488,7 +581,19 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
         }
         double2 *sg = s_sig + buf * W;
         if (act) sg[j + 1] = add2(phc, phn, ops_of(p));
+        double2 *uph = s_u + buf * 2 * KW, *upi = uph + KW;
+        if (KO && act) {
+            uph[j + 3] = phc;
+            upi[j + 3] = pic;
+        }
         __syncthreads();
+        if (KO && threadIdx.x < 6) {  // ghost columns -3..-1 and nth..nth+2, from the row itself
+            const int e = threadIdx.x < 3 ? threadIdx.x : nth + threadIdx.x;
+            double sgn;
+            const int jg = ko_fold(e - 3, nth, p.parity, &sgn);
+            uph[e] = make_double2(sgn * uph[jg + 3].x, sgn * uph[jg + 3].y);
+            upi[e] = make_double2(sgn * upi[jg + 3].x, sgn * upi[jg + 3].y);
+        }
         HalfStep hp = predict_c<REAL, FX>(pc, p.q, ops_of(p), phc, pic, phn, pin, sg[jj + 2], sg[jj]);
         if (src_mid && i >= sw.mid_lo && i <= sw.mid_hi)
             rfma(hp.pi, ldg(sw.gP + (size_t)(i - sw.mid_lo) * nth + jj), s_phase[0]);
@@ -498,7 +603,13 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
         __syncthreads();
         const size_t kc = (size_t)i * nth + jj;
         double2 nphi, npi;
-        correct_c<REAL, FX>(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], &nphi, &npi);
+        KoSums kphi{}, kpi{};
+        if (KO) {
+            kphi = ko_sums(uph, jj + 3, ops_of(p));
+            kpi = ko_sums(upi, jj + 3, ops_of(p));
+        }
+        correct_c<REAL, FX, KO>(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], ko_of(p), kphi, kpi,
+                                &nphi, &npi);
         if (src_node && i >= sw.node_lo && i <= sw.node_hi)
             rfma(npi, ldg(sw.gC + (size_t)(i - sw.node_lo) * nth + jj), s_phase[1]);
         if (act) {
@@ -517,18 +628,27 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
 }
 
 // The four instantiations of a step kernel (real or complex coefficient
-// planes, fixed-point or FP64 Pi rows) share one signature.
+// planes, fixed-point or FP64 Pi rows) share one signature; TEUK_PICK3 adds
+// the dissipation flag of corrector kernels.
 #define TEUK_PICK(K, real, fx) ((real) ? ((fx) ? K<true, true> : K<true, false>) : ((fx) ? K<false, true> : K<false, false>))
+#define TEUK_PICK3(K, real, fx, ko)                                                                            \
+    ((ko) ? ((real) ? ((fx) ? K<true, true, true> : K<true, false, true>)                                      \
+                    : ((fx) ? K<false, true, true> : K<false, false, true>))                                   \
+          : ((real) ? ((fx) ? K<true, true, false> : K<true, false, false>)                                    \
+                    : ((fx) ? K<false, true, false> : K<false, false, false>)))
 
-const void *fused_kernel_ptr(int real, int fixed_point) { return (const void *)TEUK_PICK(lw_step_fused, real, fixed_point); }
+const void *fused_kernel_ptr(int real, int fixed_point, int ko)
+{
+    return (const void *)TEUK_PICK3(lw_step_fused, real, fixed_point, ko);
+}
 
 cudaError_t launch_step_fused(const StepParams &p, const double2 *Phi, const double2 *Pi,
                               double2 *PhiO, double2 *PiO, int k, int rows_per_block, int nblocks,
                               cudaStream_t st)
 {
     const int threads = fused_block_threads(p.nth);
-    TEUK_PICK(lw_step_fused, p.real_coef, p.fixed_point)<<<nblocks, threads, fused_smem_bytes(p.nth), st>>>(
-        p, Phi, Pi, PhiO, PiO, k, rows_per_block);
+    TEUK_PICK3(lw_step_fused, p.real_coef, p.fixed_point, p.ko)<<<nblocks, threads, fused_smem_bytes(p.nth, p.ko),
+                                                                 st>>>(p, Phi, Pi, PhiO, PiO, k, rows_per_block);
     return cudaGetLastError();
 }
 
@@ -562,7 +682,7 @@ __global__ void lw_predict_kernel(StepParams p, const double2 *__restrict__ Phi,
     PiH[k0] = o.pi;
 }
 
-template <bool REAL, bool FX>
+template <bool REAL, bool FX, bool KO>
 __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
                                   const double2 *__restrict__ Pi, const double2 *__restrict__ PhiH,
                                   const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
@@ -584,7 +704,21 @@ __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
     const double2 sup = add2(PhiH[kp - j + ju], PhiH[km - j + ju], ops_of(p));
     const double2 sdn = add2(PhiH[kp - j + jd], PhiH[km - j + jd], ops_of(p));
     double2 nphi, npi;
-    correct<REAL, FX>(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, &nphi, &npi);
+    KoSums kphi{}, kpi{};
+    if (KO) {  // pair sums of the old state along the row, ghosts by the pole rule
+        const double2 *rp = Phi + (size_t)i * nth, *rq = Pi + (size_t)i * nth;
+        double2 a[6], b[6];
+        for (int q = 0; q < 3; ++q) {
+            a[q] = ko_load(rp, j - 1 - q, nth, p.parity);
+            a[q + 3] = ko_load(rp, j + 1 + q, nth, p.parity);
+            b[q] = ko_load(rq, j - 1 - q, nth, p.parity);
+            b[q + 3] = ko_load(rq, j + 1 + q, nth, p.parity);
+        }
+        const Ops ops = ops_of(p);
+        kphi = KoSums{add2(a[0], a[3], ops), add2(a[1], a[4], ops), add2(a[2], a[5], ops)};
+        kpi = KoSums{add2(b[0], b[3], ops), add2(b[1], b[4], ops), add2(b[2], b[5], ops)};
+    }
+    correct<REAL, FX, KO>(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, kphi, kpi, &nphi, &npi);
     const long long n = *p.step_base + k;
     const SourceWindow &sw = p.src;
     if (sw.active && i >= sw.node_lo && i <= sw.node_hi)
@@ -608,8 +742,9 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
         TEUK_PICK(lw_predict_kernel, p.real_coef, p.fixed_point)<<<(unsigned)((np + threads - 1) / threads), threads,
                                                                     0, st>>>(p, Phi, Pi, PhiH, PiH, k);
     if (part != 0)
-        TEUK_PICK(lw_correct_kernel, p.real_coef, p.fixed_point)<<<(unsigned)((nc + threads - 1) / threads), threads,
-                                                                    0, st>>>(p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);
+        TEUK_PICK3(lw_correct_kernel, p.real_coef, p.fixed_point, p.ko)<<<(unsigned)((nc + threads - 1) / threads),
+                                                                           threads, 0, st>>>(p, Phi, Pi, PhiH, PiH,
+                                                                                             PhiO, PiO, k);
     return cudaGetLastError();
 }
 
@@ -625,9 +760,7 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
 // sigma(j0 - 1) and sigma(j0 + TW) itself.  Small CTAs keep several tiles
 // resident per SM (the fixed-point Pi rows need up to 128 registers per
 // thread).
-#ifndef TEUK_SPLIT_TILE_MAX
-#define TEUK_SPLIT_TILE_MAX 128
-#endif
+constexpr int kSplitTileMax = 128;  // widest theta tile of the split kernels
 // Tile width for rows of nth columns, at most max_width: the multiple of 32
 // (at least 64 unless nth <= 32) that wastes the fewest lanes in the ragged
 // last tile, less a penalty of 0.02 per 32 columns below 128 for the extra
@@ -650,7 +783,7 @@ int tile_width_for(int nth, int max_width)
     }
     return best;
 }
-int split_tile_width(int nth) { return tile_width_for(nth, TEUK_SPLIT_TILE_MAX); }
+int split_tile_width(int nth) { return tile_width_for(nth, kSplitTileMax); }
 int split_theta_tiles(int nth)
 {
     const int tw = split_tile_width(nth);
@@ -673,12 +806,7 @@ int split_rows_per_block(int nth, int fixed_point)
 //    against 12.01 on 32768 x 512, same box and clock.
 //  - FP64: the single-argument 1024-thread bound keeps them at 64 registers;
 //    the two-argument form (1024, 1) made them 7% slower (10.07 -> 9.36).
-// TEUK_SPLIT_MINB, when defined, overrides the minimum for register-budget
-// experiments.
-#ifndef TEUK_SPLIT_MINB
-#define TEUK_SPLIT_MINB kFxTileMinBlocks
-#endif
-#define TEUK_SPLIT_BOUNDS_FX __launch_bounds__(kFxTileThreads, TEUK_SPLIT_MINB)
+#define TEUK_SPLIT_BOUNDS_FX __launch_bounds__(kFxTileThreads, kFxTileMinBlocks)
 #define TEUK_SPLIT_BOUNDS_FP64 __launch_bounds__(1024)
 
 template <bool REAL, bool FX>
@@ -723,7 +851,7 @@ __device__ __forceinline__ void predict_split_tile(const StepParams &p, const do
     allow_dependents();  // after the last store: the dependent sees only writes made before it
 }
 
-template <bool REAL, bool FX>
+template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ void correct_split_tile(const StepParams &p, const double2 *__restrict__ Phi,
                                                    const double2 *__restrict__ Pi, const double2 *__restrict__ PhiH,
                                                    const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
@@ -755,9 +883,38 @@ __device__ __forceinline__ void correct_split_tile(const StepParams &p, const do
     if (tx == TW - 1)
         row[TW + 1] = j0 + TW < nth ? add2(ldcg(PhiH + kr + j0 + TW), ldcg(PhiH + kr - nth + j0 + TW), ops)
                                     : make_double2(0.0, 0.0);
+    // dissipation: the row's old Phi and Pi over columns j0 - 3 .. j0 + TW + 2
+    // (entry c = column j0 - 3 + c), past the poles by the ghost rule; lanes
+    // past the last column hold ghost values too
+    const int KW = TW + 6;
+    double2 *uph = smem + blockDim.y * (TW + 2) + threadIdx.y * 2 * KW, *upi = uph + KW;
+    if (KO) {
+        const double2 *rp = Phi + kr, *rq = Pi + kr;
+        if (colok) {
+            uph[tx + 3] = phi;
+            upi[tx + 3] = pi;
+        } else {
+            uph[tx + 3] = ko_load(rp, j, nth, p.parity);
+            upi[tx + 3] = ko_load(rq, j, nth, p.parity);
+        }
+        if (tx < 3) {
+            uph[tx] = ko_load(rp, j0 - 3 + tx, nth, p.parity);
+            upi[tx] = ko_load(rq, j0 - 3 + tx, nth, p.parity);
+        }
+        if (tx >= TW - 3) {
+            uph[tx + 6] = ko_load(rp, j + 3, nth, p.parity);
+            upi[tx + 6] = ko_load(rq, j + 3, nth, p.parity);
+        }
+    }
     __syncthreads();
     double2 nphi, npi;
-    correct_c<REAL, FX>(c, p.half_dt, ops, phi, pi, hp, hm, row[tx + 2], row[tx], &nphi, &npi);
+    KoSums kphi{}, kpi{};
+    if (KO) {
+        kphi = ko_sums(uph, tx + 3, ops);
+        kpi = ko_sums(upi, tx + 3, ops);
+    }
+    correct_c<REAL, FX, KO>(c, p.half_dt, ops, phi, pi, hp, hm, row[tx + 2], row[tx], ko_of(p), kphi, kpi, &nphi,
+                            &npi);
     const long long n = ldcg(p.step_base) + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
@@ -774,17 +931,18 @@ __device__ __forceinline__ void correct_split_tile(const StepParams &p, const do
     allow_dependents();  // after the last store
 }
 
-// The split kernels, one instantiation per (REAL, FX) with its own launch
-// bounds (FX: TEUK_SPLIT_BOUNDS_FX, FP64: TEUK_SPLIT_BOUNDS_FP64).
+// The split kernels, one instantiation per (REAL, FX) -- and for the
+// corrector per dissipation flag -- with the launch bounds of their
+// arithmetic (FX: TEUK_SPLIT_BOUNDS_FX, FP64: TEUK_SPLIT_BOUNDS_FP64).
 template <bool REAL, bool FX>
 __global__ void lw_predict_split(StepParams p, const double2 *__restrict__ Phi, const double2 *__restrict__ Pi,
                                  double2 *__restrict__ PhiH, double2 *__restrict__ PiH, int k);
-template <bool REAL, bool FX>
+template <bool REAL, bool FX, bool KO>
 __global__ void lw_correct_split(StepParams p, const double2 *__restrict__ Phi, const double2 *__restrict__ Pi,
                                  const double2 *__restrict__ PhiH, const double2 *__restrict__ PiH,
                                  double2 *__restrict__ PhiO, double2 *__restrict__ PiO, int k);
 
-#define TEUK_SPLIT_KERNELS(REAL, FX, BOUNDS)                                                                  \
+#define TEUK_SPLIT_PREDICT(REAL, FX, BOUNDS)                                                                  \
     template <>                                                                                             \
     __global__ void BOUNDS lw_predict_split<REAL, FX>(StepParams p, const double2 *__restrict__ Phi,         \
                                                       const double2 *__restrict__ Pi,                        \
@@ -792,28 +950,41 @@ __global__ void lw_correct_split(StepParams p, const double2 *__restrict__ Phi, 
                                                       int k)                                                 \
     {                                                                                                       \
         predict_split_tile<REAL, FX>(p, Phi, Pi, PhiH, PiH, k);                                             \
-    }                                                                                                       \
+    }
+#define TEUK_SPLIT_CORRECT(REAL, FX, KO, BOUNDS)                                                              \
     template <>                                                                                             \
-    __global__ void BOUNDS lw_correct_split<REAL, FX>(                                                       \
+    __global__ void BOUNDS lw_correct_split<REAL, FX, KO>(                                                   \
         StepParams p, const double2 *__restrict__ Phi, const double2 *__restrict__ Pi,                        \
         const double2 *__restrict__ PhiH, const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,        \
         double2 *__restrict__ PiO, int k)                                                                    \
     {                                                                                                       \
-        correct_split_tile<REAL, FX>(p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);                                  \
+        correct_split_tile<REAL, FX, KO>(p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);                              \
     }
-TEUK_SPLIT_KERNELS(false, true, TEUK_SPLIT_BOUNDS_FX)
-TEUK_SPLIT_KERNELS(true, true, TEUK_SPLIT_BOUNDS_FX)
-TEUK_SPLIT_KERNELS(false, false, TEUK_SPLIT_BOUNDS_FP64)
-TEUK_SPLIT_KERNELS(true, false, TEUK_SPLIT_BOUNDS_FP64)
-#undef TEUK_SPLIT_KERNELS
+TEUK_SPLIT_PREDICT(false, true, TEUK_SPLIT_BOUNDS_FX)
+TEUK_SPLIT_PREDICT(true, true, TEUK_SPLIT_BOUNDS_FX)
+TEUK_SPLIT_PREDICT(false, false, TEUK_SPLIT_BOUNDS_FP64)
+TEUK_SPLIT_PREDICT(true, false, TEUK_SPLIT_BOUNDS_FP64)
+TEUK_SPLIT_CORRECT(false, true, false, TEUK_SPLIT_BOUNDS_FX)
+TEUK_SPLIT_CORRECT(true, true, false, TEUK_SPLIT_BOUNDS_FX)
+TEUK_SPLIT_CORRECT(false, false, false, TEUK_SPLIT_BOUNDS_FP64)
+TEUK_SPLIT_CORRECT(true, false, false, TEUK_SPLIT_BOUNDS_FP64)
+TEUK_SPLIT_CORRECT(false, true, true, TEUK_SPLIT_BOUNDS_FX)
+TEUK_SPLIT_CORRECT(true, true, true, TEUK_SPLIT_BOUNDS_FX)
+TEUK_SPLIT_CORRECT(false, false, true, TEUK_SPLIT_BOUNDS_FP64)
+TEUK_SPLIT_CORRECT(true, false, true, TEUK_SPLIT_BOUNDS_FP64)
+#undef TEUK_SPLIT_PREDICT
+#undef TEUK_SPLIT_CORRECT
 
-size_t split_smem_bytes(int nth, int rows)
+// Shared memory of a split CTA: R rows of TW + 2 sums; the corrector with
+// dissipation adds R rows of the old Phi and Pi, TW + 6 entries each.
+size_t split_smem_bytes(int nth, int rows, int ko)
 {
-    return sizeof(double2) * (size_t)(rows > 0 ? rows : split_rows_per_block(nth, 1)) * (split_tile_width(nth) + 2);
+    const size_t R = rows > 0 ? rows : split_rows_per_block(nth, 1), TW = split_tile_width(nth);
+    return sizeof(double2) * (R * (TW + 2) + (ko ? 2 * R * (TW + 6) : 0));
 }
-const void *split_kernel_ptr(int which, int real, int fixed_point)
+const void *split_kernel_ptr(int which, int real, int fixed_point, int ko)
 {
-    return which ? (const void *)TEUK_PICK(lw_correct_split, real, fixed_point)
+    return which ? (const void *)TEUK_PICK3(lw_correct_split, real, fixed_point, ko)
                  : (const void *)TEUK_PICK(lw_predict_split, real, fixed_point);
 }
 
@@ -833,7 +1004,7 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     cudaLaunchConfig_t cfg = {};
     const int TW = split_tile_width(p.nth), tiles = split_theta_tiles(p.nth);
     cfg.blockDim = dim3(TW, R);
-    cfg.dynamicSmemBytes = split_smem_bytes(p.nth, R);
+    cfg.dynamicSmemBytes = split_smem_bytes(p.nth, R, 0);
     cfg.stream = st;
     cfg.attrs = pdl ? attr : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;
@@ -846,7 +1017,8 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     }
     if (part != 0) {
         cfg.gridDim = dim3((p.nr - 2 + R - 1) / R, tiles);
-        e = cudaLaunchKernelEx(&cfg, TEUK_PICK(lw_correct_split, p.real_coef, p.fixed_point), p, Phi, Pi,
+        cfg.dynamicSmemBytes = split_smem_bytes(p.nth, R, p.ko);
+        e = cudaLaunchKernelEx(&cfg, TEUK_PICK3(lw_correct_split, p.real_coef, p.fixed_point, p.ko), p, Phi, Pi,
                                (const double2 *)PhiH, (const double2 *)PiH, PhiO, PiO, k);
         if (e != cudaSuccess) return e;
     }
@@ -939,6 +1111,8 @@ __device__ __forceinline__ BatchTile batch_tile(const JobDesc &J, const BatchCur
 // Row buffer words (double2) per buffer for a CTA of `block` threads: R rows
 // of tw + 2 with R tw <= block and R <= block / 32.
 __host__ __device__ __forceinline__ int batch_row_words(int block) { return block + 2 * (block / 32); }
+// Dissipation buffer words per buffer: R rows of the old Phi and Pi, tw + 6 each.
+__host__ __device__ __forceinline__ int batch_ko_words(int block) { return 2 * (block + 6 * (block / 32)); }
 
 __global__ void __launch_bounds__(kTileMaxThreads) lw_predict_batch(const JobDesc *__restrict__ jobs,
                                                                      const int *__restrict__ off, int njobs,
@@ -1033,6 +1207,9 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDes
         hm.phi = ldcg(J.phiH + kc - nth);
         hm.pi = ldcg(J.piH + kc - nth);
         const double2 phi = ldcg(Phi + kc), pi = ldcg(Pi + kc);
+        const bool ko = p.ko != 0;  // uniform over the CTA
+        const int KW = tw + 6;
+        double2 *uph = rowbuf + 2 * bw + (tile & 1) * batch_ko_words(blockDim.x) + t.tyc * 2 * KW, *upi = uph + KW;
         if (t.slot) {
             row[t.tx + 1] = t.colok ? add2(hp.phi, hm.phi, ops) : make_double2(0.0, 0.0);
             const size_t kr = (size_t)iq * nth;
@@ -1043,16 +1220,42 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDes
                 row[tw + 1] = t.j0 + tw < nth
                                   ? add2(ldcg(J.phiH + kr + t.j0 + tw), ldcg(J.phiH + kr - nth + t.j0 + tw), ops)
                                   : make_double2(0.0, 0.0);
+            if (ko) {  // the row's old Phi and Pi, columns j0 - 3 .. j0 + tw + 2 (as in the split corrector)
+                const double2 *rp = Phi + kr, *rq = Pi + kr;
+                uph[t.tx + 3] = t.j < nth ? phi : ko_load(rp, t.j, nth, p.parity);
+                upi[t.tx + 3] = t.j < nth ? pi : ko_load(rq, t.j, nth, p.parity);
+                if (t.tx < 3) {
+                    uph[t.tx] = ko_load(rp, t.j0 - 3 + t.tx, nth, p.parity);
+                    upi[t.tx] = ko_load(rq, t.j0 - 3 + t.tx, nth, p.parity);
+                }
+                if (t.tx >= tw - 3) {
+                    uph[t.tx + 6] = ko_load(rp, t.j + 3, nth, p.parity);
+                    upi[t.tx + 6] = ko_load(rq, t.j + 3, nth, p.parity);
+                }
+            }
         }
         __syncthreads();
         double2 nphi, npi;
         const double2 sup = row[t.tx + 2], sdn = row[t.tx];
-        if (real) {
-            if (p.fixed_point) correct_c<true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
-            else correct_c<true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
+        const KoCoef kw = ko_of(p);
+        if (ko) {
+            const KoSums kphi = ko_sums(uph, t.tx + 3, ops), kpi = ko_sums(upi, t.tx + 3, ops);
+            if (real) {
+                if (p.fixed_point) correct_c<true, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
+                else correct_c<true, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
+            } else {
+                if (p.fixed_point) correct_c<false, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
+                else correct_c<false, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
+            }
         } else {
-            if (p.fixed_point) correct_c<false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
-            else correct_c<false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, &nphi, &npi);
+            const KoSums z{};
+            if (real) {
+                if (p.fixed_point) correct_c<true, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
+                else correct_c<true, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
+            } else {
+                if (p.fixed_point) correct_c<false, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
+                else correct_c<false, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
+            }
         }
         const long long n = ldcg(p.step_base) + k;
         const SourceWindow &sw = p.src;
@@ -1074,9 +1277,25 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDes
 
 const void *batch_kernel_ptr(int which) { return which ? (const void *)lw_correct_batch : (const void *)lw_predict_batch; }
 
-size_t batch_smem_bytes(int block)
+// Descriptor, two sigma-row buffers and, when a job has the dissipation on,
+// two dissipation buffers (the persistent kernels alternate buffers by tile
+// so that a tile needs one barrier).
+size_t batch_smem_bytes(int block, int ko)
 {
-    return ((sizeof(JobDesc) + 15) / 16) * 16 + 2 * sizeof(double2) * (size_t)batch_row_words(block);
+    return ((sizeof(JobDesc) + 15) / 16) * 16 +
+           2 * sizeof(double2) * ((size_t)batch_row_words(block) + (ko ? (size_t)batch_ko_words(block) : 0));
+}
+
+// Let both persistent kernels take `smem` bytes of dynamic shared memory
+// (above the 48 KB default at 512-thread CTAs with the dissipation).
+cudaError_t batch_allow_smem(size_t smem)
+{
+    for (int w = 0; w < 2; ++w) {
+        const cudaError_t e = cudaFuncSetAttribute(batch_kernel_ptr(w), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const int *corr_off, int njobs,

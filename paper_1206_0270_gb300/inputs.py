@@ -14,26 +14,33 @@ import numpy as np
 
 # Workloads named by what they are.  Coordinates in units of the black-hole
 # mass M.  c_r / c_theta are the Courant factors of the time-step rule
-# dt = min(c_r h / max b, c_theta / omega_max).
+# dt = min(c_r h / max b, c_theta / omega_max) and eps the strength of the
+# angular Kreiss-Oliger dissipation; c_theta = 0.8 needs eps = 1 (the bare
+# scheme, eps = 0, needs c_theta = 0.1).
+STEP_RULE = dict(c_r=0.5, c_theta=0.8, eps=1.0)
+
 WORKLOADS = {
     # Schwarzschild, no source, Gaussian pulse (width 5M) with the lowest
     # spin-weighted angular profile, 2000 steps.
     "schwarzschild_s-2_m2_1024x64": dict(
         a=0.0, s=-2, m=2, nr=1024, nth=64, rstar_min=-100.0, rstar_max=300.0,
-        c_r=0.5, c_theta=0.1, steps=2000,
+        **STEP_RULE, steps=2000,
         pulse=dict(center=50.0, width=5.0), source=None,
         extraction=dict(rstar=100.0, every=10)),
     # Kerr a = 0.9M, circular equatorial orbit r0 = 10M, Gaussian source width
-    # 0.05M, zero initial data, 1e5 steps, waveform at r* = 500M every 10 steps.
+    # 0.05M, zero initial data, 1e5 steps (t = 1170M), waveform at r* = 500M
+    # every 10 steps.  The outer boundary at r* = 1000M stays out of causal
+    # contact with the observer for the whole run (a wave reflected there
+    # would reach r* = 500M only after t = 1490M).
     "kerr_a0.9_s-2_m2_8192x128_r0_10": dict(
-        a=0.9, s=-2, m=2, nr=8192, nth=128, rstar_min=-100.0, rstar_max=600.0,
-        c_r=0.5, c_theta=0.1, steps=100000,
+        a=0.9, s=-2, m=2, nr=8192, nth=128, rstar_min=-100.0, rstar_max=1000.0,
+        **STEP_RULE, steps=100000,
         pulse=None, source=dict(r0=10.0, sigma=0.05, amplitude=1.0, prograde=True),
         extraction=dict(rstar=500.0, every=10)),
     # Large single mode whose state (2 x 537 MB) is far larger than L2.
     "kerr_a0.9_s-2_m2_32768x512_r0_10": dict(
-        a=0.9, s=-2, m=2, nr=32768, nth=512, rstar_min=-100.0, rstar_max=600.0,
-        c_r=0.5, c_theta=0.1, steps=2000,
+        a=0.9, s=-2, m=2, nr=32768, nth=512, rstar_min=-100.0, rstar_max=1000.0,
+        **STEP_RULE, steps=2000,
         pulse=None, source=dict(r0=10.0, sigma=0.05, amplitude=1.0, prograde=True),
         extraction=dict(rstar=500.0, every=10)),
 }
@@ -44,7 +51,7 @@ WORKLOADS = {
 MODE_BATCH = dict(
     a=0.7, s=-2, r0=8.0, sigma=0.05, nr=4096, rstar_min=-100.0, rstar_max=600.0, steps=50000,
     modes=[(1, 32), (2, 32), (3, 64), (4, 64), (5, 128), (6, 128), (7, 256), (8, 256)],
-    extraction=dict(rstar=500.0, every=10), c_r=0.5, c_theta=0.1)
+    extraction=dict(rstar=500.0, every=10), **STEP_RULE)
 
 
 def rstar_grid(nr: int, rstar_min: float, rstar_max: float) -> np.ndarray:
@@ -133,19 +140,32 @@ def small_bank(n_jobs: int = 128, seed: int = 20120605):
 
 def serving_requests(n: int, rate: float, seed: int = 20120604, step_range=(1e3, 1e4),
                      grids=((2048, 64), (4096, 64), (4096, 128), (8192, 128), (16384, 256), (32768, 512)),
-                     grid_weights=(0.25, 0.25, 0.2, 0.2, 0.08, 0.02)):
+                     grid_weights=(0.25, 0.25, 0.2, 0.2, 0.08, 0.02), long_tail: int = 0,
+                     long_steps=(1e5, 1e6), long_grids=((8192, 128), (16384, 256), (32768, 512)),
+                     long_weights=(0.5, 0.3, 0.2)):
     """A Poisson stream of waveform requests: arrival gaps ~ Exp(rate), a ~
     U[0, 0.95], r0 ~ U[6, 20] M, m ~ U{1..4}, s = -2, grid drawn from `grids`
-    with `grid_weights`, steps ~ logU[step_range]."""
+    with `grid_weights`, steps ~ logU[step_range].  With long_tail = k, the
+    first k of the n requests (the earliest arrivals, so that they are on the
+    GPU while the short ones come in) are long jobs instead: steps ~
+    logU[long_steps], grid from `long_grids` with `long_weights`."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     w = np.asarray(grid_weights, float)
     w = w / w.sum()
-    for _ in range(n):
+    lw = np.asarray(long_weights, float)
+    lw = lw / lw.sum()
+    for k in range(n):
         t += rng.exponential(1.0 / rate)
-        nr, nth = grids[rng.choice(len(grids), p=w)]
+        long_job = k < long_tail
+        if long_job:
+            nr, nth = long_grids[rng.choice(len(long_grids), p=lw)]
+            lo, hi = long_steps
+        else:
+            nr, nth = grids[rng.choice(len(grids), p=w)]
+            lo, hi = step_range
         out.append(dict(arrival=t, a=float(rng.uniform(0.0, 0.95)), r0=float(rng.uniform(6.0, 20.0)),
                         m=int(rng.integers(1, 5)), s=-2, nr=int(nr), nth=int(nth),
-                        steps=int(round(10 ** rng.uniform(np.log10(step_range[0]), np.log10(step_range[1]))))))
+                        steps=int(round(10 ** rng.uniform(np.log10(lo), np.log10(hi)))), long=long_job))
     return out

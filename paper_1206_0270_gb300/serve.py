@@ -31,7 +31,10 @@ from . import teuk as T
 class Request:
     """One waveform job.  Grid r* in [rstar_min, rstar_max], nr x nth points;
     a circular equatorial orbit at r0 with Gaussian width sigma; waveform at
-    rstar_ext every `every` steps."""
+    rstar_ext every `every` steps.  The time step follows teuk_stable_dt with
+    c_r, c_theta (unless dt is given) and eps is the strength of the angular
+    dissipation (teuk_set_dissipation); c_theta = 0.8 needs eps = 1, the bare
+    scheme (eps = 0) c_theta = 0.1."""
     a: float
     s: int
     m: int
@@ -45,9 +48,11 @@ class Request:
     rstar_ext: float = 500.0
     every: int = 10
     c_r: float = 0.5
-    c_theta: float = 0.1
+    c_theta: float = 0.8
+    eps: float = 1.0
     dt: Optional[float] = None  # None: teuk_stable_dt with c_r, c_theta
     arrival: float = 0.0        # seconds (service clock) at which it may be admitted
+    keep_state: bool = False    # read the final Phi, Pi back into Result.state before retiring
 
 
 def footprint_bytes(req: Request, slice_steps: int) -> int:
@@ -68,6 +73,7 @@ class Result:
     submitted: float         # service-clock seconds
     admitted: float
     finished: float
+    state: Optional[tuple] = None  # (Phi, Pi) at the last step when the request asked for it
 
     @property
     def latency(self) -> float:
@@ -191,6 +197,7 @@ class WaveformService:
                 import torch
                 low_stream = torch.cuda.Stream()  # the job's own stream
             g = T.Solver(r.nr, r.nth, r.rstar_min, r.rstar_max, self._dt(r), r.a, r.s, r.m, stream=low_stream)
+            g.set_dissipation(r.eps)
             g.set_source(r0=r.r0, sigma=r.sigma)
             g.set_extraction(r.rstar_ext, r.every, capacity=self.slice // r.every + 2)
             self._used += need
@@ -232,12 +239,13 @@ class WaveformService:
         st = self._running.pop(rid)
         if st["job"] is not None:
             self.batch.remove(st["job"])
+        state = st["solver"].state() if self._requests[rid].keep_state else None
         st["solver"].close()
         self._used -= st["need"]
         r = self._requests[rid]
         t = np.concatenate(st["t"]) if st["t"] else np.zeros(0)
         phi = np.concatenate(st["phi"]) if st["phi"] else np.zeros((0, r.nth), complex)
-        self.results[rid] = Result(rid, r, t, phi, self._submitted[rid], st["admitted"], fin)
+        self.results[rid] = Result(rid, r, t, phi, self._submitted[rid], st["admitted"], fin, state)
 
     def _drain(self):
         """Stream every running job's new samples; retire finished jobs."""

@@ -61,6 +61,7 @@ _SIGS = {
     "teuk_set_source": (C.c_int, [_vp, C.POINTER(teuk_orbit)]),
     "teuk_set_extraction": (C.c_int, [_vp, C.c_double, C.c_int, C.c_long]),
     "teuk_step": (C.c_int, [_vp, C.c_long]),
+    "teuk_set_dissipation": (C.c_int, [_vp, C.c_double]),
     "teuk_set_stream": (C.c_int, [_vp, _vp]),
     "teuk_extract": (C.c_int, [_vp, _dp, _dp, C.c_long, C.POINTER(C.c_long)]),
     "teuk_get_state": (C.c_int, [_vp, _dp, _dp]),
@@ -256,6 +257,9 @@ class Solver:
 
     def set_option(self, option, value):
         _check(teuk_set_option(self.h, int(option), int(value)), self.h, "teuk_set_option")
+
+    def set_dissipation(self, eps):
+        _check(teuk_set_dissipation(self.h, float(eps)), self.h, "teuk_set_dissipation")
 
     def set_launch(self, rows_per_block):
         _check(teuk_set_launch(self.h, int(rows_per_block)), self.h, "teuk_set_launch")

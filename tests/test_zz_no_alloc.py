@@ -1,6 +1,7 @@
 """teuk_step_noalloc: one time step with the half step in the library's static
-device scratch, for callers that cannot allocate device memory while they step
-(for example while a stream is being captured into a CUDA graph).
+device scratch, for callers that cannot call cudaMalloc while they step (a
+real-time loop that must not block in the allocator, or a process whose device
+memory belongs to another framework's pool).
 
 Checked through the C ABI against the allocating entry point (teuk_step on a
 handle), on two calls in a row.  This file is collected last so that a run
@@ -87,4 +88,28 @@ def test_noalloc_rejects_grids_beyond_the_scratch(env):
     rc = T.teuk_step_noalloc(h.h, p(x), p(x), p(y), p(y), 0)
     assert rc == -1
     assert "static scratch" in T.teuk_last_error(h.h).decode()
+    h.close()
+
+
+def test_noalloc_rejects_overlapping_buffers(env):
+    # outputs that share bytes with an input (here shifted by one row) or with
+    # each other are refused before any device work
+    torch, T = env
+    nr, nth = 64, 32
+    h = T.Solver(nr, nth, -20.0, 40.0, 1e-3, 0.5, -2, 2)
+    x = torch.zeros((4 * nr, nth), dtype=torch.complex128, device="cuda")  # every range below lies inside
+    base = x.data_ptr()
+    row = nth * 16
+    p = lambda off: C.c_void_p(base + off)
+    span = nr * row
+    cases = [
+        (0, span, span + row, 2 * span + row),          # phi_out starts inside pi_in
+        (0, span, 2 * span, 2 * span + row),            # the two outputs overlap
+        (0, span, row, 2 * span + 2 * row),             # phi_out overlaps phi_in
+    ]
+    for a_in, b_in, a_out, b_out in cases:
+        rc = T.teuk_step_noalloc(h.h, p(a_in), p(b_in), p(a_out), p(b_out), 0)
+        assert rc == -1, (a_in, b_in, a_out, b_out)
+        assert "overlaps" in T.teuk_last_error(h.h).decode()
+    torch.cuda.synchronize()
     h.close()
