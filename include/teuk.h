@@ -385,6 +385,24 @@ int teuk_batch_destroy(teuk_batch *b);
 int teuk_fixed_dot(int on_device, int nterms, long count, const double *c, const double *x,
                    const unsigned *flip, double *out, int *ok);
 
+/* The angular Kreiss-Oliger dissipation of the corrector subtracts
+ * (eps/64) D6 u from each node, D6 u_j = 20 u_j - 15 (u_{j-1} + u_{j+1})
+ * + 6 (u_{j-2} + u_{j+2}) - (u_{j-3} + u_{j+3}) along theta (the sixth-order
+ * member of Kreiss & Oliger's family; the dissipation is this library's
+ * stabiliser of Eqs. (3)-(4), which the paper does not print).  With the
+ * fixed-point arithmetic the kernels form D6 of each real component as an
+ * exact integer sum: the seven values truncated to units of 2^(F-1079), F
+ * the largest biased exponent among them (each loses less than one unit; the
+ * largest keeps its 53 bits), rounded once to FP64 (error <= 2^-50 max|u_q|
+ * + 2^-53 |D6|); a non-finite value gives NaN.
+ *
+ * teuk_fixed_d6 evaluates that arithmetic for `count` windows of seven
+ * values, u[7 i + q] = u_{j-3+q}: out[i] = D6.  on_device = 0 runs the host
+ * build, 1 the device build (temporary device buffers; synchronous).  Host
+ * pointers owned by the caller.  TEUK_ERR_BAD_ARG for count < 0 or a NULL
+ * array, TEUK_ERR_OOM / TEUK_ERR_CUDA on device failures. */
+int teuk_fixed_d6(int on_device, long count, const double *u, double *out);
+
 /* Message of the last failed call on this handle ("" if none). */
 const char *teuk_last_error(const teuk_handle *h);
 

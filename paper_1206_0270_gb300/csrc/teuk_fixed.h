@@ -178,6 +178,111 @@ TEUK_FX_HD bool fx_dot(const Fx *c, const Fx *x, const uint32_t *flip, double *o
     return braw < 0x7FFu && (mag == 0 || (eb >= 200 && eb <= 2045));
 }
 
+// ---------------------------------------------------------------------------
+// The sixth difference of the angular dissipation,
+//   D6 = 20 u_3 - 15 (u_2 + u_4) + 6 (u_1 + u_5) - (u_0 + u_6),
+// of seven FP64 values, as an exact integer sum rounded once.
+//
+//   * each value is prepared once: v = +-m 2^4 (|v| < 2^57) and its exponent
+//     e = max(biased exponent, 1) (2047: not finite);
+//   * with F the largest e of the seven, every v is shifted right by F - e
+//     (floor), so each is truncated to units of 2^(F - 1079) by less than one
+//     unit and the largest keeps all 53 bits of its significand;
+//   * the weighted sum is exact in a signed 64-bit integer (|sum| < 64 2^57)
+//     and is rounded once to FP64, to nearest, ties to even.
+//
+// Error: |result - D6| <= 64 2^(F - 1079) + 2^-53 |D6| <= 2^-50 max|u_q|
+// + 2^-53 |D6|; scaled by the dissipation strength eps/64 this is at most
+// eps 2^-56 max|u_q| + 2^-53 |eps D6 / 64|, below one FP64 rounding of the
+// largest value of the window.  A non-finite input gives NaN.
+// ---------------------------------------------------------------------------
+
+// A value prepared for fx_d6.
+struct alignas(16) FxP {
+    long long v;  // +-m 2^4
+    int e;        // max(biased exponent, 1); 2047 if not finite
+};
+
+TEUK_FX_HD FxP fx_prep(double x)
+{
+    const uint64_t u = fx_bits(x);
+    const uint32_t hi = (uint32_t)(u >> 32);
+    const int eraw = (int)((hi >> 20) & 0x7FFu);
+    const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (eraw ? (1ull << 52) : 0ull);
+    const long long v = (long long)(m << 4);
+    FxP o;
+    o.v = (hi >> 31) ? -v : v;
+    o.e = eraw ? eraw : 1;
+    return o;
+}
+
+// floor(v / 2^s) for any s >= 0 (PTX shr.s64 clamps the count at 64)
+TEUK_FX_HD long long fx_sar(long long v, uint32_t s)
+{
+#ifdef __CUDA_ARCH__
+    long long r;
+    asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(s));
+    return r;
+#else
+    return v >> (s > 63u ? 63u : s);
+#endif
+}
+
+// RN(D 2^k) for |D| < 2^63 and D 2^k below the FP64 overflow threshold,
+// subnormal results included.
+TEUK_FX_HD double fx_ldexp_rn(long long D, int k)
+{
+    if (D == 0) return 0.0;
+    const uint64_t neg = D < 0 ? 1u : 0u;
+    const uint64_t mag = neg ? (uint64_t)0 - (uint64_t)D : (uint64_t)D;
+    const int lz = fx_clz64(mag);
+    const int eb = 63 - lz + k + 1023;  // biased exponent of the leading one
+    uint64_t r;
+    if (eb >= 1) {
+        const uint64_t nrm = mag << lz;  // leading one at bit 63
+        uint64_t m = nrm >> 11;
+        const uint64_t guard = (nrm >> 10) & 1u;
+        const uint64_t sticky = (nrm & 0x3FFu) != 0;
+        m += guard & (sticky | (m & 1u));
+        r = ((uint64_t)(eb - 1) << 52) + m;  // a significand rounded up to 2^53 carries into the exponent
+    } else {
+        // subnormal: units of 2^-1074; mag 2^k = mag 2^(k + 1074) units, k + 1074 < 52
+        const int sh = -(k + 1074);
+        if (sh <= 0) {
+            r = mag << (-sh);
+        } else if (sh >= 64) {
+            r = 0;  // mag < 2^63 <= half a unit
+        } else {
+            const uint64_t q = mag >> sh, rem = mag & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+            r = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+        }
+    }
+    return fx_double(r | (neg << 63));
+}
+
+// D6 of seven prepared values p[0..6] (p[3] the centre).
+TEUK_FX_HD double fx_d6(const FxP *p)
+{
+    int F = p[0].e;
+#pragma unroll
+    for (int q = 1; q < 7; ++q) F = p[q].e > F ? p[q].e : F;
+    if (F >= 2047) return fx_double(0x7FF8000000000000ull);
+    long long w[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) w[q] = fx_sar(p[q].v, (uint32_t)(F - p[q].e));
+    const long long D = 20 * w[3] - 15 * (w[2] + w[4]) + 6 * (w[1] + w[5]) - (w[0] + w[6]);
+    return fx_ldexp_rn(D, F - 1079);
+}
+
+// D6 of seven FP64 values u[0], u[stride], ..., u[6 stride].
+TEUK_FX_HD double fx_d6_values(const double *u, int stride)
+{
+    FxP p[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) p[q] = fx_prep(u[q * stride]);
+    return fx_d6(p);
+}
+
 
 
 }  // namespace teuk

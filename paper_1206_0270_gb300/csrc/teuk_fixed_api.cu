@@ -1,4 +1,5 @@
-// teuk_fixed_api.cu -- teuk_fixed_dot: the fixed-point sums of the Pi rows
+// teuk_fixed_api.cu -- teuk_fixed_dot and teuk_fixed_d6: the fixed-point sums
+// of the Pi rows and the exact sixth difference of the angular dissipation
 // (teuk_fixed.h) on the host or on the device, for verification.
 #include "teuk.h"
 #include "teuk_fixed.h"
@@ -44,7 +45,41 @@ __global__ void fixed_dot_kernel(int n, long count, const double *c, const doubl
     dot_any(n, c + i * n, x + i * n, flip + i * n, out + i, ok + i);
 }
 
+__global__ void fixed_d6_kernel(long count, const double *u, double *out)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    out[i] = fx_d6_values(u + i * 7, 1);
+}
+
 }  // namespace
+
+extern "C" int teuk_fixed_d6(int on_device, long count, const double *u, double *out)
+{
+    if (count < 0 || (count > 0 && (!u || !out))) return TEUK_ERR_BAD_ARG;
+    if (count == 0) return TEUK_OK;
+    if (!on_device) {
+        for (long i = 0; i < count; ++i) out[i] = fx_d6_values(u + i * 7, 1);
+        return TEUK_OK;
+    }
+    double *du = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&du, (size_t)count * 7 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, (size_t)count * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(du, u, (size_t)count * 7 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const int threads = 128;
+        fixed_d6_kernel<<<(unsigned)((count + threads - 1) / threads), threads>>>(count, du, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(du);
+    cudaFree(dout);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TEUK_ERR_OOM : TEUK_ERR_CUDA;
+    }
+    return TEUK_OK;
+}
 
 extern "C" int teuk_fixed_dot(int on_device, int nterms, long count, const double *c, const double *x,
                               const unsigned *flip, double *out, int *ok)

@@ -38,7 +38,11 @@
 // across the pole with the parity of the pole rule), for Phi and Pi alike:
 //   Phi^{n+1} = k0 Phi_i + k1 s1 + k2 s2 + k3 s3 - tb Phi^{i+1/2} + ...
 //   Pi^{n+1}  = k0 Pi_i  + k1 s1' + k2 s2' + k3 s3' + R1 tau' + ...
-// k0 = 1 - 20 eps/64, k1 = 15 eps/64, k2 = -6 eps/64, k3 = eps/64.
+// k0 = 1 - 20 eps/64, k1 = 15 eps/64, k2 = -6 eps/64, k3 = eps/64.  The
+// fixed-point kernels instead form D6 of each field exactly in integer
+// arithmetic (teuk_fixed.h, fx_d6), round it once, and add kd D6 with
+// kd = -eps/64: to Phi with one FP64 FMA, to Pi as one more term of its
+// fixed-point sum.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -93,7 +97,8 @@ struct StepParams {
     int fixed_point;       // 1: Pi rows as fixed-point sums (teuk_fixed.h); 0: FP64 FMA chains
     int ko;                // 1: angular Kreiss-Oliger dissipation on (coefficients k0..k3)
     int parity;            // ghost parity of the pole rule (+1 even |m|, -1 odd |m|)
-    double k0, k1, k2, k3; // 1 - 20 eps/64, 15 eps/64, -6 eps/64, eps/64
+    double k0, k1, k2, k3; // 1 - 20 eps/64, 15 eps/64, -6 eps/64, eps/64 (FP64 arithmetic)
+    double kd;             // -eps/64 (fixed-point arithmetic: weight of the exact D6)
     PredPlanes pred;
     CorrPlanes corr;
     SourceWindow src;

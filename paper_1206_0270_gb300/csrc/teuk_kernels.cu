@@ -341,9 +341,32 @@ struct KoSums {
     double2 s1, s2, s3;
 };
 struct KoCoef {
-    double k0, k1, k2, k3;
+    double k0, k1, k2, k3, kd;
 };
-__device__ __forceinline__ KoCoef ko_of(const StepParams &p) { return KoCoef{p.k0, p.k1, p.k2, p.k3}; }
+__device__ __forceinline__ KoCoef ko_of(const StepParams &p) { return KoCoef{p.k0, p.k1, p.k2, p.k3, p.kd}; }
+
+// What the corrector needs of the dissipation at one node: the FP64
+// kernels take the pair sums of the old Phi and Pi, the fixed-point kernels
+// the exact sixth differences D6 Phi and D6 Pi (teuk_fixed.h, fx_d6).
+struct KoIn {
+    KoSums sphi, spi;
+    double2 dphi, dpi;
+};
+
+// D6 of both components of entries c - 3 .. c + 3 of a row of complex
+// values (raw FP64 values, prepared here).
+__device__ __forceinline__ double2 ko_d6_raw(const double2 *u, int c)
+{
+    const double *b = (const double *)(u + c - 3);
+    return make_double2(fx_d6_values(b, 2), fx_d6_values(b + 1, 2));
+}
+
+// The same from rows of values prepared once each (fx_prep): re[] and im[]
+// hold the two components; identical results.
+__device__ __forceinline__ double2 ko_d6_prepared(const FxP *re, const FxP *im, int c)
+{
+    return make_double2(fx_d6(re + c - 3), fx_d6(im + c - 3));
+}
 
 // Theta index j of a row continued past the poles by the ghost rule: the
 // reflection across theta = 0 maps j < 0 to -1 - j, the one across theta = pi
@@ -377,19 +400,38 @@ __device__ __forceinline__ KoSums ko_sums(const double2 *u, int c, const Ops ops
     return KoSums{add2(u[c - 1], u[c + 1], ops), add2(u[c - 2], u[c + 2], ops), add2(u[c - 3], u[c + 3], ops)};
 }
 
+// The dissipation inputs of entry c of staged rows of the old Phi and Pi
+// (raw FP64 values, columns c - 3 .. c + 3 valid).
+template <bool FX>
+__device__ __forceinline__ KoIn ko_from_rows(const double2 *uph, const double2 *upi, int c, const Ops ops)
+{
+    KoIn ko{};
+    if (FX) {
+        ko.dphi = ko_d6_raw(uph, c);
+        ko.dpi = ko_d6_raw(upi, c);
+    } else {
+        ko.sphi = ko_sums(uph, c, ops);
+        ko.spi = ko_sums(upi, c, ops);
+    }
+    return ko;
+}
+
 // Corrector (Eq. 4) at one node.  hp: half step at i + 1/2, hm: at i - 1/2,
 // sup/sdn: sigma' = Phi^{i+1/2} + Phi^{i-1/2} at j+1, j-1.  As in the
 // predictor, the Pi row is a fixed-point sum with an FP64 fallback.  KO adds
 // the dissipation: Pi^n enters with weight k0 and kdpi = k1 s1 + k2 s2 + k3 s3
 // (formed in FP64 from the pair sums of Pi^n) with weight one.
-template <bool REAL, bool KO>
+// KO with FX: kdpi is D6 Pi and k0 the weight kd = -eps/64 of it; without
+// FX: kdpi = k1 s1 + k2 s2 + k3 s3 and k0 the weight of Pi.
+template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ double2 corr_pi_fp64(const CorrCoef &c, const Ops ops, double2 pi, double2 tau,
                                                 const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn,
                                                 double k0, double2 kdpi)
 {
     // R1 Pi^{+} + R2 Pi^{-} = R1 tau' + (R2 - R1) Pi^{-}, tau' = Pi^{+} + Pi^{-}, R2 - R1 = -2 tb (nt2)
     double2 npi = pi;
-    if (KO) npi = make_double2(fma_rn(k0, pi.x, kdpi.x), fma_rn(k0, pi.y, kdpi.y));
+    if (KO && FX) npi = make_double2(fma_rn(k0, kdpi.x, pi.x), fma_rn(k0, kdpi.y, pi.y));
+    if (KO && !FX) npi = make_double2(fma_rn(k0, pi.x, kdpi.x), fma_rn(k0, pi.y, kdpi.y));
     kfma<REAL>(npi, c.R1, tau);
     rfma(npi, c.nt2, hm.pi);
     kfma<REAL>(npi, c.R3, hp.phi);
@@ -404,9 +446,10 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
                                            const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn,
                                            double k0, double2 kdpi)
 {
-    if (!FX) return corr_pi_fp64<REAL, KO>(c, ops, pi, tau, hp, hm, sup, sdn, k0, kdpi);
+    if (!FX) return corr_pi_fp64<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, k0, kdpi);
     const Fx one = fx_unpack_coef(1.0);
-    const Fx c0 = KO ? fx_unpack_coef(k0) : one;
+    // with KO: Pi enters with weight one and D6 Pi (kdpi) with weight kd (k0)
+    const Fx c0 = one, cg = KO ? fx_unpack_coef(k0) : one;
     const Fx pr = fx_unpack(pi.x), pim = fx_unpack(pi.y), tr = fx_unpack(tau.x), ti = fx_unpack(tau.y);
     const Fx mr = fx_unpack(hm.pi.x), mi = fx_unpack(hm.pi.y);
     const Fx ar = fx_unpack(hp.phi.x), ai = fx_unpack(hp.phi.y), br = fx_unpack(hm.phi.x), bi = fx_unpack(hm.phi.y);
@@ -419,7 +462,7 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
     if (KO) {
         const Fx gr = fx_unpack(kdpi.x), gi = fx_unpack(kdpi.y);
         if (REAL) {
-            const Fx C[8] = {c0, R1r, nt2, R3r, R4r, KA, KC, one};
+            const Fx C[8] = {c0, R1r, nt2, R3r, R4r, KA, KC, cg};
             const Fx Xr[8] = {pr, tr, mr, ar, br, ur, dr, gr};
             const Fx Xi[8] = {pim, ti, mi, ai, bi, ui, di, gi};
             const uint32_t F[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -427,7 +470,7 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
             ok &= fx_dot<8>(C, Xi, F, &o.y);
         } else {
             const Fx R1i = fx_unpack_coef(c.R1.y), R3i = fx_unpack_coef(c.R3.y), R4i = fx_unpack_coef(c.R4.y);
-            const Fx C[11] = {c0, R1r, R1i, nt2, R3r, R3i, R4r, R4i, KA, KC, one};
+            const Fx C[11] = {c0, R1r, R1i, nt2, R3r, R3i, R4r, R4i, KA, KC, cg};
             const Fx Xr[11] = {pr, tr, ti, mr, ar, ai, br, bi, ur, dr, gr};
             const uint32_t Fr[11] = {0, 0, 1, 0, 0, 1, 0, 1, 0, 0, 0};
             const Fx Xi[11] = {pim, ti, tr, mi, ai, ar, bi, br, ui, di, gi};
@@ -452,7 +495,7 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
         ok = fx_dot<10>(C, Xr, Fr, &o.x);
         ok &= fx_dot<10>(C, Xi, Fi, &o.y);
     }
-    if (!ok) o = corr_pi_fp64<REAL, KO>(c, ops, pi, tau, hp, hm, sup, sdn, k0, kdpi);
+    if (!ok) o = corr_pi_fp64<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, k0, kdpi);
     return o;
 }
 
@@ -468,32 +511,36 @@ __device__ __forceinline__ double2 ko_combine(const KoCoef &kc, const KoSums &ks
 template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, const Ops ops, double2 phi,
                                           double2 pi, const HalfStep &hp, const HalfStep &hm, double2 sup,
-                                          double2 sdn, const KoCoef &kc, const KoSums &kphi, const KoSums &kpi,
-                                          double2 *phi_out, double2 *pi_out)
+                                          double2 sdn, const KoCoef &kc, const KoIn &ko, double2 *phi_out,
+                                          double2 *pi_out)
 {
     const double2 tau = add2(hp.pi, hm.pi, ops);
     double2 nphi = phi;
     double2 kdpi = make_double2(0.0, 0.0);
-    if (KO) {
-        const double2 kd = ko_combine(kc, kphi, ops);
+    double kw = kc.k0;
+    if (KO && FX) {
+        nphi = make_double2(fma_rn(kc.kd, ko.dphi.x, phi.x), fma_rn(kc.kd, ko.dphi.y, phi.y));
+        kdpi = ko.dpi;
+        kw = kc.kd;
+    } else if (KO) {
+        const double2 kd = ko_combine(kc, ko.sphi, ops);
         nphi = make_double2(fma_rn(kc.k0, phi.x, kd.x), fma_rn(kc.k0, phi.y, kd.y));
-        kdpi = ko_combine(kc, kpi, ops);
+        kdpi = ko_combine(kc, ko.spi, ops);
     }
     rfma(nphi, -c.tb, hp.phi);
     rfma(nphi, c.tb, hm.phi);
     rfma(nphi, half_dt, tau);
     *phi_out = nphi;
-    *pi_out = corr_pi<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, kc.k0, kdpi);
+    *pi_out = corr_pi<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, kw, kdpi);
 }
 
 template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ void correct(const StepParams &p, size_t k, double2 phi, double2 pi,
                                         const HalfStep &hp, const HalfStep &hm, double2 sup,
-                                        double2 sdn, const KoSums &kphi, const KoSums &kpi, double2 *phi_out,
-                                        double2 *pi_out)
+                                        double2 sdn, const KoIn &ko, double2 *phi_out, double2 *pi_out)
 {
-    correct_c<REAL, FX, KO>(load_corr<REAL>(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, ko_of(p), kphi,
-                            kpi, phi_out, pi_out);
+    correct_c<REAL, FX, KO>(load_corr<REAL>(p, k), p.half_dt, ops_of(p), phi, pi, hp, hm, sup, sdn, ko_of(p), ko,
+                            phi_out, pi_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -603,13 +650,10 @@ __global__ void __launch_bounds__(kFusedMaxNth) lw_step_fused(StepParams p, cons
         __syncthreads();
         const size_t kc = (size_t)i * nth + jj;
         double2 nphi, npi;
-        KoSums kphi{}, kpi{};
-        if (KO) {
-            kphi = ko_sums(uph, jj + 3, ops_of(p));
-            kpi = ko_sums(upi, jj + 3, ops_of(p));
-        }
-        correct_c<REAL, FX, KO>(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], ko_of(p), kphi, kpi,
-                                &nphi, &npi);
+        KoIn ko{};
+        if (KO) ko = ko_from_rows<FX>(uph, upi, jj + 3, ops_of(p));
+        correct_c<REAL, FX, KO>(cc, p.half_dt, ops_of(p), phc, pic, hp, hm, sh[jj + 2], sh[jj], ko_of(p), ko, &nphi,
+                                &npi);
         if (src_node && i >= sw.node_lo && i <= sw.node_hi)
             rfma(npi, ldg(sw.gC + (size_t)(i - sw.node_lo) * nth + jj), s_phase[1]);
         if (act) {
@@ -704,21 +748,17 @@ __global__ void lw_correct_kernel(StepParams p, const double2 *__restrict__ Phi,
     const double2 sup = add2(PhiH[kp - j + ju], PhiH[km - j + ju], ops_of(p));
     const double2 sdn = add2(PhiH[kp - j + jd], PhiH[km - j + jd], ops_of(p));
     double2 nphi, npi;
-    KoSums kphi{}, kpi{};
-    if (KO) {  // pair sums of the old state along the row, ghosts by the pole rule
+    KoIn ko{};
+    if (KO) {  // the old state along the row, columns j-3 .. j+3, ghosts by the pole rule
         const double2 *rp = Phi + (size_t)i * nth, *rq = Pi + (size_t)i * nth;
-        double2 a[6], b[6];
-        for (int q = 0; q < 3; ++q) {
-            a[q] = ko_load(rp, j - 1 - q, nth, p.parity);
-            a[q + 3] = ko_load(rp, j + 1 + q, nth, p.parity);
-            b[q] = ko_load(rq, j - 1 - q, nth, p.parity);
-            b[q + 3] = ko_load(rq, j + 1 + q, nth, p.parity);
+        double2 a[7], b[7];
+        for (int q = 0; q < 7; ++q) {
+            a[q] = ko_load(rp, j - 3 + q, nth, p.parity);
+            b[q] = ko_load(rq, j - 3 + q, nth, p.parity);
         }
-        const Ops ops = ops_of(p);
-        kphi = KoSums{add2(a[0], a[3], ops), add2(a[1], a[4], ops), add2(a[2], a[5], ops)};
-        kpi = KoSums{add2(b[0], b[3], ops), add2(b[1], b[4], ops), add2(b[2], b[5], ops)};
+        ko = ko_from_rows<FX>(a, b, 3, ops_of(p));
     }
-    correct<REAL, FX, KO>(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, kphi, kpi, &nphi, &npi);
+    correct<REAL, FX, KO>(p, kc, Phi[kc], Pi[kc], hp, hm, sup, sdn, ko, &nphi, &npi);
     const long long n = *p.step_base + k;
     const SourceWindow &sw = p.src;
     if (sw.active && i >= sw.node_lo && i <= sw.node_hi)
@@ -885,36 +925,43 @@ __device__ __forceinline__ void correct_split_tile(const StepParams &p, const do
                                     : make_double2(0.0, 0.0);
     // dissipation: the row's old Phi and Pi over columns j0 - 3 .. j0 + TW + 2
     // (entry c = column j0 - 3 + c), past the poles by the ghost rule; lanes
-    // past the last column hold ghost values too
+    // past the last column hold ghost values too.  FP64 kernels stage the
+    // values; fixed-point kernels stage each component prepared once for the
+    // exact sixth difference (fx_prep: Phi re, Phi im, Pi re, Pi im rows).
     const int KW = TW + 6;
     double2 *uph = smem + blockDim.y * (TW + 2) + threadIdx.y * 2 * KW, *upi = uph + KW;
+    FxP *kp = (FxP *)(smem + blockDim.y * (TW + 2)) + threadIdx.y * 4 * KW;
+    auto stage = [&](int e, double2 a, double2 b) {
+        if (FX) {
+            kp[e] = fx_prep(a.x);
+            kp[KW + e] = fx_prep(a.y);
+            kp[2 * KW + e] = fx_prep(b.x);
+            kp[3 * KW + e] = fx_prep(b.y);
+        } else {
+            uph[e] = a;
+            upi[e] = b;
+        }
+    };
     if (KO) {
         const double2 *rp = Phi + kr, *rq = Pi + kr;
-        if (colok) {
-            uph[tx + 3] = phi;
-            upi[tx + 3] = pi;
-        } else {
-            uph[tx + 3] = ko_load(rp, j, nth, p.parity);
-            upi[tx + 3] = ko_load(rq, j, nth, p.parity);
-        }
-        if (tx < 3) {
-            uph[tx] = ko_load(rp, j0 - 3 + tx, nth, p.parity);
-            upi[tx] = ko_load(rq, j0 - 3 + tx, nth, p.parity);
-        }
-        if (tx >= TW - 3) {
-            uph[tx + 6] = ko_load(rp, j + 3, nth, p.parity);
-            upi[tx + 6] = ko_load(rq, j + 3, nth, p.parity);
-        }
+        if (colok)
+            stage(tx + 3, phi, pi);
+        else
+            stage(tx + 3, ko_load(rp, j, nth, p.parity), ko_load(rq, j, nth, p.parity));
+        if (tx < 3) stage(tx, ko_load(rp, j0 - 3 + tx, nth, p.parity), ko_load(rq, j0 - 3 + tx, nth, p.parity));
+        if (tx >= TW - 3) stage(tx + 6, ko_load(rp, j + 3, nth, p.parity), ko_load(rq, j + 3, nth, p.parity));
     }
     __syncthreads();
     double2 nphi, npi;
-    KoSums kphi{}, kpi{};
-    if (KO) {
-        kphi = ko_sums(uph, tx + 3, ops);
-        kpi = ko_sums(upi, tx + 3, ops);
+    KoIn ko{};
+    if (KO && FX) {
+        ko.dphi = ko_d6_prepared(kp, kp + KW, tx + 3);
+        ko.dpi = ko_d6_prepared(kp + 2 * KW, kp + 3 * KW, tx + 3);
+    } else if (KO) {
+        ko.sphi = ko_sums(uph, tx + 3, ops);
+        ko.spi = ko_sums(upi, tx + 3, ops);
     }
-    correct_c<REAL, FX, KO>(c, p.half_dt, ops, phi, pi, hp, hm, row[tx + 2], row[tx], ko_of(p), kphi, kpi, &nphi,
-                            &npi);
+    correct_c<REAL, FX, KO>(c, p.half_dt, ops, phi, pi, hp, hm, row[tx + 2], row[tx], ko_of(p), ko, &nphi, &npi);
     const long long n = ldcg(p.step_base) + k;
     const SourceWindow &sw = p.src;
     if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
@@ -976,11 +1023,13 @@ TEUK_SPLIT_CORRECT(true, false, true, TEUK_SPLIT_BOUNDS_FP64)
 #undef TEUK_SPLIT_CORRECT
 
 // Shared memory of a split CTA: R rows of TW + 2 sums; the corrector with
-// dissipation adds R rows of the old Phi and Pi, TW + 6 entries each.
+// dissipation adds R rows of the old Phi and Pi, TW + 6 entries each (as four
+// rows of prepared components, 16 bytes each, in the fixed-point kernels).
 size_t split_smem_bytes(int nth, int rows, int ko)
 {
     const size_t R = rows > 0 ? rows : split_rows_per_block(nth, 1), TW = split_tile_width(nth);
-    return sizeof(double2) * (R * (TW + 2) + (ko ? 2 * R * (TW + 6) : 0));
+    static_assert(sizeof(FxP) == sizeof(double2), "prepared components take 16 bytes");
+    return sizeof(double2) * (R * (TW + 2) + (ko ? 4 * R * (TW + 6) : 0));
 }
 const void *split_kernel_ptr(int which, int real, int fixed_point, int ko)
 {
@@ -1239,22 +1288,21 @@ __global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDes
         const double2 sup = row[t.tx + 2], sdn = row[t.tx];
         const KoCoef kw = ko_of(p);
         if (ko) {
-            const KoSums kphi = ko_sums(uph, t.tx + 3, ops), kpi = ko_sums(upi, t.tx + 3, ops);
             if (real) {
-                if (p.fixed_point) correct_c<true, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
-                else correct_c<true, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
+                if (p.fixed_point) correct_c<true, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<true>(uph, upi, t.tx + 3, ops), &nphi, &npi);
+                else correct_c<true, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<false>(uph, upi, t.tx + 3, ops), &nphi, &npi);
             } else {
-                if (p.fixed_point) correct_c<false, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
-                else correct_c<false, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, kphi, kpi, &nphi, &npi);
+                if (p.fixed_point) correct_c<false, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<true>(uph, upi, t.tx + 3, ops), &nphi, &npi);
+                else correct_c<false, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<false>(uph, upi, t.tx + 3, ops), &nphi, &npi);
             }
         } else {
-            const KoSums z{};
+            const KoIn z{};
             if (real) {
-                if (p.fixed_point) correct_c<true, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
-                else correct_c<true, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
+                if (p.fixed_point) correct_c<true, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
+                else correct_c<true, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
             } else {
-                if (p.fixed_point) correct_c<false, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
-                else correct_c<false, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, z, &nphi, &npi);
+                if (p.fixed_point) correct_c<false, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
+                else correct_c<false, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
             }
         }
         const long long n = ldcg(p.step_base) + k;

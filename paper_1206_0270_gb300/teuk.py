@@ -77,6 +77,7 @@ _SIGS = {
     "teuk_time_kernels": (C.c_int, [_vp, C.c_long, _dp]),
     "teuk_fixed_dot": (C.c_int, [C.c_int, C.c_int, C.c_long, _dp, _dp, C.POINTER(C.c_uint), _dp,
                                  C.POINTER(C.c_int)]),
+    "teuk_fixed_d6": (C.c_int, [C.c_int, C.c_long, _dp, _dp]),
     "teuk_batch_create": (C.c_int, [_vp, C.POINTER(_vp)]),
     "teuk_batch_add": (C.c_int, [_vp, _vp, C.c_long, C.POINTER(C.c_int)]),
     "teuk_batch_remove": (C.c_int, [_vp, C.c_int]),
@@ -144,6 +145,19 @@ def fixed_dot(c, x, flip=None, device=False):
                         ok.ctypes.data_as(C.POINTER(C.c_int)))
     _check(rc, None, "teuk_fixed_dot")
     return out, ok.astype(bool)
+
+
+def fixed_d6(u, device=False):
+    """Exact sixth differences of the angular dissipation (teuk_fixed_d6):
+    u of shape (count, 7) float64, u[i, q] = u_{j-3+q}.  Returns out float64
+    (count,); device=True runs the device build of the arithmetic."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    if u.ndim != 2 or u.shape[1] != 7:
+        raise ValueError("u must have shape (count, 7)")
+    out = np.zeros(u.shape[0])
+    rc = teuk_fixed_d6(1 if device else 0, u.shape[0], u.ctypes.data_as(_dp), out.ctypes.data_as(_dp))
+    _check(rc, None, "teuk_fixed_d6")
+    return out
 
 
 def stable_dt(nr, nth, rstar_min, rstar_max, a, s, m, c_r=0.5, c_theta=0.1):

@@ -164,3 +164,95 @@ def test_device_build_equals_host_build():
             od, kd = T.fixed_dot(c, x, flip, device=True)
             assert np.array_equal(kh, kd)
             assert np.array_equal(oh[kh].view(np.uint64), od[kd].view(np.uint64))
+
+
+# ---------------------------------------------------------------------------
+# The exact sixth difference of the angular dissipation (teuk_fixed_d6)
+# ---------------------------------------------------------------------------
+
+D6_WEIGHTS = (-1, 6, -15, 20, -15, 6, -1)
+
+
+def d6_model(u):
+    """The arithmetic stated in include/teuk.h, written out with Python
+    integers: prepare, align to the largest exponent (floor), weighted exact
+    sum, one rounding to nearest (CPython's int/int division is correctly
+    rounded, subnormals included)."""
+    prep = []
+    for x in u:
+        bits = int(np.float64(x).view(np.uint64))
+        eraw = (bits >> 52) & 0x7FF
+        m = (bits & ((1 << 52) - 1)) | ((1 << 52) if eraw else 0)
+        v = m << 4
+        prep.append((-v if bits >> 63 else v, max(eraw, 1) if eraw != 0x7FF else 2047))
+    F = max(e for _, e in prep)
+    if F >= 2047:
+        return float("nan")
+    D = sum(wt * (v >> (F - e)) for wt, (v, e) in zip(D6_WEIGHTS, prep))
+    k = F - 1079
+    return D * 2.0 ** k if D == 0 else (Fraction(D) * Fraction(2) ** k).__float__()
+
+
+def d6_exact(u):
+    return sum(wt * Fraction(float(x)) for wt, x in zip(D6_WEIGHTS, u))
+
+
+def d6_cases(rng, count):
+    j = np.arange(7)
+    smooth = np.sin(0.3 * (rng.integers(0, 100, (count, 1)) + j)) * 10.0 ** rng.integers(-8, 8, (count, 1))
+    noisy = rng.standard_normal((count, 7)) * 10.0 ** rng.integers(-5, 5, (count, 7))
+    wide = rng.standard_normal((count, 7)) * 10.0 ** rng.integers(-300, 300, (count, 7))
+    zeros = rng.standard_normal((count, 7))
+    zeros[rng.random((count, 7)) < 0.5] = 0.0
+    return np.concatenate([smooth, noisy, wide, zeros])
+
+
+def test_d6_equals_its_stated_arithmetic_bit_for_bit():
+    u = d6_cases(np.random.default_rng(61), 300)
+    out = T.fixed_d6(u)
+    ref = np.array([d6_model(r) for r in u])
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+
+
+def test_d6_error_bound_against_exact_arithmetic():
+    u = d6_cases(np.random.default_rng(62), 300)
+    out = T.fixed_d6(u)
+    for r, o in zip(u, out):
+        ex = d6_exact(r)
+        mx = max(abs(Fraction(float(x))) for x in r)
+        bound = Fraction(2) ** -50 * mx + Fraction(2) ** -53 * abs(ex) + Fraction(2) ** -1075
+        assert abs(Fraction(float(o)) - ex) <= bound, (r, o, float(ex))
+
+
+def test_d6_annihilates_low_degree_polynomials_and_scales_exactly():
+    # D6 of samples of a polynomial of degree < 6 is exactly zero; of q^6 it is
+    # -6! (D6 = -delta^6); integer samples are exact, so no truncation occurs
+    q = np.arange(-3, 4, dtype=np.float64)
+    rng = np.random.default_rng(63)
+    polys = [np.polyval(rng.integers(-50, 50, deg + 1).astype(np.float64), q) for deg in range(6)]
+    out = T.fixed_d6(np.array(polys + [q ** 6, np.full(7, 3.25), q ** 6 + 7 * q ** 3]))
+    assert np.all(out[:6] == 0.0) and out[6] == -720.0 and out[7] == 0.0 and out[8] == -720.0
+    # a power-of-two scale passes through exactly (normal range)
+    u = d6_cases(np.random.default_rng(64), 200)[:400]
+    u = u[np.all(np.abs(u) < 1e200, axis=1) & np.all((np.abs(u) > 1e-200) | (u == 0), axis=1)]
+    assert np.array_equal(T.fixed_d6(4.0 * u), 4.0 * T.fixed_d6(u))
+
+
+def test_d6_subnormals_and_non_finite():
+    tiny = np.array([[5e-324, 0.0, 1e-310, -2e-310, 3e-321, 0.0, 7e-300],
+                     [1e-320, 2e-320, 3e-320, 4e-320, 3e-320, 2e-320, 1e-320]])
+    out = T.fixed_d6(tiny)
+    ref = np.array([d6_model(r) for r in tiny])
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+    assert out[1] == float(d6_exact(tiny[1]))          # exact: all values share one exponent
+    bad = np.array([[1.0, 2.0, np.inf, 0.0, 0.0, 0.0, 0.0], [np.nan] + [1.0] * 6])
+    assert np.isnan(T.fixed_d6(bad)).all()
+    with pytest.raises(ValueError):
+        T.fixed_d6(np.ones((3, 6)))
+
+
+@pytest.mark.gpu
+def test_d6_device_build_equals_host_build():
+    u = d6_cases(np.random.default_rng(65), 20000)
+    oh, od = T.fixed_d6(u, device=False), T.fixed_d6(u, device=True)
+    assert np.array_equal(oh.view(np.uint64), od.view(np.uint64))
