@@ -47,7 +47,8 @@ UNIT = "grid-pt updates/s"
 # adds to the corrector, per real component of Phi and Pi, 3 pair sums and the
 # weighted sum k1 s1 + k2 s2 + k3 s3 (1 multiply + 2 FMAs), and applies it with
 # the central weight (1 FMA for Phi, 1 multiply for Pi): 10 + 9 flops per
-# complex component pair, 38 per node.
+# complex component pair, 38 per node (algorithmic: the fixed-point kernels
+# form these sums as exact integer sums instead).
 FLOPS_PER_UPDATE = 100
 FLOPS_PREDICTOR_POINT = 48
 FLOPS_CORRECTOR_POINT = 52
@@ -59,20 +60,21 @@ FP64_PEAK_FLOPS = 1.25e12
 # How the kernels execute that work: the Phi rows and the sums tau, sigma on
 # the FP64 pipe (20 instructions per update, adds and multiplies issued as
 # FMAs), the Pi rows as fixed-point sums of 38 exact integer products per
-# update on the integer pipes; the dissipation adds 26 FP64 instructions and
-# 2 products.  Measured FP64 issue rate on GB300 (FMA-chain probe): 1.906 per
-# clock per SM.
+# update on the integer pipes.  The dissipation adds 2 FP64 instructions (its
+# term in the Phi row), 2 products (its term in the Pi rows) and four exact
+# integer sixth differences per node.  Measured FP64 issue rate on GB300
+# (FMA-chain probe): 1.906 per clock per SM.
 FP64_INSTR_PER_UPDATE = 20
 FIXED_POINT_PRODUCTS_PER_UPDATE = 38
-FP64_INSTR_DISSIPATION = 26
+FP64_INSTR_DISSIPATION = 2
 FIXED_POINT_PRODUCTS_DISSIPATION = 2
 FP64_FMA_PER_CLK_SM = 1.906
 NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # of the split kernels on 8192 x 128, valid for the kernel and launch sources
 # whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(predictor=125.87e6 + 15.97e6, corrector=151.01e6 + 16.74e6,
-                   sources_sha256="0e90dd64ec9b435947cc1f85a10f9ace89c5a6ef1d14570db7fd9f8c82fe9dee")
+NCU_TRAFFIC = dict(predictor=125.87e6 + 16.53e6, corrector=151.02e6 + 20.32e6,
+                   sources_sha256="9eb8f74b42576d030e6c5ca32ae2089bd46468501bb7f0e1c1cdd4d9d4bb3069")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits
@@ -476,6 +478,7 @@ def run_hbm_probe(T, stream, ws, hbm_peak, hbm_src, same_src, chunk=64, reps=6):
     try:
         P.set_initial(np.zeros((nr, nth), complex), np.zeros((nr, nth), complex))
         P.set_source(**w["source"])
+        P.set_dissipation(w["eps"])
         ex = w["extraction"]
         P.set_extraction(ex["rstar"], ex["every"], capacity=chunk * (reps + 3) // ex["every"] + 16)
         for _ in range(2):
