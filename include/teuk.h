@@ -219,7 +219,8 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  *     (default 64). */
 #define TEUK_OPT_PDL 1
 #define TEUK_OPT_GRAPH_CHUNK 2
-#define TEUK_OPT_BLOCK_THREADS 3  /* batches only: CTA threads, a multiple of 32 <= 512; 0 = automatic (128) */
+#define TEUK_OPT_BLOCK_THREADS 3  /* batches only (mode 0): CTA threads, a multiple of 32 <= 512, at most 128
+                                    for fixed-point jobs; 0 = automatic (128 fixed point, 256 FP64) */
 /* TEUK_OPT_REAL_PATH: 1 (default) stores real coefficient planes and uses
  * real-by-complex products when every coefficient is real (a = 0, or
  * s = m = 0: 6 and 7 instead of 9 and 10 products per Pi row); 0 keeps the
@@ -235,8 +236,9 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
 #define TEUK_OPT_SPLIT_ROWS 5
 /* TEUK_OPT_BATCH_MODE (batches only): 1 (default) advances every job with its
  * own kernels on its own stream (graph replay per chunk), the jobs running
- * concurrently; 0 advances all jobs with one persistent predictor and one
- * corrector launch per step that work through a tile list of every job.
+ * concurrently; 0 advances the jobs with one predictor and one corrector
+ * launch per time step for each group of up to 64 jobs that share an
+ * arithmetic, each launch covering the tiles of all jobs of its group.
  * Both give the same numbers as stepping each handle alone. */
 #define TEUK_OPT_BATCH_MODE 6
 /* TEUK_OPT_FIXED_POINT: 1 (default) evaluates the Pi rows of Eqs. (3)-(4) as
@@ -245,6 +247,10 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  * product with FP64 fused multiply-adds.  The two differ only by rounding
  * (both agree with the oracle to about 1e-14 per step). */
 #define TEUK_OPT_FIXED_POINT 7
+/* TEUK_OPT_BATCH_CTAS (batches only, mode 0): 0 (default) launches one CTA
+ * per tile; k = 1..64 launches a persistent grid of k CTAs per SM (at most as
+ * many as stay resident), each CTA looping over the tiles. */
+#define TEUK_OPT_BATCH_CTAS 8
 int teuk_set_option(teuk_handle *h, int option, long value);
 
 /* Current fused-kernel launch shape. */
@@ -303,12 +309,14 @@ int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in,
  * each handle alone.  Two modes (TEUK_OPT_BATCH_MODE):
  *   1 (default): every job advances with its own kernels on its own stream
  *     (graph replay per chunk), all jobs concurrently and independently;
- *   0: one persistent predictor and one persistent corrector launch per time
- *     step work through the theta tiles of every job; jobs advance in slices
- *     of min(graph chunk, smallest remaining step count) steps, a job that
- *     has taken its steps leaves at the next slice boundary, and full slices
+ *   0: per time step, one predictor and one corrector launch for each group
+ *     of up to 64 jobs that share an arithmetic cover the theta tiles of all
+ *     of them (one CTA per tile, or a persistent grid of resident CTAs that
+ *     loop over the tiles: TEUK_OPT_BATCH_CTAS); jobs advance in slices of
+ *     min(graph chunk, smallest remaining step count) steps, a job that has
+ *     taken its steps leaves at the next slice boundary, and full slices
  *     replay a CUDA graph captured for the current set of jobs.
- * teuk_batch_autotune picks the mode (and the persistent launch's CTA size).
+ * teuk_batch_autotune picks the launch form.
  *
  * Rules: a handle in a batch is driven by the batch only -- teuk_step, the
  * other teuk_set_* calls (teuk_set_stream excepted), teuk_step_noalloc and
@@ -342,17 +350,17 @@ int teuk_batch_remaining(const teuk_batch *b, int job_id, long *remaining);
 /* Wait for the batch's queued work. */
 int teuk_batch_sync(teuk_batch *b);
 
-/* TEUK_OPT_PDL, TEUK_OPT_GRAPH_CHUNK, TEUK_OPT_BLOCK_THREADS (persistent
- * launch) or TEUK_OPT_BATCH_MODE. */
+/* TEUK_OPT_PDL, TEUK_OPT_GRAPH_CHUNK, TEUK_OPT_BLOCK_THREADS,
+ * TEUK_OPT_BATCH_CTAS (mode 0) or TEUK_OPT_BATCH_MODE. */
 int teuk_batch_set_option(teuk_batch *b, int option, long value);
 
-/* Time the persistent launch at each candidate CTA size (64, 128, 256
- * threads; a job's rows are cut into theta tiles of at most the CTA width)
- * and the per-job launches on the batch's own jobs -- the timed steps count
- * as progress -- and keep the fastest; *best_block receives its CTA size, or
- * 0 when per-job launches won (TEUK_OPT_BATCH_MODE is set accordingly).
+/* Time the launch forms on the batch's own jobs -- per-job launches, the
+ * multi-job launches with one CTA per tile, and the persistent multi-job
+ * launches -- and keep the fastest (TEUK_OPT_BATCH_MODE and
+ * TEUK_OPT_BATCH_CTAS are set accordingly); the timed steps count as
+ * progress.  *best (may be NULL) receives 0, 1 or 2 for those three forms.
  * Synchronises. */
-int teuk_batch_autotune(teuk_batch *b, int *best_block);
+int teuk_batch_autotune(teuk_batch *b, int *best);
 
 /* Kernel launches that teuk_batch_step(b, n) issues when no job finishes. */
 long teuk_batch_launches_for(const teuk_batch *b, long n);

@@ -1,15 +1,19 @@
 // teuk_batch.cu -- batched stepping of many independent solver handles.
 //
 // A template bank is thousands of independent (a, r0, m) evolutions of
-// uneven grid size and length.  A batch advances all of its active jobs by
-// one time step with a single predictor launch and a single corrector launch
-// (lw_predict_batch / lw_correct_batch): CTA b finds its job by a binary
-// search over the jobs' tile offsets and works on one tile of that job.  Jobs
-// advance in slices; a slice is min(chunk, smallest remaining step count)
-// steps, so a job that reaches its step count leaves at a slice boundary.
-// Full slices replay a CUDA graph captured for the current set of jobs.  The
-// CTA size is chosen by timing the candidates on the jobs themselves
-// (teuk_batch_autotune), so tuning advances the jobs instead of wasting work.
+// uneven grid size and length.  Two ways to advance a batch:
+//   mode 1: every job with its own split kernels on its own stream (graph
+//     replay per chunk), the jobs running concurrently;
+//   mode 0: every time step is one predictor and one corrector launch per
+//     group of up to kMultiMaxJobs jobs that share an arithmetic
+//     (lw_predict_multi / lw_correct_multi over the tiles of all of them),
+//     with one CTA per tile or a persistent grid of resident CTAs.  Jobs
+//     advance in slices of min(chunk, smallest remaining step count) steps,
+//     so a job that reaches its step count leaves at a slice boundary; full
+//     slices replay a CUDA graph captured for the current set of jobs.
+// Both run the split kernels' tile code, so every job gets the bits it gets
+// alone.  teuk_batch_autotune times the launch forms on the jobs themselves
+// (the timed steps count as progress).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -34,17 +38,22 @@ struct teuk_batch {
     };
     std::vector<Job> jobs;
 
-    // device tables of the active set (rebuilt when it changes)
+    // the active set (rebuilt when it changes): the jobs' descriptors on the
+    // device (for the step-counter update) and the multi-job launch groups
     JobDesc *d_jobs = nullptr;
-    int *d_off = nullptr;  // pred offsets [cap_jobs + 1], then corr offsets [cap_jobs + 1]
     int cap_jobs = 0;
     std::vector<int> active;  // job ids in table order
     std::vector<JobDesc> host_desc;
-    int pred_tiles = 0, corr_tiles = 0;
-    size_t smem = 0;
-    int block = 0;          // CTA threads in use
-    int ctas = 0;           // persistent CTAs per launch (resident on all SMs)
-    int block_request = 0;  // 0 = automatic
+    struct Group {
+        int real = 0, fx = 0, ko = 0, block = 0;
+        size_t smem = 0;
+        int ctas = 0;               // CTAs per launch: 0 = one per tile
+        std::vector<int> members;   // indices into active
+        MultiArgs pred, corr;       // predictor tiles (nr - 1 rows), corrector tiles (nr - 2 rows)
+    };
+    std::vector<Group> groups;
+    int block_request = 0;  // 0 = automatic (128 threads for fixed-point jobs, 256 for FP64 ones)
+    int ctas_request = 0;   // 0 = one CTA per tile; k > 0 = persistent, k CTAs per SM (at most what fits)
     bool layout_dirty = true;
     cudaGraphExec_t graph = nullptr;
     int pdl = 1, chunk = 64;
@@ -108,7 +117,6 @@ extern "C" int teuk_batch_destroy(teuk_batch *b)
         if (j.done) cudaEventDestroy(j.done);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_jobs) cudaFree(b->d_jobs);
-    if (b->d_off) cudaFree(b->d_off);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -170,17 +178,21 @@ extern "C" int teuk_batch_sync(teuk_batch *b)
     return TEUK_OK;
 }
 
-// CTA size: 128 threads unless requested otherwise.  A job's rows are cut
-// into theta tiles of at most the CTA width, so any CTA size fits any job.
-static int pick_block(const teuk_batch *b)
+// CTA threads of a job's multi-job launch: the requested size (fixed-point
+// jobs at most kFxTileThreads, the bound their kernels are compiled for) or
+// the split kernels' default, 128 for fixed-point and 256 for FP64 jobs.
+static int job_block(const teuk_batch *b, const teuk_handle *h)
 {
-    return b->block_request ? b->block_request : 128;
+    const int fx = h->sp.fixed_point;
+    const int want = b->block_request ? b->block_request : (fx ? kFxTileThreads : 2 * kFxTileThreads);
+    return fx ? std::min(want, kFxTileThreads) : want;
 }
 
-// Rebuild the job table and tile offsets for the jobs with steps left.
+// Rebuild the job table and the launch groups for the jobs with steps left.
 static int rebuild(teuk_batch *b)
 {
     b->active.clear();
+    b->groups.clear();
     for (int id = 0; id < (int)b->jobs.size(); ++id)
         if (b->jobs[id].member && b->jobs[id].remaining > 0) b->active.push_back(id);
     drop_graph(b);
@@ -189,14 +201,11 @@ static int rebuild(teuk_batch *b)
         b->layout_dirty = false;
         return TEUK_OK;
     }
-    b->block = pick_block(b);
     if (nj > b->cap_jobs) {
         BCU(cudaStreamSynchronize(b->stream));  // queued slices still read the old table
         if (b->d_jobs) { cudaFree(b->d_jobs); b->d_jobs = nullptr; }
-        if (b->d_off) { cudaFree(b->d_off); b->d_off = nullptr; }
         const int cap = std::max(nj, 2 * b->cap_jobs);
-        if (cudaMalloc(&b->d_jobs, (size_t)cap * sizeof(JobDesc)) != cudaSuccess ||
-            cudaMalloc(&b->d_off, 2 * (size_t)(cap + 1) * sizeof(int)) != cudaSuccess) {
+        if (cudaMalloc(&b->d_jobs, (size_t)cap * sizeof(JobDesc)) != cudaSuccess) {
             cudaGetLastError();
             b->cap_jobs = 0;
             return bfail(b, TEUK_ERR_OOM, "batch: out of device memory for the job table");
@@ -204,51 +213,75 @@ static int rebuild(teuk_batch *b)
         b->cap_jobs = cap;
     }
     b->host_desc.assign(nj, JobDesc{});
-    std::vector<int> off(2 * (size_t)(b->cap_jobs + 1), 0);
-    int *poff = off.data(), *coff = off.data() + (b->cap_jobs + 1);
-    size_t smem = 0;
-    int ko_any = 0;
+    int sms = 0;
+    BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     for (int q = 0; q < nj; ++q) {
         teuk_handle *h = b->jobs[b->active[q]].h;
         JobDesc &d = b->host_desc[q];
         d.p = h->sp;
-        ko_any |= h->sp.ko;
         d.phi[0] = h->phi[0]; d.phi[1] = h->phi[1];
         d.pi[0] = h->pi[0]; d.pi[1] = h->pi[1];
         d.phiH = h->phiH; d.piH = h->piH;
         d.cur = h->cur;
-        d.tw = tile_width_for(h->nth, b->block);
-        d.rows = std::max(1, b->block / d.tw);
+        const int block = job_block(b, h);
+        d.tw = multi_tile_width(h->nth, block);
+        d.rows = block / d.tw;
         d.tiles = (h->nth + d.tw - 1) / d.tw;
-        const int pt = (h->nr - 1 + d.rows - 1) / d.rows * d.tiles, ct = (h->nr - 2 + d.rows - 1) / d.rows * d.tiles;
-        poff[q + 1] = poff[q] + pt;
-        coff[q + 1] = coff[q] + ct;
+        // the job's group: same arithmetic and CTA size, room for one more job
+        teuk_batch::Group *g = nullptr;
+        for (auto &c : b->groups)
+            if (c.real == h->sp.real_coef && c.fx == h->sp.fixed_point && c.ko == h->sp.ko && c.block == block &&
+                (int)c.members.size() < kMultiMaxJobs)
+                g = &c;
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->real = h->sp.real_coef;
+            g->fx = h->sp.fixed_point;
+            g->ko = h->sp.ko;
+            g->block = block;
+            g->pred.njobs = g->corr.njobs = 0;
+            g->pred.off[0] = g->corr.off[0] = 0;
+        }
+        g->smem = std::max(g->smem, multi_smem_bytes(d.tw, block, h->sp.ko));
+        const int slot = (int)g->members.size();
+        g->members.push_back(q);
+        for (int w = 0; w < 2; ++w) {
+            MultiArgs &a = w ? g->corr : g->pred;
+            const int rows = w ? h->nr - 2 : h->nr - 1;
+            a.jobs[slot] = d;
+            a.off[slot + 1] = a.off[slot] + (rows + d.rows - 1) / d.rows * d.tiles;
+            a.njobs = slot + 1;
+            a.ntiles = a.off[slot + 1];
+        }
     }
-    b->pred_tiles = poff[nj];
-    b->corr_tiles = coff[nj];
-    smem = batch_smem_bytes(b->block, ko_any);
-    b->smem = smem;
-    BCU(batch_allow_smem(smem));
-    int sms = 0, per_sm = 0;
-    BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    for (int w = 0; w < 2; ++w) {
-        int n = 0;
-        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel_ptr(w), b->block, smem));
-        per_sm = w == 0 ? n : std::min(per_sm, n);
+    for (auto &g : b->groups) {
+        g.ctas = 0;
+        if (b->ctas_request > 0) {  // persistent: as many CTAs as stay resident, at most the request per SM
+            int per_sm = b->ctas_request;
+            for (int w = 0; w < 2; ++w) {
+                int n = 0;
+                BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_kernel_ptr(w, g.real, g.fx, g.ko),
+                                                                  g.block, g.smem));
+                per_sm = std::min(per_sm, std::max(1, n));
+            }
+            g.ctas = sms * per_sm;
+        }
     }
-    b->ctas = std::max(1, sms * std::max(1, per_sm));
     BCU(cudaMemcpyAsync(b->d_jobs, b->host_desc.data(), nj * sizeof(JobDesc), cudaMemcpyHostToDevice, b->stream));
-    BCU(cudaMemcpyAsync(b->d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     b->layout_dirty = false;
     return TEUK_OK;
 }
 
-// After an odd number of steps the jobs' current buffers flipped: refresh the table.
+// After an odd number of steps the jobs' current buffers flipped: the launch
+// groups (baked into a captured graph) are refreshed and the graph dropped.
 static int refresh_cur(teuk_batch *b)
 {
     for (int q = 0; q < (int)b->active.size(); ++q) b->host_desc[q].cur = b->jobs[b->active[q]].h->cur;
-    BCU(cudaMemcpyAsync(b->d_jobs, b->host_desc.data(), b->active.size() * sizeof(JobDesc), cudaMemcpyHostToDevice,
-                        b->stream));
+    for (auto &g : b->groups)
+        for (int slot = 0; slot < (int)g.members.size(); ++slot)
+            g.pred.jobs[slot].cur = g.corr.jobs[slot].cur = b->host_desc[g.members[slot]].cur;
+    drop_graph(b);
     return TEUK_OK;
 }
 
@@ -257,14 +290,17 @@ static int refresh_cur(teuk_batch *b)
 // other step kernels use programmatic dependent launch when enabled.
 static cudaError_t launch_batch_steps(teuk_batch *b, int k0, int n, cudaStream_t st)
 {
-    const int nj = (int)b->active.size();
     for (int k = k0; k < k0 + n; ++k) {
-        cudaError_t e = launch_step_batch(b->d_jobs, b->d_off, b->d_off + (b->cap_jobs + 1), nj, b->pred_tiles,
-                                          b->corr_tiles, b->block, b->smem, b->ctas, 1.0, -0.0, k, st,
-                                          b->pdl != 0 && k > k0, b->pdl != 0);
-        if (e != cudaSuccess) return e;
+        for (int w = 0; w < 2; ++w)
+            for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+                const auto &g = b->groups[gi];
+                const bool pdl = b->pdl != 0 && !(k == k0 && w == 0 && gi == 0);
+                const cudaError_t e = launch_step_multi(w ? g.corr : g.pred, w, g.real, g.fx, g.ko, g.block, g.smem,
+                                                        g.ctas, k, st, pdl);
+                if (e != cudaSuccess) return e;
+            }
     }
-    return launch_advance_batch(b->d_jobs, nj, n, st);
+    return launch_advance_batch(b->d_jobs, (int)b->active.size(), n, st);
 }
 
 static int capture(teuk_batch *b)
@@ -398,6 +434,12 @@ extern "C" int teuk_batch_set_option(teuk_batch *b, int option, long value)
         b->block_request = (int)value;
         b->layout_dirty = true;
         break;
+    case TEUK_OPT_BATCH_CTAS:
+        if (value < 0 || value > 64)
+            return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: CTAs per SM is 0 (one per tile) to 64");
+        b->ctas_request = (int)value;
+        b->layout_dirty = true;
+        break;
     default:
         return bfail(b, TEUK_ERR_BAD_ARG, "teuk_batch_set_option: unknown option");
     }
@@ -405,7 +447,7 @@ extern "C" int teuk_batch_set_option(teuk_batch *b, int option, long value)
     return TEUK_OK;
 }
 
-extern "C" int teuk_batch_autotune(teuk_batch *b, int *best_block)
+extern "C" int teuk_batch_autotune(teuk_batch *b, int *best)
 {
     if (!b) return TEUK_ERR_BAD_ARG;
     if (b->layout_dirty) {
@@ -413,18 +455,20 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best_block)
         if (rc) return rc;
     }
     if (b->active.empty()) return bfail(b, TEUK_ERR_STATE, "teuk_batch_autotune: no job has steps left");
-    // per-job launches, then the persistent launch at three CTA sizes; each
-    // candidate gets an equal share of the steps the shortest job has left
-    const int cands[][2] = {{1, 0}, {0, 64}, {0, 128}, {0, 256}};
+    // per-job launches, multi-job launches with one CTA per tile, and the
+    // persistent multi-job launch (resident CTAs); each candidate gets an
+    // equal share of the steps the shortest job has left
+    const int cands[][2] = {{1, 0}, {0, 0}, {0, 64}};  // {mode, CTAs per SM}
     const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
     long long share = 1LL << 62;
     for (int id : b->active) share = std::min(share, b->jobs[id].remaining / ncand);
     cudaEvent_t e0, e1;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));
-    int best_mode = b->mode, best = b->block_request;
+    int best_c = b->mode == 1 ? 0 : (b->ctas_request ? 2 : 1);
     double best_rate = -1.0;
-    for (const auto &c : cands) {
+    for (int ci = 0; ci < ncand; ++ci) {
+        const auto &c = cands[ci];
         if (b->layout_dirty) {
             int rc = rebuild(b);
             if (rc) return rc;
@@ -434,7 +478,7 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best_block)
         const long long budget = std::min(share, minrem) & ~1LL;
         if (b->active.empty() || budget < 8) break;
         b->mode = c[0];
-        if (c[0] == 0) b->block_request = c[1];
+        if (c[0] == 0) b->ctas_request = c[1];
         b->layout_dirty = true;
         int rc = rebuild(b);
         if (rc) return rc;
@@ -459,16 +503,15 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best_block)
         const double rate = (double)pts * (double)n / (ms > 0 ? ms : 1e-3);
         if (rate > best_rate) {
             best_rate = rate;
-            best_mode = c[0];
-            best = c[0] == 0 ? c[1] : b->block_request;
+            best_c = ci;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->mode = best_mode;
-    b->block_request = best;
+    b->mode = cands[best_c][0];
+    if (b->mode == 0) b->ctas_request = cands[best_c][1];
     b->layout_dirty = true;
-    if (best_block) *best_block = best_mode == 0 ? best : 0;
+    if (best) *best = best_c;
     return TEUK_OK;
 }
 
@@ -481,9 +524,27 @@ extern "C" long teuk_batch_launches_for(const teuk_batch *b, long n)
             if (j.member && j.remaining > 0) total += teuk_launches_for(j.h, n);
         return total;
     }
-    // each step is two launches, each slice adds one counter update
+    // per step one predictor and one corrector launch per group; each slice
+    // adds one counter update.  Groups as the next rebuild forms them.
+    long groups = 0;
+    if (!b->layout_dirty) {
+        groups = (long)b->groups.size();
+    } else {
+        struct Key { int real, fx, ko, block; long n; };
+        std::vector<Key> keys;
+        for (const auto &j : b->jobs) {
+            if (!j.member || j.remaining <= 0) continue;
+            const int block = job_block(b, j.h);
+            bool found = false;
+            for (auto &k : keys)
+                if (k.real == j.h->sp.real_coef && k.fx == j.h->sp.fixed_point && k.ko == j.h->sp.ko &&
+                    k.block == block) { ++k.n; found = true; }
+            if (!found) keys.push_back(Key{j.h->sp.real_coef, j.h->sp.fixed_point, j.h->sp.ko, block, 1});
+        }
+        for (const auto &k : keys) groups += (k.n + kMultiMaxJobs - 1) / kMultiMaxJobs;
+    }
     const long slices = (n + b->chunk - 1) / b->chunk;
-    return 2 * n + slices;
+    return 2 * n * groups + slices;
 }
 
 extern "C" const char *teuk_batch_last_error(const teuk_batch *b) { return b ? b->err.c_str() : ""; }

@@ -121,6 +121,20 @@ struct JobDesc {
     int tiles;                // theta tiles per row
 };
 
+// The jobs of one multi-job launch (lw_predict_multi / lw_correct_multi), all
+// with the same arithmetic (real or complex planes, fixed point or FP64,
+// dissipation or not).  It is passed in the kernels' parameter space, so a
+// captured graph node keeps its own copy.  Tile t of the launch belongs to
+// the job q with off[q] <= t < off[q + 1]; a job's tiles are `rows` r* rows
+// by `tw` theta columns, rows * tw = the CTA size.
+constexpr int kMultiMaxJobs = 64;  // 64 x 368-byte descriptors: 23.8 KB of the 32 KB parameter space
+struct MultiArgs {
+    int njobs;
+    int ntiles;  // off[njobs]
+    int off[kMultiMaxJobs + 1];
+    JobDesc jobs[kMultiMaxJobs];
+};
+
 // ---------------------------------------------------------------------------
 // Kernels (teuk_kernels.cu)
 // ---------------------------------------------------------------------------
@@ -166,18 +180,22 @@ cudaError_t launch_zero_boundary_rows(double2 *Phi, double2 *Pi, int nr, int nth
 cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long long npts,
                                    unsigned long long *count, cudaStream_t st);
 
-// Persistent batch kernels: `ctas` CTAs of `block` threads work through the
-// tiles of all jobs (min(ctas, tiles) CTAs per launch).
-cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const int *corr_off, int njobs,
-                              int pred_tiles, int corr_tiles, int block, size_t smem, int ctas, double one,
-                              double nzero, int k, cudaStream_t st, bool pdl_pred, bool pdl_corr);
+// Multi-job kernels: which = 0 predictor, 1 corrector; `ctas` = 0 gives one
+// CTA per tile, otherwise a persistent grid of min(ctas, tiles) CTAs that
+// loop over the tiles.  real / fixed_point / ko select the instantiation and
+// must match every job of `a`.
+cudaError_t launch_step_multi(const MultiArgs &a, int which, int real, int fixed_point, int ko, int block,
+                              size_t smem, int ctas, int k, cudaStream_t st, bool pdl);
+const void *multi_kernel_ptr(int which, int real, int fixed_point, int ko);
+// Tile width of a job in a multi-job launch of `block`-thread CTAs: 32, 64
+// or 128 columns, dividing the CTA size.
+int multi_tile_width(int nth, int block);
+// Dynamic shared memory of a multi-job CTA for a job of tile width tw.
+size_t multi_smem_bytes(int tw, int block, int ko);
 
 cudaError_t launch_advance_batch(const JobDesc *jobs, int njobs, long long by, cudaStream_t st);
 
-size_t batch_smem_bytes(int block, int ko);
-cudaError_t batch_allow_smem(size_t smem);
 int tile_width_for(int nth, int max_width);
-const void *batch_kernel_ptr(int which);
 
 int fused_block_threads(int nth);
 size_t fused_smem_bytes(int nth, int ko);

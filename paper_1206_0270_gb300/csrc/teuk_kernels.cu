@@ -849,20 +849,35 @@ int split_rows_per_block(int nth, int fixed_point)
 #define TEUK_SPLIT_BOUNDS_FX __launch_bounds__(kFxTileThreads, kFxTileMinBlocks)
 #define TEUK_SPLIT_BOUNDS_FP64 __launch_bounds__(1024)
 
-template <bool REAL, bool FX>
-__device__ __forceinline__ void predict_split_tile(const StepParams &p, const double2 *__restrict__ Phi,
+// Where a thread sits in a split tile: tile width TW and height R (TW R
+// threads), its column tx and row ty, and the tile's r* row block rb and
+// theta tile tt.  The split kernels take it from their launch shape; the
+// multi-job kernels from the job table.
+struct TileIdx {
+    int TW, R, tx, ty, rb, tt;
+};
+__device__ __forceinline__ TileIdx tile_of_launch()
+{
+    return TileIdx{(int)blockDim.x, (int)blockDim.y, (int)threadIdx.x, (int)threadIdx.y, (int)blockIdx.x,
+                   (int)blockIdx.y};
+}
+
+// SIGNAL: end with the programmatic-launch signal (the multi-job kernels
+// signal once, after their last tile).
+template <bool REAL, bool FX, bool SIGNAL = true>
+__device__ __forceinline__ void predict_split_tile(const TileIdx &ti, const StepParams &p, const double2 *__restrict__ Phi,
                                                    const double2 *__restrict__ Pi, double2 *__restrict__ PhiH,
                                                    double2 *__restrict__ PiH, int k)
 {
     extern __shared__ double2 smem[];
-    const int nth = p.nth, TW = blockDim.x, tx = threadIdx.x;
-    const int j0 = blockIdx.y * TW, j = j0 + tx;
+    const int nth = p.nth, TW = ti.TW, tx = ti.tx;
+    const int j0 = ti.tt * TW, j = j0 + tx;
     const bool colok = j < nth;
     const int jj = colok ? j : nth - 1;
-    const int hp = blockIdx.x * blockDim.y + threadIdx.y;
+    const int hp = ti.rb * ti.R + ti.ty;
     const bool rowok = hp < p.nr - 1;
     const int hq = rowok ? hp : p.nr - 2;
-    double2 *row = smem + threadIdx.y * (TW + 2);
+    double2 *row = smem + ti.ty * (TW + 2);
     const size_t k0 = (size_t)hq * nth + jj;
     const PredCoef c = load_pred<REAL>(p, k0);
     grid_dependency_wait();
@@ -888,24 +903,24 @@ __device__ __forceinline__ void predict_split_tile(const StepParams &p, const do
         PhiH[k0] = o.phi;
         PiH[k0] = o.pi;
     }
-    allow_dependents();  // after the last store: the dependent sees only writes made before it
+    if (SIGNAL) allow_dependents();  // after the last store: the dependent sees only writes made before it
 }
 
-template <bool REAL, bool FX, bool KO>
-__device__ __forceinline__ void correct_split_tile(const StepParams &p, const double2 *__restrict__ Phi,
+template <bool REAL, bool FX, bool KO, bool SIGNAL = true>
+__device__ __forceinline__ void correct_split_tile(const TileIdx &ti, const StepParams &p, const double2 *__restrict__ Phi,
                                                    const double2 *__restrict__ Pi, const double2 *__restrict__ PhiH,
                                                    const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
                                                    double2 *__restrict__ PiO, int k)
 {
     extern __shared__ double2 smem[];
-    const int nth = p.nth, TW = blockDim.x, tx = threadIdx.x;
-    const int j0 = blockIdx.y * TW, j = j0 + tx;
+    const int nth = p.nth, TW = ti.TW, tx = ti.tx;
+    const int j0 = ti.tt * TW, j = j0 + tx;
     const bool colok = j < nth;
     const int jj = colok ? j : nth - 1;
-    const int i = 1 + blockIdx.x * blockDim.y + threadIdx.y;
+    const int i = 1 + ti.rb * ti.R + ti.ty;
     const bool rowok = i <= p.nr - 2;
     const int iq = rowok ? i : p.nr - 2;
-    double2 *row = smem + threadIdx.y * (TW + 2);
+    double2 *row = smem + ti.ty * (TW + 2);
     const size_t kc = (size_t)iq * nth + jj;
     const CorrCoef c = load_corr<REAL>(p, kc);
     grid_dependency_wait();
@@ -929,8 +944,8 @@ __device__ __forceinline__ void correct_split_tile(const StepParams &p, const do
     // values; fixed-point kernels stage each component prepared once for the
     // exact sixth difference (fx_prep: Phi re, Phi im, Pi re, Pi im rows).
     const int KW = TW + 6;
-    double2 *uph = smem + blockDim.y * (TW + 2) + threadIdx.y * 2 * KW, *upi = uph + KW;
-    FxP *kp = (FxP *)(smem + blockDim.y * (TW + 2)) + threadIdx.y * 4 * KW;
+    double2 *uph = smem + ti.R * (TW + 2) + ti.ty * 2 * KW, *upi = uph + KW;
+    FxP *kp = (FxP *)(smem + ti.R * (TW + 2)) + ti.ty * 4 * KW;
     auto stage = [&](int e, double2 a, double2 b) {
         if (FX) {
             kp[e] = fx_prep(a.x);
@@ -975,7 +990,7 @@ __device__ __forceinline__ void correct_split_tile(const StepParams &p, const do
             p.ext.ring[(size_t)slot * nth + j] = nphi;
         }
     }
-    allow_dependents();  // after the last store
+    if (SIGNAL) allow_dependents();  // after the last store
 }
 
 // The split kernels, one instantiation per (REAL, FX) -- and for the
@@ -996,7 +1011,7 @@ __global__ void lw_correct_split(StepParams p, const double2 *__restrict__ Phi, 
                                                       double2 *__restrict__ PhiH, double2 *__restrict__ PiH, \
                                                       int k)                                                 \
     {                                                                                                       \
-        predict_split_tile<REAL, FX>(p, Phi, Pi, PhiH, PiH, k);                                             \
+        predict_split_tile<REAL, FX>(tile_of_launch(), p, Phi, Pi, PhiH, PiH, k);                                             \
     }
 #define TEUK_SPLIT_CORRECT(REAL, FX, KO, BOUNDS)                                                              \
     template <>                                                                                             \
@@ -1005,7 +1020,7 @@ __global__ void lw_correct_split(StepParams p, const double2 *__restrict__ Phi, 
         const double2 *__restrict__ PhiH, const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,        \
         double2 *__restrict__ PiO, int k)                                                                    \
     {                                                                                                       \
-        correct_split_tile<REAL, FX, KO>(p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);                              \
+        correct_split_tile<REAL, FX, KO>(tile_of_launch(), p, Phi, Pi, PhiH, PiH, PhiO, PiO, k);                              \
     }
 TEUK_SPLIT_PREDICT(false, true, TEUK_SPLIT_BOUNDS_FX)
 TEUK_SPLIT_PREDICT(true, true, TEUK_SPLIT_BOUNDS_FX)
@@ -1075,298 +1090,175 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
 }
 
 // ---------------------------------------------------------------------------
-// Batched split kernels: one launch covers the tiles of every job of a batch
+// Multi-job split kernels: one launch covers the tiles of many jobs
 // ---------------------------------------------------------------------------
 
-// Dynamic shared memory of a batch CTA: the job descriptor, then `rows` rows
-// of nth + 2 sums.
+// A template bank is many independent evolutions of uneven size; a single
+// job of a small grid cannot fill the GPU, and one launch per job per kernel
+// leaves the GPU waiting on launches.  These kernels run the split kernels'
+// tile code (predict_split_tile / correct_split_tile, so every job gets the
+// bits it gets alone) for the tiles of up to kMultiMaxJobs jobs in one
+// launch.  The jobs' parameters sit in the kernel's parameter space
+// (MultiArgs, __grid_constant__): a CTA reads them through the constant
+// cache, as the split kernels read theirs.
+//
+// CTA b works on tiles b, b + G, b + 2G, ... (G = gridDim.x): a single tile
+// when the grid has one CTA per tile, a persistent loop when the grid is
+// capped at the CTAs the GPU holds at once.  A CTA visits tiles in
+// increasing order, so its job index only moves forward.
 
-// Largest j < njobs with off[j] <= b (off is increasing, off[0] = 0).
-__device__ __forceinline__ int find_job(const int *off, int njobs, int b)
+int multi_tile_width(int nth, int block)
 {
-    int lo = 0, hi = njobs - 1;
+    int best = 32;
+    double best_score = -1.0;
+    for (int tw = 128; tw >= 32; tw /= 2) {
+        if (tw > block || block % tw) continue;
+        const int lanes = (nth + tw - 1) / tw * tw;
+        const double score = (double)nth / lanes - (tw < 128 ? 0.02 * (128 - tw) / 32 : 0.0);
+        if (score > best_score + 1e-12) {  // ties keep the wider tile
+            best = tw;
+            best_score = score;
+        }
+    }
+    return best;
+}
+
+size_t multi_smem_bytes(int tw, int block, int ko)
+{
+    const size_t R = (size_t)block / tw;
+    return sizeof(double2) * (R * (tw + 2) + (ko ? 4 * R * (tw + 6) : 0));
+}
+
+// First job of tile b: the largest q with off[q] <= b.
+__device__ __forceinline__ int multi_first_job(const MultiArgs &a, int b)
+{
+    int lo = 0, hi = a.njobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (ldcg(off + mid) <= b) lo = mid; else hi = mid - 1;
+        if (a.off[mid] <= b) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
-// The batch kernels are persistent: a fixed grid of CTAs, CTA c working
-// through tiles [c T / G, (c + 1) T / G) in order.  A CTA copies a job's
-// descriptor to shared memory (through L2: the host rewrites the table
-// between slices) only when its range enters the next job, and alternates
-// two sigma-row buffers so that each tile needs one barrier.
-struct BatchCursor {
-    int jb = -1, beg = 0, end = 0;  // current job and its tile range
-    int rb = 0, tt = 0;             // r* row block and theta tile of the current tile
-    int tx = 0, ty = 0;             // this thread's column and row within a tile
-};
-
-__device__ __forceinline__ void batch_enter(const JobDesc *jobs, const int *off, int njobs, int tile,
-                                            BatchCursor &cur, JobDesc *sj)
+__device__ __forceinline__ TileIdx multi_tile(const JobDesc &J, int t)
 {
-    if (tile < cur.end) return;  // uniform over the CTA
-    __syncthreads();             // every thread is done with the previous descriptor
-    int jb = cur.jb < 0 ? find_job(off, njobs, tile) : cur.jb + 1;
-    while (jb + 1 < njobs && ldcg(off + jb + 1) <= tile) ++jb;
-    const unsigned long long *src = (const unsigned long long *)(jobs + jb);
-    unsigned long long *dst = (unsigned long long *)sj;
-    for (int w = threadIdx.x; w < (int)(sizeof(JobDesc) / 8); w += blockDim.x) dst[w] = ldcg(src + w);
-    cur.jb = jb;
-    cur.beg = ldcg(off + jb);
-    cur.end = ldcg(off + jb + 1);
-    // the tile geometry of the job, read from the table (the copy is not yet visible)
-    const int tw = ldcg(&jobs[jb].tw), tiles = ldcg(&jobs[jb].tiles);
-    cur.ty = threadIdx.x / tw;
-    cur.tx = threadIdx.x - cur.ty * tw;
-    cur.rb = (tile - cur.beg) / tiles;
-    cur.tt = tile - cur.beg - cur.rb * tiles;
-    __syncthreads();
+    const int tw = J.tw, tiles = J.tiles, rb = t / tiles;
+    const int ty = (int)threadIdx.x / tw;
+    return TileIdx{tw, J.rows, (int)threadIdx.x - ty * tw, ty, rb, t - rb * tiles};
 }
 
-// Move the cursor to the next tile of the same job (the caller re-enters
-// when it leaves the job).
-__device__ __forceinline__ void batch_next(const JobDesc &J, BatchCursor &cur)
+// PERSIST: loop over tiles b, b + G, ...; otherwise the grid has one CTA per
+// tile (fewer registers live across the tile code).
+template <bool REAL, bool FX, bool PERSIST>
+__device__ __forceinline__ void predict_multi_body(const MultiArgs &a, int k)
 {
-    if (++cur.tt == J.tiles) {
-        cur.tt = 0;
-        ++cur.rb;
-    }
-}
-
-// Tile of the current job at the cursor: theta columns from j0 = tt tw;
-// threads past the job's rows only join the barrier.
-struct BatchTile {
-    int tx, tyc, j0, j, jj, rb;
-    bool slot, colok;
-};
-
-__device__ __forceinline__ BatchTile batch_tile(const JobDesc &J, const BatchCursor &cur)
-{
-    BatchTile t;
-    const int R = J.rows;
-    t.rb = cur.rb;
-    t.j0 = cur.tt * J.tw;
-    t.tx = cur.tx;
-    t.slot = cur.ty < R;
-    t.tyc = t.slot ? cur.ty : R - 1;
-    t.j = t.j0 + t.tx;
-    t.colok = t.slot && t.j < J.p.nth;
-    t.jj = t.j < J.p.nth ? t.j : J.p.nth - 1;
-    return t;
-}
-
-// Row buffer words (double2) per buffer for a CTA of `block` threads: R rows
-// of tw + 2 with R tw <= block and R <= block / 32.
-__host__ __device__ __forceinline__ int batch_row_words(int block) { return block + 2 * (block / 32); }
-// Dissipation buffer words per buffer: R rows of the old Phi and Pi, tw + 6 each.
-__host__ __device__ __forceinline__ int batch_ko_words(int block) { return 2 * (block + 6 * (block / 32)); }
-
-__global__ void __launch_bounds__(kTileMaxThreads) lw_predict_batch(const JobDesc *__restrict__ jobs,
-                                                                     const int *__restrict__ off, int njobs,
-                                                                     int ntiles, int k, Ops ops)
-{
-    extern __shared__ double2 smem[];
-    JobDesc &J = *(JobDesc *)smem;
-    double2 *rowbuf = smem + (sizeof(JobDesc) + 15) / 16;
-    const int bw = batch_row_words(blockDim.x);
-    const int t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
-    const int t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
-    BatchCursor cur;
-    for (int tile = t0; tile < t1; ++tile) {
-        batch_enter(jobs, off, njobs, tile, cur, &J);
-        const BatchTile t = batch_tile(J, cur);
-        const StepParams &p = J.p;
-        const int nth = p.nth, tw = J.tw;
-        const int hp = t.rb * J.rows + t.tyc;
-        const bool rowok = t.slot && hp < p.nr - 1;
-        const int hq = min(hp, p.nr - 2);
-        double2 *row = rowbuf + (tile & 1) * bw + t.tyc * (tw + 2);
-        const size_t k0 = (size_t)hq * nth + t.jj;
-        const bool real = p.real_coef != 0;  // uniform over the CTA
-        const PredCoef c = real ? load_pred<true>(p, k0) : load_pred<false>(p, k0);
-        if (tile == t0) grid_dependency_wait();
+    int q = multi_first_job(a, blockIdx.x);
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        while (PERSIST && q + 1 < a.njobs && a.off[q + 1] <= tile) ++q;
+        const JobDesc &J = a.jobs[q];
         const int from = J.cur ^ (k & 1);
-        const double2 *Phi = J.phi[from], *Pi = J.pi[from];
-        const double2 phi0 = ldcg(Phi + k0), pi0 = ldcg(Pi + k0), phi1 = ldcg(Phi + k0 + nth),
-                      pi1 = ldcg(Pi + k0 + nth);
-        if (t.slot) {
-            row[t.tx + 1] = t.colok ? add2(phi0, phi1, ops) : make_double2(0.0, 0.0);
-            const size_t kr = (size_t)hq * nth;
-            if (t.tx == 0)
-                row[0] = t.j0 > 0 ? add2(ldcg(Phi + kr + t.j0 - 1), ldcg(Phi + kr + nth + t.j0 - 1), ops)
-                                  : make_double2(0.0, 0.0);
-            if (t.tx == tw - 1)
-                row[tw + 1] = t.j0 + tw < nth
-                                  ? add2(ldcg(Phi + kr + t.j0 + tw), ldcg(Phi + kr + nth + t.j0 + tw), ops)
-                                  : make_double2(0.0, 0.0);
-        }
-        __syncthreads();
-        const double2 sup = row[t.tx + 2], sdn = row[t.tx];
-        HalfStep o = real ? (p.fixed_point ? predict_c<true, true>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn)
-                                           : predict_c<true, false>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn))
-                          : (p.fixed_point ? predict_c<false, true>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn)
-                                           : predict_c<false, false>(c, p.q, ops, phi0, pi0, phi1, pi1, sup, sdn));
-        const SourceWindow &sw = p.src;
-        if (sw.active && hq >= sw.mid_lo && hq <= sw.mid_hi) {
-            const long long n = ldcg(p.step_base) + k;
-            rfma(o.pi, ldg(sw.gP + (size_t)(hq - sw.mid_lo) * nth + t.jj),
-                 unit_phase(sw.m_omega * ((double)n * p.dt)));
-        }
-        if (t.colok && rowok) {
-            J.phiH[k0] = o.phi;
-            J.piH[k0] = o.pi;
-        }
-        batch_next(J, cur);
+        predict_split_tile<REAL, FX, false>(multi_tile(J, tile - a.off[q]), J.p, J.phi[from], J.pi[from], J.phiH,
+                                            J.piH, k);
+        if (!PERSIST) break;
+        if (tile + (int)gridDim.x < a.ntiles) __syncthreads();  // the next tile reuses the shared rows
     }
     allow_dependents();  // after the CTA's last store
 }
 
-__global__ void __launch_bounds__(kTileMaxThreads) lw_correct_batch(const JobDesc *__restrict__ jobs,
-                                                                     const int *__restrict__ off, int njobs,
-                                                                     int ntiles, int k, Ops ops)
+template <bool REAL, bool FX, bool KO, bool PERSIST>
+__device__ __forceinline__ void correct_multi_body(const MultiArgs &a, int k)
 {
-    extern __shared__ double2 smem[];
-    JobDesc &J = *(JobDesc *)smem;
-    double2 *rowbuf = smem + (sizeof(JobDesc) + 15) / 16;
-    const int bw = batch_row_words(blockDim.x);
-    const int t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
-    const int t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
-    BatchCursor cur;
-    for (int tile = t0; tile < t1; ++tile) {
-        batch_enter(jobs, off, njobs, tile, cur, &J);
-        const BatchTile t = batch_tile(J, cur);
-        const StepParams &p = J.p;
-        const int nth = p.nth, tw = J.tw;
-        const int i = 1 + t.rb * J.rows + t.tyc;
-        const bool rowok = t.slot && i <= p.nr - 2;
-        const int iq = min(i, p.nr - 2);
-        double2 *row = rowbuf + (tile & 1) * bw + t.tyc * (tw + 2);
-        const size_t kc = (size_t)iq * nth + t.jj;
-        const bool real = p.real_coef != 0;
-        const CorrCoef c = real ? load_corr<true>(p, kc) : load_corr<false>(p, kc);
-        if (tile == t0) grid_dependency_wait();
+    int q = multi_first_job(a, blockIdx.x);
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        while (PERSIST && q + 1 < a.njobs && a.off[q + 1] <= tile) ++q;
+        const JobDesc &J = a.jobs[q];
         const int from = J.cur ^ (k & 1);
-        const double2 *Phi = J.phi[from], *Pi = J.pi[from];
-        double2 *PhiO = J.phi[1 - from], *PiO = J.pi[1 - from];
-        HalfStep hp, hm;
-        hp.phi = ldcg(J.phiH + kc);
-        hp.pi = ldcg(J.piH + kc);
-        hm.phi = ldcg(J.phiH + kc - nth);
-        hm.pi = ldcg(J.piH + kc - nth);
-        const double2 phi = ldcg(Phi + kc), pi = ldcg(Pi + kc);
-        const bool ko = p.ko != 0;  // uniform over the CTA
-        const int KW = tw + 6;
-        double2 *uph = rowbuf + 2 * bw + (tile & 1) * batch_ko_words(blockDim.x) + t.tyc * 2 * KW, *upi = uph + KW;
-        if (t.slot) {
-            row[t.tx + 1] = t.colok ? add2(hp.phi, hm.phi, ops) : make_double2(0.0, 0.0);
-            const size_t kr = (size_t)iq * nth;
-            if (t.tx == 0)
-                row[0] = t.j0 > 0 ? add2(ldcg(J.phiH + kr + t.j0 - 1), ldcg(J.phiH + kr - nth + t.j0 - 1), ops)
-                                  : make_double2(0.0, 0.0);
-            if (t.tx == tw - 1)
-                row[tw + 1] = t.j0 + tw < nth
-                                  ? add2(ldcg(J.phiH + kr + t.j0 + tw), ldcg(J.phiH + kr - nth + t.j0 + tw), ops)
-                                  : make_double2(0.0, 0.0);
-            if (ko) {  // the row's old Phi and Pi, columns j0 - 3 .. j0 + tw + 2 (as in the split corrector)
-                const double2 *rp = Phi + kr, *rq = Pi + kr;
-                uph[t.tx + 3] = t.j < nth ? phi : ko_load(rp, t.j, nth, p.parity);
-                upi[t.tx + 3] = t.j < nth ? pi : ko_load(rq, t.j, nth, p.parity);
-                if (t.tx < 3) {
-                    uph[t.tx] = ko_load(rp, t.j0 - 3 + t.tx, nth, p.parity);
-                    upi[t.tx] = ko_load(rq, t.j0 - 3 + t.tx, nth, p.parity);
-                }
-                if (t.tx >= tw - 3) {
-                    uph[t.tx + 6] = ko_load(rp, t.j + 3, nth, p.parity);
-                    upi[t.tx + 6] = ko_load(rq, t.j + 3, nth, p.parity);
-                }
-            }
-        }
-        __syncthreads();
-        double2 nphi, npi;
-        const double2 sup = row[t.tx + 2], sdn = row[t.tx];
-        const KoCoef kw = ko_of(p);
-        if (ko) {
-            if (real) {
-                if (p.fixed_point) correct_c<true, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<true>(uph, upi, t.tx + 3, ops), &nphi, &npi);
-                else correct_c<true, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<false>(uph, upi, t.tx + 3, ops), &nphi, &npi);
-            } else {
-                if (p.fixed_point) correct_c<false, true, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<true>(uph, upi, t.tx + 3, ops), &nphi, &npi);
-                else correct_c<false, false, true>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, ko_from_rows<false>(uph, upi, t.tx + 3, ops), &nphi, &npi);
-            }
-        } else {
-            const KoIn z{};
-            if (real) {
-                if (p.fixed_point) correct_c<true, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
-                else correct_c<true, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
-            } else {
-                if (p.fixed_point) correct_c<false, true, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
-                else correct_c<false, false, false>(c, p.half_dt, ops, phi, pi, hp, hm, sup, sdn, kw, z, &nphi, &npi);
-            }
-        }
-        const long long n = ldcg(p.step_base) + k;
-        const SourceWindow &sw = p.src;
-        if (sw.active && iq >= sw.node_lo && iq <= sw.node_hi)
-            rfma(npi, ldg(sw.gC + (size_t)(iq - sw.node_lo) * nth + t.jj),
-                 unit_phase(sw.m_omega * (((double)n + 0.5) * p.dt)));
-        if (t.colok && rowok) {
-            PhiO[kc] = nphi;
-            PiO[kc] = npi;
-            if (iq == p.ext.i_ext && ((n + 1) % p.ext.every) == 0) {
-                const long long slot_k = ((n + 1) / p.ext.every - 1) % p.ext.capacity;
-                p.ext.ring[(size_t)slot_k * nth + t.j] = nphi;
-            }
-        }
-        batch_next(J, cur);
+        correct_split_tile<REAL, FX, KO, false>(multi_tile(J, tile - a.off[q]), J.p, J.phi[from], J.pi[from],
+                                                J.phiH, J.piH, J.phi[from ^ 1], J.pi[from ^ 1], k);
+        if (!PERSIST) break;
+        if (tile + (int)gridDim.x < a.ntiles) __syncthreads();
     }
     allow_dependents();
 }
 
-const void *batch_kernel_ptr(int which) { return which ? (const void *)lw_correct_batch : (const void *)lw_predict_batch; }
+// One instantiation per arithmetic and launch form, with the split kernels'
+// launch bounds.
+template <bool REAL, bool FX, bool PERSIST>
+__global__ void lw_predict_multi(const __grid_constant__ MultiArgs a, int k);
+template <bool REAL, bool FX, bool KO, bool PERSIST>
+__global__ void lw_correct_multi(const __grid_constant__ MultiArgs a, int k);
 
-// Descriptor, two sigma-row buffers and, when a job has the dissipation on,
-// two dissipation buffers (the persistent kernels alternate buffers by tile
-// so that a tile needs one barrier).
-size_t batch_smem_bytes(int block, int ko)
-{
-    return ((sizeof(JobDesc) + 15) / 16) * 16 +
-           2 * sizeof(double2) * ((size_t)batch_row_words(block) + (ko ? (size_t)batch_ko_words(block) : 0));
-}
-
-// Let both persistent kernels take `smem` bytes of dynamic shared memory
-// (above the 48 KB default at 512-thread CTAs with the dissipation).
-cudaError_t batch_allow_smem(size_t smem)
-{
-    for (int w = 0; w < 2; ++w) {
-        const cudaError_t e = cudaFuncSetAttribute(batch_kernel_ptr(w), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
-        if (e != cudaSuccess) return e;
+#define TEUK_MULTI_PREDICT(REAL, FX, PERSIST, BOUNDS)                                                        \
+    template <>                                                                                            \
+    __global__ void BOUNDS lw_predict_multi<REAL, FX, PERSIST>(const __grid_constant__ MultiArgs a, int k) \
+    {                                                                                                      \
+        predict_multi_body<REAL, FX, PERSIST>(a, k);                                                       \
     }
-    return cudaSuccess;
+#define TEUK_MULTI_CORRECT(REAL, FX, KO, PERSIST, BOUNDS)                                                        \
+    template <>                                                                                                \
+    __global__ void BOUNDS lw_correct_multi<REAL, FX, KO, PERSIST>(const __grid_constant__ MultiArgs a, int k) \
+    {                                                                                                          \
+        correct_multi_body<REAL, FX, KO, PERSIST>(a, k);                                                       \
+    }
+#define TEUK_MULTI_BOTH(PERSIST)                                                \
+    TEUK_MULTI_PREDICT(false, true, PERSIST, TEUK_SPLIT_BOUNDS_FX)              \
+    TEUK_MULTI_PREDICT(true, true, PERSIST, TEUK_SPLIT_BOUNDS_FX)               \
+    TEUK_MULTI_PREDICT(false, false, PERSIST, TEUK_SPLIT_BOUNDS_FP64)           \
+    TEUK_MULTI_PREDICT(true, false, PERSIST, TEUK_SPLIT_BOUNDS_FP64)            \
+    TEUK_MULTI_CORRECT(false, true, false, PERSIST, TEUK_SPLIT_BOUNDS_FX)       \
+    TEUK_MULTI_CORRECT(true, true, false, PERSIST, TEUK_SPLIT_BOUNDS_FX)        \
+    TEUK_MULTI_CORRECT(false, false, false, PERSIST, TEUK_SPLIT_BOUNDS_FP64)    \
+    TEUK_MULTI_CORRECT(true, false, false, PERSIST, TEUK_SPLIT_BOUNDS_FP64)     \
+    TEUK_MULTI_CORRECT(false, true, true, PERSIST, TEUK_SPLIT_BOUNDS_FX)        \
+    TEUK_MULTI_CORRECT(true, true, true, PERSIST, TEUK_SPLIT_BOUNDS_FX)         \
+    TEUK_MULTI_CORRECT(false, false, true, PERSIST, TEUK_SPLIT_BOUNDS_FP64)     \
+    TEUK_MULTI_CORRECT(true, false, true, PERSIST, TEUK_SPLIT_BOUNDS_FP64)
+TEUK_MULTI_BOTH(false)
+TEUK_MULTI_BOTH(true)
+#undef TEUK_MULTI_BOTH
+#undef TEUK_MULTI_PREDICT
+#undef TEUK_MULTI_CORRECT
+
+// Kernel of a multi-job launch form (persistent or one CTA per tile).
+#define TEUK_PICK_P(K, real, fx, P) \
+    ((real) ? ((fx) ? K<true, true, P> : K<true, false, P>) : ((fx) ? K<false, true, P> : K<false, false, P>))
+#define TEUK_PICK3_P(K, real, fx, ko, P)                                                                     \
+    ((ko) ? ((real) ? ((fx) ? K<true, true, true, P> : K<true, false, true, P>)                              \
+                    : ((fx) ? K<false, true, true, P> : K<false, false, true, P>))                            \
+          : ((real) ? ((fx) ? K<true, true, false, P> : K<true, false, false, P>)                            \
+                    : ((fx) ? K<false, true, false, P> : K<false, false, false, P>)))
+static const void *multi_ptr(int which, int real, int fx, int ko, bool persist)
+{
+    if (which)
+        return persist ? (const void *)TEUK_PICK3_P(lw_correct_multi, real, fx, ko, true)
+                       : (const void *)TEUK_PICK3_P(lw_correct_multi, real, fx, ko, false);
+    return persist ? (const void *)TEUK_PICK_P(lw_predict_multi, real, fx, true)
+                   : (const void *)TEUK_PICK_P(lw_predict_multi, real, fx, false);
 }
 
-cudaError_t launch_step_batch(const JobDesc *jobs, const int *pred_off, const int *corr_off, int njobs,
-                              int pred_tiles, int corr_tiles, int block, size_t smem, int ctas, double one,
-                              double nzero, int k, cudaStream_t st, bool pdl_pred, bool pdl_corr)
+// The persistent form's kernel (for occupancy queries).
+const void *multi_kernel_ptr(int which, int real, int fixed_point, int ko)
 {
+    return multi_ptr(which, real, fixed_point, ko, true);
+}
+
+cudaError_t launch_step_multi(const MultiArgs &a, int which, int real, int fixed_point, int ko, int block,
+                              size_t smem, int ctas, int k, cudaStream_t st, bool pdl)
+{
+    if (a.ntiles <= 0) return cudaSuccess;
+    const bool persist = ctas > 0 && ctas < a.ntiles;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(persist ? ctas : a.ntiles);
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cfg.attrs = pdl_pred ? attr : nullptr;
-    cfg.numAttrs = pdl_pred ? 1 : 0;
-    const Ops ops{one, nzero};
-    cfg.gridDim = dim3(std::min(ctas, pred_tiles));
-    cudaError_t e = cudaLaunchKernelEx(&cfg, lw_predict_batch, jobs, pred_off, njobs, pred_tiles, k, ops);
-    if (e != cudaSuccess) return e;
-    cfg.attrs = pdl_corr ? attr : nullptr;
-    cfg.numAttrs = pdl_corr ? 1 : 0;
-    cfg.gridDim = dim3(std::min(ctas, corr_tiles));
-    e = cudaLaunchKernelEx(&cfg, lw_correct_batch, jobs, corr_off, njobs, corr_tiles, k, ops);
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    void *args[] = {(void *)&a, (void *)&k};
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, multi_ptr(which, real, fixed_point, ko, persist), args);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

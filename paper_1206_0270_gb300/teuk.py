@@ -34,6 +34,8 @@ TEUK_OPT_REAL_PATH = 4
 TEUK_OPT_SPLIT_ROWS = 5
 TEUK_OPT_BATCH_MODE = 6
 TEUK_OPT_FIXED_POINT = 7
+TEUK_OPT_BATCH_CTAS = 8
+BATCH_FORMS = ("per-job launches", "multi-job launches, one CTA per tile", "persistent multi-job launches")
 ERRORS = {-1: "TEUK_ERR_BAD_ARG", -2: "TEUK_ERR_OOM", -3: "TEUK_ERR_CUDA", -4: "TEUK_ERR_NONFINITE",
           -5: "TEUK_ERR_STATE", -6: "TEUK_ERR_OVERFLOW"}
 
@@ -342,6 +344,8 @@ class Batch:
         _bcheck(teuk_batch_set_option(self.b, int(option), int(value)), self.b, "teuk_batch_set_option")
 
     def autotune(self):
+        """Time the launch forms and keep the fastest; returns its index in
+        BATCH_FORMS."""
         best = C.c_int()
         _bcheck(teuk_batch_autotune(self.b, C.byref(best)), self.b, "teuk_batch_autotune")
         return best.value

@@ -62,15 +62,20 @@ def run_alone(T):
     return res
 
 
-@pytest.mark.parametrize("pdl,chunk,block,mode", [(1, 64, 0, 0), (0, 64, 0, 0), (1, 8, 512, 0), (1, 2, 256, 0),
-                                                  (1, 64, 64, 0), (1, 64, 0, 1), (0, 2, 0, 1), (1, 6, 0, 1)])
-def test_batch_equals_individual_runs(teuk, pdl, chunk, block, mode):
-    # mode 0: one persistent launch for all jobs; mode 1: per-job launches
+@pytest.mark.parametrize("pdl,chunk,block,ctas,mode", [
+    (1, 64, 0, 0, 0), (0, 64, 0, 0, 0), (1, 8, 512, 0, 0), (1, 2, 256, 0, 0), (1, 64, 64, 0, 0), (1, 64, 96, 0, 0),
+    (1, 64, 0, 1, 0), (0, 6, 0, 2, 0), (1, 64, 64, 64, 0),
+    (1, 64, 0, 0, 1), (0, 2, 0, 0, 1), (1, 6, 0, 0, 1)])
+def test_batch_equals_individual_runs(teuk, pdl, chunk, block, ctas, mode):
+    # mode 0: one launch per kernel for all jobs (one CTA per tile, or a
+    # persistent grid of `ctas` CTAs per SM looping over the tiles); mode 1:
+    # per-job launches
     alone = run_alone(teuk)
     B = teuk.Batch()
     B.set_option(teuk.TEUK_OPT_PDL, pdl)
     B.set_option(teuk.TEUK_OPT_GRAPH_CHUNK, chunk)
     B.set_option(teuk.TEUK_OPT_BLOCK_THREADS, block)
+    B.set_option(teuk.TEUK_OPT_BATCH_CTAS, ctas)
     B.set_option(teuk.TEUK_OPT_BATCH_MODE, mode)
     solvers = []
     for q, j in enumerate(JOBS):
@@ -97,7 +102,7 @@ def test_batch_in_slices_remove_and_autotune(teuk):
         solvers.append(g)
         B.add(g, j["steps"])
     best = B.autotune()          # timed steps count as progress
-    assert best in (0, 64, 128, 256)
+    assert best in (0, 1, 2)
     B.step(5)
     B.set_option(teuk.TEUK_OPT_BATCH_MODE, 0)  # switch modes mid-run, odd slices
     B.step(33)
@@ -120,13 +125,15 @@ def test_batch_in_slices_remove_and_autotune(teuk):
     B.close()
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_batch_matches_oracle(teuk, mode):
-    # both modes: one persistent launch for all jobs (0), per-job launches (1)
+@pytest.mark.parametrize("mode,ctas", [(0, 0), (0, 4), (1, 0)])
+def test_batch_matches_oracle(teuk, mode, ctas):
+    # the multi-job launches (mode 0; one CTA per tile, or persistent) and
+    # per-job launches (mode 1)
     j = JOBS[0]
     g, dt = make(teuk, j, 0)
     other, _ = make(teuk, JOBS[3], 3)
     B = teuk.Batch()
+    B.set_option(teuk.TEUK_OPT_BATCH_CTAS, ctas)
     B.set_option(teuk.TEUK_OPT_BATCH_MODE, mode)
     B.add(g, j["steps"])
     B.add(other, JOBS[3]["steps"])
@@ -171,6 +178,9 @@ def test_batch_bad_arguments(teuk):
     h.step(1)                    # usable again after removal
     with pytest.raises(teuk.TeukError):
         B.set_option(teuk.TEUK_OPT_BLOCK_THREADS, 100)
+    for bad in (-1, 65):
+        with pytest.raises(teuk.TeukError):
+            B.set_option(teuk.TEUK_OPT_BATCH_CTAS, bad)
     assert B.step(0) == 0
     B.close()
 
@@ -207,12 +217,13 @@ def test_batch_mixes_fixed_point_and_fp64_jobs(teuk, mode):
     B.close()
 
 
-@pytest.mark.parametrize("mode", ["auto", 0])
+@pytest.mark.parametrize("mode", ["auto", 0, "persistent"])
 def test_mode_batch_at_full_size_equals_individual_runs(teuk, mode):
     """The batched-modes workload at its own sizes: a = 0.7, r0 = 8, m = 1..8
     on 4096 x {32, 32, 64, 64, 128, 128, 256, 256}, r* in [-100, 600], with
     the source and waveform extraction, in the benchmark's launch
-    configuration (autotuned) and in one persistent launch per step.  Uneven
+    configuration (autotuned) and in the multi-job launches (one CTA per tile,
+    and persistent).  Uneven
     step counts (640 .. 1200) must give each job the same bits as stepping
     its handle alone; the single-job path is held to the oracle by the
     parity tests."""
@@ -243,6 +254,9 @@ def test_mode_batch_at_full_size_equals_individual_runs(teuk, mode):
         B.add(g, j["steps"])
     if mode == "auto":
         B.autotune()
+    elif mode == "persistent":
+        B.set_option(teuk.TEUK_OPT_BATCH_CTAS, 8)
+        B.set_option(teuk.TEUK_OPT_BATCH_MODE, 0)
     else:
         B.set_option(teuk.TEUK_OPT_BATCH_MODE, mode)
     while B.step(10 ** 6):
