@@ -655,8 +655,10 @@ def serving_result(T, S, raw, *, slice_steps, fill_points, memory_gb, policies=(
     budget = int(memory_gb * 2 ** 30)
 
     def served(reqs, policy):
-        svc = S.WaveformService(memory_budget=budget, slice_steps=slice_steps, policy=policy,
-                                fill_points=fill_points)
+        # "async-remaining": the async policy ranking jobs by remaining work
+        name, _, order = policy.partition("-")
+        svc = S.WaveformService(memory_budget=budget, slice_steps=slice_steps, policy=name,
+                                fill_points=fill_points, order=order or "age")
         for r in reqs:
             svc.submit(r)
         torch.cuda.synchronize()
@@ -728,20 +730,26 @@ def run_serving(args):
     build.build()
     from paper_1206_0270_gb300 import inputs, serve as S
     from paper_1206_0270_gb300 import teuk as T
-    raw = inputs.serving_requests(args.requests, args.rate, long_tail=args.long_tail)
+    long_steps = tuple(float(x) for x in args.long_steps.split(","))
+    long_grids = tuple(tuple(int(v) for v in g.split("x")) for g in args.long_grids.split(","))
+    raw = inputs.serving_requests(args.requests, args.rate, long_tail=args.long_tail, long_steps=long_steps,
+                                  long_grids=long_grids, long_weights=None)
     sweep = [float(x) for x in args.rate_sweep.split(",") if x.strip()]
+    policies = tuple(x for x in args.policies.split(",") if x)
     r = serving_result(T, S, raw, slice_steps=args.slice, fill_points=args.fill_points, memory_gb=args.memory_gb,
-                       policies=("async", "fill", "share", "priority"), sweep=sweep, n_requests=args.requests,
-                       rate=args.rate)
-    a = r["policies"]["async"]
+                       policies=policies, sweep=sweep, n_requests=args.requests, rate=args.rate)
+    pol = policies[0]
+    a = r["policies"][pol]
     line = dict(metric="served waveforms/s", value=a["value"], unit="waveforms/s", n_gpus=1, steps=1, warmup=0,
                 ms_per_step=1e3 * r["requests"] / a["value"], higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload="serving", requests=r["requests"], rate_per_s=args.rate,
                             slice_steps=args.slice, fill_points=args.fill_points, memory_budget_gb=args.memory_gb,
                             point_updates=r["point_updates"], grids="2048x64..32768x512",
-                            steps="logU[1e3, 1e4]", long_tail=args.long_tail),
-                policy="async", latency_s=a["latency_s"], grid_pt_updates_per_s=a["grid_pt_updates_per_s"],
+                            steps="logU[1e3, 1e4]", long_tail=args.long_tail,
+                            long_steps=args.long_steps if args.long_tail else None,
+                            long_grids=args.long_grids if args.long_tail else None),
+                policy=pol, latency_s=a["latency_s"], grid_pt_updates_per_s=a["grid_pt_updates_per_s"],
                 policies=r["policies"], one_by_one=r["one_by_one"], short_half=r.get("short_half"),
                 rate_sweep=r.get("rate_sweep"))
     print(json.dumps(line), flush=True)
@@ -784,7 +792,12 @@ def main():
                          "('' to skip)")
     ap.add_argument("--memory-gb", type=float, default=200.0, help="serving: device memory budget (GiB)")
     ap.add_argument("--long-tail", type=int, default=0,
-                    help="serving: number of long requests (1e5..1e6 steps, 8192x128..32768x512) in the stream")
+                    help="serving: number of long requests in the stream (the earliest arrivals)")
+    ap.add_argument("--long-steps", default="1e5,1e6", help="serving: step range of the long requests (logU)")
+    ap.add_argument("--long-grids", default="32768x512,8192x128,16384x256",
+                    help="serving: grids of the long requests, taken in turn")
+    ap.add_argument("--policies", default="async,async-remaining,fill,share,priority",
+                    help="serving: scheduling policies to run (the first is the line's value)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the batched and serving blocks of the default run")
     args = ap.parse_args()

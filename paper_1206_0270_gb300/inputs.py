@@ -148,19 +148,19 @@ def serving_requests(n: int, rate: float, seed: int = 20120604, step_range=(1e3,
     with `grid_weights`, steps ~ logU[step_range].  With long_tail = k, the
     first k of the n requests (the earliest arrivals, so that they are on the
     GPU while the short ones come in) are long jobs instead: steps ~
-    logU[long_steps], grid from `long_grids` with `long_weights`."""
+    logU[long_steps], grid from `long_grids` with `long_weights` (None: the
+    long jobs take the grids in turn)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     w = np.asarray(grid_weights, float)
     w = w / w.sum()
-    lw = np.asarray(long_weights, float)
-    lw = lw / lw.sum()
+    lw = None if long_weights is None else np.asarray(long_weights, float) / np.sum(long_weights)
     for k in range(n):
         t += rng.exponential(1.0 / rate)
         long_job = k < long_tail
         if long_job:
-            nr, nth = long_grids[rng.choice(len(long_grids), p=lw)]
+            nr, nth = long_grids[k % len(long_grids) if lw is None else rng.choice(len(long_grids), p=lw)]
             lo, hi = long_steps
         else:
             nr, nth = grids[rng.choice(len(grids), p=w)]

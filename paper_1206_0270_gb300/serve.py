@@ -103,15 +103,25 @@ class WaveformService:
     rank among the running jobs (the oldest highest, promoted as older jobs
     retire): a younger job's kernels then take only the SMs an older job's
     kernels leave free, as in first-come first-served order, instead of
-    slowing a small older job down to the pace of a large younger one."""
+    slowing a small older job down to the pace of a large younger one.
+    With order="remaining" the async policy ranks the running jobs by the
+    work they have left (remaining steps x grid points) instead of by age:
+    every running job gets its next slice, and the stream priorities follow
+    that rank (the least work highest; a job moves down when a smaller one
+    arrives), so short requests pass a long job that is already running
+    (shortest remaining work first) while the long job takes the SMs they
+    leave free."""
 
     def __init__(self, memory_budget: int, slice_steps: int = 640, max_jobs: int = 4096,
                  stream=None, clock: Callable[[], float] = time.perf_counter, policy: str = "async",
-                 fill_points: int = 2_000_000, age_priority: bool = True):
+                 fill_points: int = 2_000_000, age_priority: bool = True, order: str = "age"):
         if slice_steps < 2 or slice_steps % 2:
             raise ValueError("slice_steps must be even and >= 2")
         if policy not in ("share", "fill", "priority", "async"):
             raise ValueError("policy is 'share', 'fill', 'priority' or 'async'")
+        if order not in ("age", "remaining") or (order == "remaining" and policy != "async"):
+            raise ValueError("order is 'age' or, with the async policy, 'remaining'")
+        self.order = order
         self.policy = policy
         self.fill_points = int(fill_points)
         self.budget = int(memory_budget)
@@ -289,18 +299,28 @@ class WaveformService:
                 progressed = True
         self._admit()
         pts = 0
-        for rank, rid in enumerate(sorted(self._running, key=lambda q: (self._submitted[q], q))):
+        by_work = self.order == "remaining"
+        if by_work:
+            def rank_key(q):
+                r = self._requests[q]
+                return (self._running[q]["remaining"] * r.nr * r.nth, self._submitted[q], q)
+        else:
+            def rank_key(q):
+                return (self._submitted[q], q)
+        for rank, rid in enumerate(sorted(self._running, key=rank_key)):
             st = self._running[rid]
-            if pts and pts >= self.fill_points:
+            if pts and pts >= self.fill_points and not by_work:
                 break
             r = self._requests[rid]
             pts += r.nr * r.nth
             if st["event"] is None and st["remaining"] > 0:
                 if self.age_priority:
                     # CUDA priorities: smaller numbers are higher, from high (greatest)
-                    # up to low (least); the oldest job gets the greatest
+                    # up to low (least); the first in rank gets the greatest.  By age a
+                    # job is only promoted; by remaining work it also moves down when a
+                    # job with less work arrives
                     want = min(self._prio[1] + rank, self._prio[0])
-                    if want < st["level"]:     # promote, never demote
+                    if want < st["level"] or (by_work and want != st["level"]):
                         st["stream"] = torch.cuda.Stream(priority=want)
                         st["solver"].set_stream(st["stream"])
                         st["level"] = want

@@ -307,3 +307,31 @@ def test_age_priority_can_be_switched_off(fake_cuda):
     run(svc)
     assert all(s.priorities == [0] for s in fake_cuda)   # default-priority streams, never moved
     svc.close()
+
+
+def test_async_by_remaining_work_runs_every_job_and_ranks_by_work(fake_cuda):
+    # a long job admitted first, then short ones: every job advances in every
+    # round (no fill cutoff), the shortest remaining work gets the greatest
+    # priority, and the long job moves down when shorter ones arrive
+    log = []
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), fill_points=64 * 8,
+                            order="remaining")
+    svc.submit(request(steps=400))
+    svc._admit()
+    fake_cuda[0].ticks = log
+    svc.step()                                   # the long job alone: greatest priority
+    assert fake_cuda[0].priorities[-1] == -5
+    for n in (40, 80):
+        svc.submit(request(steps=n))
+    svc._admit()
+    for s in fake_cuda:
+        s.ticks = log
+    svc.step()
+    assert [s.priorities[-1] for s in fake_cuda] == [-3, -5, -4]
+    res = run(svc)
+    assert len(res) == 3 and all(s.closed for s in fake_cuda)
+    # the short jobs finish before the long one although it came first
+    assert max(res[1].finished, res[2].finished) <= res[0].finished
+    with pytest.raises(ValueError):
+        S.WaveformService(memory_budget=1 << 30, policy="fill", order="remaining")
+    svc.close()
