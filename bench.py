@@ -452,8 +452,15 @@ def run_gpu(args):
         line["batched"] = [batch_result(T, "batch_modes", 0.2, "all"), batch_result(T, "template_bank", 0.01, "all"),
                            batch_result(T, "small_bank", 0.2, "all")]
         line["serving"] = serving_result(T, SV, inputs.serving_requests(64, 4.0), slice_steps=640,
-                                         fill_points=2_000_000, memory_gb=200.0, policies=("async",))
+                                         fill_points=2_000_000, memory_gb=200.0, policies=("async", "async-remaining"))
         line["serving"].update(rate_per_s=4.0, step_fraction=1.0, steps="logU[1e3, 1e4]")
+        # a long request on the GPU while short ones arrive: 32 requests at
+        # 4/s, the first an 8192 x 128 job of 1e5 steps
+        line["serving_long_tail"] = serving_result(
+            T, SV, inputs.serving_requests(32, 4.0, long_tail=1, long_steps=(1e5, 1e5), long_grids=((8192, 128),),
+                                           long_weights=None),
+            slice_steps=640, fill_points=2_000_000, memory_gb=200.0, policies=("async-remaining", "async"))
+        line["serving_long_tail"].update(rate_per_s=4.0, steps="logU[1e3, 1e4]; first request 8192x128, 1e5 steps")
     if ws == 1 and not args.no_cpu_baseline:
         per = args.cpu_sample_steps
         upd, times = oracle_rate(per, 1)

@@ -959,12 +959,31 @@ __device__ __forceinline__ void correct_split_tile(const TileIdx &ti, const Step
     };
     if (KO) {
         const double2 *rp = Phi + kr, *rq = Pi + kr;
-        if (colok)
-            stage(tx + 3, phi, pi);
-        else
-            stage(tx + 3, ko_load(rp, j, nth, p.parity), ko_load(rq, j, nth, p.parity));
-        if (tx < 3) stage(tx, ko_load(rp, j0 - 3 + tx, nth, p.parity), ko_load(rq, j0 - 3 + tx, nth, p.parity));
-        if (tx >= TW - 3) stage(tx + 6, ko_load(rp, j + 3, nth, p.parity), ko_load(rq, j + 3, nth, p.parity));
+        // Fast staging when every ghost column of the window reflects a column
+        // of this tile (rows of at least 6 columns whose last tile has at least
+        // 3): the owners write the ghosts (the reflection flips the sign for
+        // odd |m|) and only halo columns inside the row are loaded.  Otherwise
+        // the edge lanes fold every halo column by the pole rule.
+        const bool last = j0 + TW >= nth;
+        const bool fast = nth >= 6 && (last ? j0 <= nth - 3 : j0 + TW + 3 <= nth);
+        if (fast) {
+            if (colok) {
+                stage(tx + 3, phi, pi);
+                const double2 gph = make_double2(p.parity * phi.x, p.parity * phi.y);
+                const double2 gpi = make_double2(p.parity * pi.x, p.parity * pi.y);
+                if (j0 == 0 && j <= 2) stage(2 - j, gph, gpi);                      // column -1 - j
+                if (last && j >= nth - 3) stage(2 * nth - 1 - j - j0 + 3, gph, gpi);  // column 2 nth - 1 - j
+            }
+            if (j0 > 0 && tx < 3) stage(tx, ldcg(rp + j0 - 3 + tx), ldcg(rq + j0 - 3 + tx));
+            if (!last && tx >= TW - 3) stage(tx + 6, ldcg(rp + j + 3), ldcg(rq + j + 3));
+        } else {
+            if (colok)
+                stage(tx + 3, phi, pi);
+            else
+                stage(tx + 3, ko_load(rp, j, nth, p.parity), ko_load(rq, j, nth, p.parity));
+            if (tx < 3) stage(tx, ko_load(rp, j0 - 3 + tx, nth, p.parity), ko_load(rq, j0 - 3 + tx, nth, p.parity));
+            if (tx >= TW - 3) stage(tx + 6, ko_load(rp, j + 3, nth, p.parity), ko_load(rq, j + 3, nth, p.parity));
+        }
     }
     __syncthreads();
     double2 nphi, npi;
