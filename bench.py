@@ -73,8 +73,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # of the split kernels on 8192 x 128, valid for the kernel and launch sources
 # whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(predictor=125.87e6 + 16.53e6, corrector=151.02e6 + 20.32e6,
-                   sources_sha256="9eb8f74b42576d030e6c5ca32ae2089bd46468501bb7f0e1c1cdd4d9d4bb3069")
+NCU_TRAFFIC = dict(predictor=125.86e6 + 16.01e6, corrector=151.04e6 + 19.77e6,
+                   sources_sha256="664b21b44d77376b2ac74d3f0cc46b7c7b1850bb94be2fd3f39d962f2aa2b2d3")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits

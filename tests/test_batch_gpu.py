@@ -269,3 +269,55 @@ def test_mode_batch_at_full_size_equals_individual_runs(teuk, mode):
     B.close()
     for g in solvers:
         g.close()
+
+
+@pytest.mark.parametrize("ctas", [0, 3])
+def test_multi_job_groups_beyond_64_jobs(teuk, ctas):
+    """80 small jobs in mode 0: 65 complex fixed-point jobs with the
+    dissipation (two launch groups: 64 + 1) and five each with real planes,
+    with FP64 Pi rows and without the dissipation (a group each), with one
+    CTA per tile or a persistent grid; every job equals the same job
+    stepped alone, bit for bit."""
+    rng = np.random.default_rng(70)
+    specs = []
+    for q in range(80):
+        a = 0.0 if q % 16 == 0 else float(rng.uniform(0.1, 0.9))   # a = 0: real planes
+        specs.append(dict(nr=int(rng.integers(24, 90)), nth=int(rng.choice([8, 20, 32, 48, 64, 100])), a=a,
+                          s=-2, m=int(rng.integers(1, 4)), steps=int(rng.integers(3, 40)),
+                          src=dict(r0=6.0, sigma=1.0) if q % 2 else None, ext=(5.0, 3) if q % 4 == 1 else None,
+                          eps=0.0 if q % 16 == 4 else 1.0, fx=0 if q % 16 == 8 else 1))
+
+    def build(q):
+        j = specs[q]
+        g, _ = make(teuk, j, 1000 + q)
+        if not j["fx"]:
+            g.set_option(teuk.TEUK_OPT_FIXED_POINT, 0)
+        return g, j
+
+    alone = []
+    for q in range(len(specs)):
+        g, j = build(q)
+        g.step(j["steps"])
+        alone.append(collect(g, j))
+        g.close()
+    B = teuk.Batch()
+    B.set_option(teuk.TEUK_OPT_BATCH_CTAS, ctas)
+    B.set_option(teuk.TEUK_OPT_BATCH_MODE, 0)
+    solvers = []
+    for q in range(len(specs)):
+        g, j = build(q)
+        solvers.append((g, j))
+        B.add(g, j["steps"])
+    # 2 launches per group per time step plus one counter update per slice:
+    # five groups
+    assert B.launches_for(2) == 2 * 2 * 5 + 1
+    while B.step(10 ** 6):
+        pass
+    B.sync()
+    for (g, j), ref in zip(solvers, alone):
+        assert g.step_count == j["steps"]
+        for x, y in zip(collect(g, j), ref):
+            np.testing.assert_array_equal(x, y)
+    B.close()
+    for g, _ in solvers:
+        g.close()
