@@ -321,3 +321,57 @@ def test_multi_job_groups_beyond_64_jobs(teuk, ctas):
     B.close()
     for g, _ in solvers:
         g.close()
+
+
+def test_template_bank_at_full_size_every_launch_form(teuk):
+    """The template-bank workload at its full grid sizes: 256 seeded jobs, a
+    in [0, 0.95], r0 in [6, 20], m = 1..4, 2048..16384 x 64..256 (304 M grid
+    points, 83 GB resident), with the source, waveform extraction and the
+    workload's dissipation; uneven short step counts (6..12) so that jobs
+    leave at slice boundaries after odd slices.  Per-job launches, multi-job
+    launches (one CTA per tile: four launch groups of 64) and the persistent
+    multi-job launches each give every job the same final state, bit for bit
+    (compared by digest), as the job stepped alone."""
+    import hashlib
+    T = teuk
+    rule = inputs.STEP_RULE
+    rmin, rmax = -100.0, 600.0
+    jobs = inputs.template_bank(256)
+    for q, j in enumerate(jobs):
+        j["sigma"] = max(0.05, 2.0 * 700.0 / (j["nr"] - 1))
+        j["steps"] = 6 + q % 7
+        j["dt"] = T.stable_dt(j["nr"], j["nth"], rmin, rmax, j["a"], j["s"], j["m"], rule["c_r"], rule["c_theta"])
+
+    def make_job(j):
+        g = T.Solver(j["nr"], j["nth"], rmin, rmax, j["dt"], j["a"], j["s"], j["m"])
+        g.set_dissipation(rule["eps"])
+        g.set_source(r0=j["r0"], sigma=j["sigma"])
+        g.set_extraction(500.0, 3, capacity=8)
+        return g
+
+    def digest(g):
+        phi, pi = g.state()
+        return hashlib.sha256(phi.tobytes() + pi.tobytes() + g.extract()[1].tobytes()).hexdigest()
+
+    alone = []
+    for j in jobs:
+        g = make_job(j)
+        g.step(j["steps"])
+        alone.append(digest(g))
+        g.close()
+    for mode, ctas in ((1, 0), (0, 0), (0, 8)):
+        B = T.Batch()
+        B.set_option(T.TEUK_OPT_BATCH_CTAS, ctas)
+        B.set_option(T.TEUK_OPT_BATCH_MODE, mode)
+        solvers = [make_job(j) for j in jobs]
+        for g, j in zip(solvers, jobs):
+            B.add(g, j["steps"])
+        while B.step(10 ** 6):
+            pass
+        B.sync()
+        got = [digest(g) for g in solvers]
+        B.close()
+        for g in solvers:
+            g.close()
+        bad = [q for q in range(len(jobs)) if got[q] != alone[q]]
+        assert not bad, (mode, ctas, bad[:10])
