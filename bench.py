@@ -57,6 +57,8 @@ FLOPS_DISSIPATION_POINT = 38
 BYTES_PER_UPDATE_ALG = 64
 # Nominal FP64 rate of GB300 (152 SMs x 2 FP64 FMA/clk/SM x 2 flops x 2.07 GHz).
 FP64_PEAK_FLOPS = 1.25e12
+# Instruction issue: 4 warp schedulers per SM, one warp instruction each per clock.
+ISSUE_PER_CLK_SM = 4
 # How the kernels execute that work: the Phi rows and the sums tau, sigma on
 # the FP64 pipe (20 instructions per update, adds and multiplies issued as
 # FMAs), the Pi rows as fixed-point sums of 38 exact integer products per
@@ -74,6 +76,8 @@ NUM_SMS = 152
 # of the split kernels on 8192 x 128, valid for the kernel and launch sources
 # whose SHA-256 is recorded here; reported as null otherwise.
 NCU_TRAFFIC = dict(predictor=125.86e6 + 16.01e6, corrector=151.04e6 + 19.77e6,
+                   # warp instructions per launch (smsp__inst_executed.sum), same capture
+                   predictor_inst=30.403100e6, corrector_inst=48.021326e6,
                    sources_sha256="664b21b44d77376b2ac74d3f0cc46b7c7b1850bb94be2fd3f39d962f2aa2b2d3")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
@@ -335,6 +339,19 @@ def run_gpu(args):
                     step_in_graph=dict(ms=per_launch_s * 1e3,
                                        tflops=flops_update * upd_per_launch / per_launch_s / 1e12),
                     hbm_alg_gbs=BYTES_PER_UPDATE_ALG * upd_per_launch / per_launch_s / 1e9)
+    # the binding resource of this integer-heavy path: instruction issue, from
+    # the warp instructions per launch of the ncu capture (valid while the
+    # kernel sources hash to the captured version) over the CUDA-event times
+    if same_src:
+        inst = {"lw_predict_split": NCU_TRAFFIC["predictor_inst"], "lw_correct_split": NCU_TRAFFIC["corrector_inst"]}
+        clk = 2.07e9
+        roofline["issue"] = dict(
+            unit="warp instructions/s", peak=NUM_SMS * ISSUE_PER_CLK_SM * clk,
+            peak_source="152 SMs x 4 schedulers x 1 warp instruction/clk x 2.07 GHz",
+            kernels={k: dict(warp_instructions=inst[k], achieved=inst[k] / (kern[k][1] / 1e3),
+                             frac=inst[k] / (kern[k][1] / 1e3) / (NUM_SMS * ISSUE_PER_CLK_SM * clk)) for k in inst},
+            thread_instructions_per_update=32 * (inst["lw_predict_split"] / ((nr - 1) * nth) +
+                                                 inst["lw_correct_split"] / ((nr - 2) * nth)))
     # secondary roof: HBM (not binding here), against the measured copy bandwidth
     hbm_peak, hbm_src = measured_hbm_gbs()
     dram_step = (NCU_TRAFFIC["predictor"] + NCU_TRAFFIC["corrector"]) if same_src else None
