@@ -344,12 +344,12 @@ def run_gpu(args):
     # kernel sources hash to the captured version) over the CUDA-event times
     if same_src:
         inst = {"lw_predict_split": NCU_TRAFFIC["predictor_inst"], "lw_correct_split": NCU_TRAFFIC["corrector_inst"]}
-        clk = 2.07e9
+        issue_peak = NUM_SMS * ISSUE_PER_CLK_SM * 2.07e9
         roofline["issue"] = dict(
-            unit="warp instructions/s", peak=NUM_SMS * ISSUE_PER_CLK_SM * clk,
+            unit="warp instructions/s", peak=issue_peak,
             peak_source="152 SMs x 4 schedulers x 1 warp instruction/clk x 2.07 GHz",
             kernels={k: dict(warp_instructions=inst[k], achieved=inst[k] / (kern[k][1] / 1e3),
-                             frac=inst[k] / (kern[k][1] / 1e3) / (NUM_SMS * ISSUE_PER_CLK_SM * clk)) for k in inst},
+                             frac=inst[k] / (kern[k][1] / 1e3) / issue_peak) for k in inst},
             thread_instructions_per_update=32 * (inst["lw_predict_split"] / ((nr - 1) * nth) +
                                                  inst["lw_correct_split"] / ((nr - 2) * nth)))
     # secondary roof: HBM (not binding here), against the measured copy bandwidth

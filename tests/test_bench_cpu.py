@@ -89,3 +89,17 @@ def test_issue_roofline_constants():
     corr = 32 * bench.NCU_TRAFFIC["corrector_inst"] / (8190 * 128)
     assert round(pred) == 928 and round(corr) == 1466
     assert bench.NUM_SMS * bench.ISSUE_PER_CLK_SM * 2.07e9 == pytest.approx(1.2586e12, rel=1e-4)
+
+
+def test_run_gpu_does_not_rebind_the_clock_sampler():
+    # run_gpu samples clocks with the object it binds to `clk` before the
+    # timed region; no later assignment may rebind that name
+    import ast
+    import inspect
+    import bench
+    tree = ast.parse(inspect.getsource(bench.run_gpu))
+    targets = [t.id for node in ast.walk(tree) if isinstance(node, (ast.Assign, ast.AugAssign))
+               for t in (node.targets if isinstance(node, ast.Assign) else [node.target]) if isinstance(t, ast.Name)]
+    withs = [it.optional_vars.id for node in ast.walk(tree) if isinstance(node, ast.With) for it in node.items
+             if isinstance(it.optional_vars, ast.Name)]
+    assert targets.count("clk") + withs.count("clk") == 1, (targets.count("clk"), withs.count("clk"))
