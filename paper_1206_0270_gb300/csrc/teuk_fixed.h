@@ -7,8 +7,8 @@
 // integer pipe:
 //
 //   * each operand is split into its 53-bit significand m and exponent e,
-//     value = m 2^(e - 1075) (subnormals: no hidden bit, e = 1, which is
-//     exact; zeros never set the frame);
+//     value = m 2^(e - 1075) (subnormals and zero fields: no hidden bit,
+//     e = 1, which is exact; a zero coefficient never sets the frame);
 //   * each product m_c m_x (at most 106 bits) is formed exactly with four
 //     32 x 32 -> 64-bit multiply-adds;
 //   * all products are aligned to the largest product exponent E and
@@ -22,13 +22,14 @@
 // error of the same sum formed by FP64 fused multiply-adds (each of its n
 // roundings is relative to a partial sum).  Integer addition is exact and
 // associative, so the result does not depend on the order of the terms, and
-// terms whose coefficient or field is zero change nothing, not even the
-// frame.
+// terms whose coefficient or field is zero add nothing; a zero coefficient
+// does not take part in the choice of the frame either.
 //
 // The sum reports failure, and the caller evaluates it with FP64 FMAs
 // instead, when an input is not finite or the result is below 2^-823 (there
-// a product with a subnormal field could have set the frame; coefficients of
-// the scheme are far below the 2^170 this bound allows) or would overflow.
+// a product with a subnormal or zero field, counted at the exponent of the
+// smallest subnormal, could have set the frame; coefficients of the scheme
+// are far below the 2^170 this bound allows) or would overflow.
 //
 // Everything here is plain integer arithmetic on host and device, so the
 // same code is tested on the CPU against exact rational arithmetic.
@@ -100,11 +101,10 @@ TEUK_FX_HD Fx fx_unpack(double v)
     const uint64_t u = fx_bits(v);
     const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
     const uint32_t eraw = (hi >> 20) & 0x7FFu;
-    const bool zero = ((hi & 0x7FFFFFFFu) | lo) == 0;
     Fx o;
     o.mhi = (hi & 0xFFFFFu) | (eraw ? 0x100000u : 0u);
     o.mlo = lo;
-    o.e = zero ? -4096 : (eraw ? (int)eraw : 1);
+    o.e = eraw ? (int)eraw : 1;
     o.neg = hi >> 31;
     o.braw = eraw;
     return o;

@@ -17,7 +17,10 @@ __host__ __device__ void dot_case(const double *c, const double *x, const unsign
     Fx C[N], X[N];
     uint32_t F[N];
     for (int k = 0; k < N; ++k) {
-        C[k] = fx_unpack(c[k]);
+        // coefficients as the kernels split them (normal or zero; others as fields)
+        const uint64_t cb = fx_bits(c[k]) & 0x7FFFFFFFFFFFFFFFull;
+        const bool normal_or_zero = cb == 0 || (cb >= 0x0010000000000000ull && cb < 0x7FF0000000000000ull);
+        C[k] = normal_or_zero ? fx_unpack_coef(c[k]) : fx_unpack(c[k]);
         X[k] = fx_unpack(x[k]);
         F[k] = flip[k] & 1u;
     }
