@@ -257,12 +257,13 @@ static int rebuild(teuk_batch *b)
     }
     for (auto &g : b->groups) {
         g.ctas = 0;
+        g.pred.sbuf_words = g.corr.sbuf_words = (int)(g.smem / sizeof(double2));
         if (b->ctas_request > 0) {  // persistent: as many CTAs as stay resident, at most the request per SM
             int per_sm = b->ctas_request;
             for (int w = 0; w < 2; ++w) {
                 int n = 0;
                 BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_kernel_ptr(w, g.real, g.fx, g.ko),
-                                                                  g.block, g.smem));
+                                                                  g.block, 2 * g.smem));
                 per_sm = std::min(per_sm, std::max(1, n));
             }
             g.ctas = sms * per_sm;

@@ -130,7 +130,8 @@ struct JobDesc {
 constexpr int kMultiMaxJobs = 64;  // 64 x 368-byte descriptors: 23.8 KB of the 32 KB parameter space
 struct MultiArgs {
     int njobs;
-    int ntiles;  // off[njobs]
+    int ntiles;      // off[njobs]
+    int sbuf_words;  // shared rows of one tile (double2 words); the persistent form alternates two sets
     int off[kMultiMaxJobs + 1];
     JobDesc jobs[kMultiMaxJobs];
 };
@@ -182,7 +183,8 @@ cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long l
 
 // Multi-job kernels: which = 0 predictor, 1 corrector; `ctas` = 0 gives one
 // CTA per tile, otherwise a persistent grid of min(ctas, tiles) CTAs that
-// loop over the tiles.  real / fixed_point / ko select the instantiation and
+// loop over the tiles.  `smem` is one tile's shared rows (a.sbuf_words
+// double2 words); the persistent form takes twice that.  real / fixed_point / ko select the instantiation and
 // must match every job of `a`.
 cudaError_t launch_step_multi(const MultiArgs &a, int which, int real, int fixed_point, int ko, int block,
                               size_t smem, int ctas, int k, cudaStream_t st, bool pdl);

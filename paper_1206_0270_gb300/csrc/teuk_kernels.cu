@@ -855,11 +855,12 @@ int split_rows_per_block(int nth, int fixed_point)
 // multi-job kernels from the job table.
 struct TileIdx {
     int TW, R, tx, ty, rb, tt;
+    int sbuf;  // offset (double2 words) of the tile's shared rows in the dynamic shared memory
 };
 __device__ __forceinline__ TileIdx tile_of_launch()
 {
     return TileIdx{(int)blockDim.x, (int)blockDim.y, (int)threadIdx.x, (int)threadIdx.y, (int)blockIdx.x,
-                   (int)blockIdx.y};
+                   (int)blockIdx.y, 0};
 }
 
 // SIGNAL: end with the programmatic-launch signal (the multi-job kernels
@@ -869,7 +870,8 @@ __device__ __forceinline__ void predict_split_tile(const TileIdx &ti, const Step
                                                    const double2 *__restrict__ Pi, double2 *__restrict__ PhiH,
                                                    double2 *__restrict__ PiH, int k)
 {
-    extern __shared__ double2 smem[];
+    extern __shared__ double2 smem_all[];
+    double2 *smem = smem_all + ti.sbuf;
     const int nth = p.nth, TW = ti.TW, tx = ti.tx;
     const int j0 = ti.tt * TW, j = j0 + tx;
     const bool colok = j < nth;
@@ -912,7 +914,8 @@ __device__ __forceinline__ void correct_split_tile(const TileIdx &ti, const Step
                                                    const double2 *__restrict__ PiH, double2 *__restrict__ PhiO,
                                                    double2 *__restrict__ PiO, int k)
 {
-    extern __shared__ double2 smem[];
+    extern __shared__ double2 smem_all[];
+    double2 *smem = smem_all + ti.sbuf;
     const int nth = p.nth, TW = ti.TW, tx = ti.tx;
     const int j0 = ti.tt * TW, j = j0 + tx;
     const bool colok = j < nth;
@@ -1159,27 +1162,31 @@ __device__ __forceinline__ int multi_first_job(const MultiArgs &a, int b)
     return lo;
 }
 
-__device__ __forceinline__ TileIdx multi_tile(const JobDesc &J, int t)
+__device__ __forceinline__ TileIdx multi_tile(const JobDesc &J, int t, int sbuf)
 {
     const int tw = J.tw, tiles = J.tiles, rb = t / tiles;
     const int ty = (int)threadIdx.x / tw;
-    return TileIdx{tw, J.rows, (int)threadIdx.x - ty * tw, ty, rb, t - rb * tiles};
+    return TileIdx{tw, J.rows, (int)threadIdx.x - ty * tw, ty, rb, t - rb * tiles, sbuf};
 }
 
-// PERSIST: loop over tiles b, b + G, ...; otherwise the grid has one CTA per
-// tile (fewer registers live across the tile code).
+// PERSIST: loop over tiles b, b + G, ..., alternating two sets of shared
+// rows (a.sbuf_words apart): the tile code's own barrier keeps every warp
+// within one tile of the others, so a warp that starts the next tile never
+// overwrites rows another warp still reads, and no barrier is needed between
+// tiles.  Otherwise the grid has one CTA per tile (fewer registers live
+// across the tile code).
 template <bool REAL, bool FX, bool PERSIST>
 __device__ __forceinline__ void predict_multi_body(const MultiArgs &a, int k)
 {
     int q = multi_first_job(a, blockIdx.x);
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
         while (PERSIST && q + 1 < a.njobs && a.off[q + 1] <= tile) ++q;
         const JobDesc &J = a.jobs[q];
         const int from = J.cur ^ (k & 1);
-        predict_split_tile<REAL, FX, false>(multi_tile(J, tile - a.off[q]), J.p, J.phi[from], J.pi[from], J.phiH,
-                                            J.piH, k);
+        predict_split_tile<REAL, FX, false>(multi_tile(J, tile - a.off[q], (it & 1) * a.sbuf_words), J.p,
+                                            J.phi[from], J.pi[from], J.phiH, J.piH, k);
         if (!PERSIST) break;
-        if (tile + (int)gridDim.x < a.ntiles) __syncthreads();  // the next tile reuses the shared rows
     }
     allow_dependents();  // after the CTA's last store
 }
@@ -1188,14 +1195,15 @@ template <bool REAL, bool FX, bool KO, bool PERSIST>
 __device__ __forceinline__ void correct_multi_body(const MultiArgs &a, int k)
 {
     int q = multi_first_job(a, blockIdx.x);
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
         while (PERSIST && q + 1 < a.njobs && a.off[q + 1] <= tile) ++q;
         const JobDesc &J = a.jobs[q];
         const int from = J.cur ^ (k & 1);
-        correct_split_tile<REAL, FX, KO, false>(multi_tile(J, tile - a.off[q]), J.p, J.phi[from], J.pi[from],
-                                                J.phiH, J.piH, J.phi[from ^ 1], J.pi[from ^ 1], k);
+        correct_split_tile<REAL, FX, KO, false>(multi_tile(J, tile - a.off[q], (it & 1) * a.sbuf_words), J.p,
+                                                J.phi[from], J.pi[from], J.phiH, J.piH, J.phi[from ^ 1],
+                                                J.pi[from ^ 1], k);
         if (!PERSIST) break;
-        if (tile + (int)gridDim.x < a.ntiles) __syncthreads();
     }
     allow_dependents();
 }
@@ -1265,14 +1273,14 @@ cudaError_t launch_step_multi(const MultiArgs &a, int which, int real, int fixed
                               size_t smem, int ctas, int k, cudaStream_t st, bool pdl)
 {
     if (a.ntiles <= 0) return cudaSuccess;
-    const bool persist = ctas > 0 && ctas < a.ntiles;
+    const bool persist = ctas > 0 && ctas < a.ntiles;  // then smem holds two sets of rows
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(persist ? ctas : a.ntiles);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = persist ? 2 * smem : smem;
     cfg.stream = st;
     cfg.attrs = pdl ? attr : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;
