@@ -75,10 +75,10 @@ NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # of the split kernels on 8192 x 128, valid for the kernel and launch sources
 # whose SHA-256 is recorded here; reported as null otherwise.
-NCU_TRAFFIC = dict(predictor=125.86e6 + 15.71e6, corrector=151.04e6 + 19.24e6,
+NCU_TRAFFIC = dict(predictor=125.86e6 + 15.71e6, corrector=151.04e6 + 19.35e6,
                    # warp instructions per launch (smsp__inst_executed.sum), same capture
                    predictor_inst=28.502788e6, corrector_inst=46.80953e6,
-                   sources_sha256="64135bf23dc2b487c58117cf1c911b940e7a5d40a41f516218177233c573b8b6")
+                   sources_sha256="e42d4171986babf4c40c5f3cc4cae57cc09637cc47289f9af9c08d1a57a25942")
 TRAFFIC_SOURCES = ["paper_1206_0270_gb300/csrc/teuk_kernels.cu",   # kernels and their launchers
                    "paper_1206_0270_gb300/csrc/teuk_fixed.h",      # their arithmetic
                    "paper_1206_0270_gb300/csrc/teuk_internal.h",   # parameter layout, thread limits
