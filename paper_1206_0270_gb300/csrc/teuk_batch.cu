@@ -57,7 +57,7 @@ struct teuk_batch {
     bool layout_dirty = true;
     cudaGraphExec_t graph = nullptr;
     int pdl = 1, chunk = 64;
-    int mode = 1;                     // 0: one persistent launch for all jobs; 1: per-job launches
+    int mode = 1;                     // 0: multi-job launches per group of jobs; 1: per-job launches
     cudaEvent_t fork = nullptr;       // per-job launches: the slice may start
     std::string err;
 };
