@@ -478,6 +478,14 @@ def run_gpu(args):
                                            long_weights=None),
             slice_steps=640, fill_points=2_000_000, memory_gb=200.0, policies=("async-remaining", "async"))
         line["serving_long_tail"].update(rate_per_s=4.0, steps="logU[1e3, 1e4]; first request 8192x128, 1e5 steps")
+        # many small requests at once (overload): 128 requests at 200/s on
+        # 256..512 x 16..32 grids, 2e3..8e3 steps each
+        small = dict(grids=((256, 16), (256, 32), (512, 16), (512, 32)), grid_weights=(1, 1, 1, 1),
+                     step_range=(2e3, 8e3))
+        line["serving_small"] = serving_result(
+            T, SV, inputs.serving_requests(128, 200.0, **small), slice_steps=640, fill_points=2_000_000,
+            memory_gb=200.0, policies=("fill+multi", "share+multi", "async"))
+        line["serving_small"].update(rate_per_s=200.0, grids="256..512 x 16..32", steps="logU[2e3, 8e3]")
     if ws == 1 and not args.no_cpu_baseline:
         per = args.cpu_sample_steps
         upd, times = oracle_rate(per, 1)
@@ -679,10 +687,13 @@ def serving_result(T, S, raw, *, slice_steps, fill_points, memory_gb, policies=(
     budget = int(memory_gb * 2 ** 30)
 
     def served(reqs, policy):
-        # "async-remaining": the async policy ranking jobs by remaining work
-        name, _, order = policy.partition("-")
+        # "async-remaining": the async policy ranking jobs by remaining work;
+        # "share+multi": the share policy with multi-job launches (batch mode 0)
+        base, _, multi = policy.partition("+")
+        name, _, order = base.partition("-")
         svc = S.WaveformService(memory_budget=budget, slice_steps=slice_steps, policy=name,
-                                fill_points=fill_points, order=order or "age")
+                                fill_points=fill_points, order=order or "age",
+                                batch_mode=0 if multi == "multi" else None)
         for r in reqs:
             svc.submit(r)
         torch.cuda.synchronize()

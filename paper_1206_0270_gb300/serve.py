@@ -110,11 +110,16 @@ class WaveformService:
     that rank (the least work highest; a job moves down when a smaller one
     arrives), so short requests pass a long job that is already running
     (shortest remaining work first) while the long job takes the SMs they
-    leave free."""
+    leave free.
+    batch_mode (the common-slice policies "share", "fill", "priority"): the
+    batch's launch form, TEUK_OPT_BATCH_MODE; 0 steps every running job with
+    one multi-job launch per kernel and time step, which serves many small
+    grids far faster than a launch per job (default: per-job launches)."""
 
     def __init__(self, memory_budget: int, slice_steps: int = 640, max_jobs: int = 4096,
                  stream=None, clock: Callable[[], float] = time.perf_counter, policy: str = "async",
-                 fill_points: int = 2_000_000, age_priority: bool = True, order: str = "age"):
+                 fill_points: int = 2_000_000, age_priority: bool = True, order: str = "age",
+                 batch_mode: Optional[int] = None):
         if slice_steps < 2 or slice_steps % 2:
             raise ValueError("slice_steps must be even and >= 2")
         if policy not in ("share", "fill", "priority", "async"):
@@ -132,6 +137,8 @@ class WaveformService:
         self._t0 = clock()
         self.batch = T.Batch(stream=stream)
         self.batch.set_option(T.TEUK_OPT_GRAPH_CHUNK, 64 if self.slice % 64 == 0 else 2)
+        if batch_mode is not None:   # the common-slice policies' launch form (teuk_batch)
+            self.batch.set_option(T.TEUK_OPT_BATCH_MODE, int(batch_mode))
         self._queue: list = []      # heap of (arrival, rid)
         self._requests: dict = {}
         self._submitted: dict = {}

@@ -61,11 +61,15 @@ class FakeSolver:
 
 
 class FakeBatch:
+    made = []
+
     def __init__(self, stream=None):
         self.jobs, self.next, self.ticks = {}, 0, 0
+        self.options = {}
+        FakeBatch.made.append(self)
 
     def set_option(self, option, value):
-        pass
+        self.options[option] = value
 
     def add(self, solver, steps):
         jid = self.next
@@ -96,6 +100,7 @@ class FakeBatch:
 
 class FakeLib:
     TEUK_OPT_GRAPH_CHUNK = 4
+    TEUK_OPT_BATCH_MODE = 6
     Solver = FakeSolver
     Batch = FakeBatch
     made = []
@@ -334,4 +339,18 @@ def test_async_by_remaining_work_runs_every_job_and_ranks_by_work(fake_cuda):
     assert max(res[1].finished, res[2].finished) <= res[0].finished
     with pytest.raises(ValueError):
         S.WaveformService(memory_budget=1 << 30, policy="fill", order="remaining")
+    svc.close()
+
+
+def test_batch_mode_option_reaches_the_batch(fake):
+    # the common-slice policies can step their jobs with multi-job launches
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), policy="share", batch_mode=0)
+    assert FakeBatch.made[-1].options == {FakeLib.TEUK_OPT_GRAPH_CHUNK: 2, FakeLib.TEUK_OPT_BATCH_MODE: 0}
+    for n in (30, 50):
+        svc.submit(request(steps=n))
+    res = run(svc)
+    assert sorted(len(r.t) for r in res.values()) == [3, 5]
+    svc.close()
+    svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), policy="share")
+    assert FakeLib.TEUK_OPT_BATCH_MODE not in FakeBatch.made[-1].options
     svc.close()

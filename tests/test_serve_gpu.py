@@ -39,15 +39,18 @@ def run_alone(S, r):
     return res[rid]
 
 
-@pytest.mark.parametrize("policy,fill", [("share", 0), ("fill", 60000), ("fill", 1), ("priority", 60000),
-                                         ("async", 60000), ("async", 1)])
-def test_results_same_alone_and_in_the_mix(serve, policy, fill):
+@pytest.mark.parametrize("policy,fill,mode", [("share", 0, None), ("fill", 60000, None), ("fill", 1, None),
+                                              ("priority", 60000, None), ("async", 60000, None),
+                                              ("async", 1, None), ("share", 0, 0), ("fill", 60000, 0)])
+def test_results_same_alone_and_in_the_mix(serve, policy, fill, mode):
+    # mode 0: the common slices step the jobs with multi-job launches
     S = serve
     rs = reqs(S) + [S.Request(a=0.2, s=-2, m=2, nr=100, nth=8, steps=0, sigma=3.0, rstar_ext=10.0)]
     alone = [run_alone(S, r) for r in rs]
     # the mix: a budget that fits about two jobs at a time, staggered arrivals
     budget = 2 * S.footprint_bytes(rs[2], 64)
-    svc = S.WaveformService(memory_budget=budget, slice_steps=64, policy=policy, fill_points=fill)
+    svc = S.WaveformService(memory_budget=budget, slice_steps=64, policy=policy, fill_points=fill,
+                            batch_mode=mode)
     ids = []
     for k, r in enumerate(rs):
         r2 = S.Request(**{**r.__dict__, "arrival": 0.002 * k})
