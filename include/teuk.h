@@ -402,7 +402,10 @@ int teuk_fixed_dot(int on_device, int nterms, long count, const double *c, const
  * exact integer sum: the seven values truncated to units of 2^(F-1079), F
  * the largest biased exponent among them (each loses less than one unit; the
  * largest keeps its 53 bits), rounded once to FP64 (error <= 2^-50 max|u_q|
- * + 2^-53 |D6|); a non-finite value gives NaN.
+ * + 2^-53 |D6|); a non-finite value gives NaN.  That rounded D6 enters Phi's
+ * FP64 row; in Pi's fixed-point sum the term (-eps/64) D6 enters unrounded
+ * when eps/64 is a power of two (the integer sum shifted to the sum's
+ * frame), and as the product of -eps/64 with the rounded D6 otherwise.
  *
  * teuk_fixed_d6 evaluates that arithmetic for `count` windows of seven
  * values, u[7 i + q] = u_{j-3+q}: out[i] = D6.  on_device = 0 runs the host

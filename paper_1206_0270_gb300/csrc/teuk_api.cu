@@ -312,6 +312,7 @@ extern "C" int teuk_create(const teuk_grid *g, double a, int s, int m, void *cud
     p.parity = h->parity;
     p.k0 = 1.0; p.k1 = 0.0; p.k2 = 0.0; p.k3 = 0.0;
     p.kd = 0.0;
+    p.kd_shift = StepParams::kNotPow2;
     h->su = su;
     p.pred = PredPlanes{su.pa, su.pb, su.eb, su.KAp, su.KCp, su.P1, su.Q1, su.Q2};
     p.corr = CorrPlanes{su.tb, su.nt2, su.KAc, su.KCc, su.R1, su.R3, su.R4};
@@ -646,6 +647,11 @@ extern "C" int teuk_set_dissipation(teuk_handle *h, double eps)
     p.k2 = -6.0 * eps / 64.0;
     p.k3 = eps / 64.0;
     p.kd = -eps / 64.0;
+    {
+        int ex = 0;
+        const double fr = std::frexp(eps / 64.0, &ex);  // eps/64 = fr 2^ex, fr in [0.5, 1)
+        p.kd_shift = (eps > 0.0 && fr == 0.5) ? ex - 1 : StepParams::kNotPow2;
+    }
     h->eps = eps;
     if (h->variant == 0 && h->nth <= kFusedMaxNth) choose_launch(h, h->rows_per_block);  // occupancy depends on it
     return TEUK_OK;

@@ -88,6 +88,18 @@ TEUK_FX_HD uint64_t fx_shr(uint64_t p, uint32_t s)
 #endif
 }
 
+// floor(v / 2^s) for any s >= 0 (PTX shr.s64 clamps the count at 64)
+TEUK_FX_HD long long fx_sar(long long v, uint32_t s)
+{
+#ifdef __CUDA_ARCH__
+    long long r;
+    asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(s));
+    return r;
+#else
+    return v >> (s > 63u ? 63u : s);
+#endif
+}
+
 // An FP64 number split for the fixed-point sums.
 struct Fx {
     uint32_t mhi, mlo;  // significand: high 21 bits (hidden bit included for normal numbers), low 32 bits
@@ -142,12 +154,16 @@ TEUK_FX_HD uint64_t fx_prod47(const Fx &c, const Fx &x)
 
 // *out = sum_k (-1)^flip[k] c[k] x[k] for N <= 16 terms.  Returns false
 // (with *out unspecified) when the caller must use FP64 arithmetic instead.
-template <int N>
-TEUK_FX_HD bool fx_dot(const Fx *c, const Fx *x, const uint32_t *flip, double *out)
+// With EXTRA, one more term enters already formed: P 2^(TP - 2103), |P| <
+// 2^59 like a truncated product, P = 0 with a very negative TP when it is
+// zero (at most 15 product terms then).
+template <int N, bool EXTRA = false>
+TEUK_FX_HD bool fx_dot(const Fx *c, const Fx *x, const uint32_t *flip, double *out, long long P = 0,
+                       int TP = -100000)
 {
-    static_assert(N >= 1 && N <= 16, "at most 16 terms fit the 64-bit accumulator");
+    static_assert(N >= 1 && N + (EXTRA ? 1 : 0) <= 16, "at most 16 terms fit the 64-bit accumulator");
     int T[N];
-    int E = 0;
+    int E = EXTRA && TP > 0 ? TP : 0;
     uint32_t braw = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -156,7 +172,7 @@ TEUK_FX_HD bool fx_dot(const Fx *c, const Fx *x, const uint32_t *flip, double *o
         braw = c[k].braw > braw ? c[k].braw : braw;
         braw = x[k].braw > braw ? x[k].braw : braw;
     }
-    uint64_t acc = 0;  // two's complement, units of 2^(E - 2103)
+    uint64_t acc = EXTRA ? (uint64_t)fx_sar(P, (uint32_t)(E - TP)) : 0;  // two's complement, units of 2^(E - 2103)
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const uint64_t v = fx_shr(fx_prod47(c[k], x[k]), (uint32_t)(E - T[k]));
@@ -216,17 +232,6 @@ TEUK_FX_HD FxP fx_prep(double x)
     return o;
 }
 
-// floor(v / 2^s) for any s >= 0 (PTX shr.s64 clamps the count at 64)
-TEUK_FX_HD long long fx_sar(long long v, uint32_t s)
-{
-#ifdef __CUDA_ARCH__
-    long long r;
-    asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(s));
-    return r;
-#else
-    return v >> (s > 63u ? 63u : s);
-#endif
-}
 
 // RN(D 2^k) for |D| < 2^63 and D 2^k below the FP64 overflow threshold,
 // subnormal results included.
@@ -260,19 +265,34 @@ TEUK_FX_HD double fx_ldexp_rn(long long D, int k)
     return fx_double(r | (neg << 63));
 }
 
-// D6 of seven prepared values p[0..6] (p[3] the centre).
-TEUK_FX_HD double fx_d6(const FxP *p)
+// The exact integer sum of D6 before its rounding: D6 = D 2^(F - 1079)
+// (F = 2047: an input was not finite).
+struct FxI {
+    long long D;
+    int F;
+};
+
+TEUK_FX_HD FxI fx_d6_int(const FxP *p)
 {
     int F = p[0].e;
 #pragma unroll
     for (int q = 1; q < 7; ++q) F = p[q].e > F ? p[q].e : F;
-    if (F >= 2047) return fx_double(0x7FF8000000000000ull);
     long long w[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) w[q] = fx_sar(p[q].v, (uint32_t)(F - p[q].e));
-    const long long D = 20 * w[3] - 15 * (w[2] + w[4]) + 6 * (w[1] + w[5]) - (w[0] + w[6]);
-    return fx_ldexp_rn(D, F - 1079);
+    FxI r;
+    r.D = 20 * w[3] - 15 * (w[2] + w[4]) + 6 * (w[1] + w[5]) - (w[0] + w[6]);
+    r.F = F;
+    return r;
 }
+
+TEUK_FX_HD double fx_d6_round(const FxI &r)
+{
+    return r.F >= 2047 ? fx_double(0x7FF8000000000000ull) : fx_ldexp_rn(r.D, r.F - 1079);
+}
+
+// D6 of seven prepared values p[0..6] (p[3] the centre).
+TEUK_FX_HD double fx_d6(const FxP *p) { return fx_d6_round(fx_d6_int(p)); }
 
 // D6 of seven FP64 values u[0], u[stride], ..., u[6 stride].
 TEUK_FX_HD double fx_d6_values(const double *u, int stride)

@@ -99,6 +99,8 @@ struct StepParams {
     int parity;            // ghost parity of the pole rule (+1 even |m|, -1 odd |m|)
     double k0, k1, k2, k3; // 1 - 20 eps/64, 15 eps/64, -6 eps/64, eps/64 (FP64 arithmetic)
     double kd;             // -eps/64 (fixed-point arithmetic: weight of the exact D6)
+    int kd_shift;          // log2(eps/64) when eps/64 is a power of two, else kNotPow2
+    static constexpr int kNotPow2 = 0x7FFF;
     PredPlanes pred;
     CorrPlanes corr;
     SourceWindow src;

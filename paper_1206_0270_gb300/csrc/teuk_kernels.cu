@@ -342,15 +342,20 @@ struct KoSums {
 };
 struct KoCoef {
     double k0, k1, k2, k3, kd;
+    int kd_shift;
 };
-__device__ __forceinline__ KoCoef ko_of(const StepParams &p) { return KoCoef{p.k0, p.k1, p.k2, p.k3, p.kd}; }
+__device__ __forceinline__ KoCoef ko_of(const StepParams &p)
+{
+    return KoCoef{p.k0, p.k1, p.k2, p.k3, p.kd, p.kd_shift};
+}
 
 // What the corrector needs of the dissipation at one node: the FP64
 // kernels take the pair sums of the old Phi and Pi, the fixed-point kernels
 // the exact sixth differences D6 Phi and D6 Pi (teuk_fixed.h, fx_d6).
 struct KoIn {
     KoSums sphi, spi;
-    double2 dphi, dpi;
+    double2 dphi;    // D6 Phi, rounded (it enters Phi's FP64 row)
+    FxI ipr, ipi;    // D6 Pi, exact (it enters Pi's fixed-point sum unrounded)
 };
 
 // D6 of both components of entries c - 3 .. c + 3 of a row of complex
@@ -366,6 +371,39 @@ __device__ __forceinline__ double2 ko_d6_raw(const double2 *u, int c)
 __device__ __forceinline__ double2 ko_d6_prepared(const FxP *re, const FxP *im, int c)
 {
     return make_double2(fx_d6(re + c - 3), fx_d6(im + c - 3));
+}
+
+// The exact sums (unrounded) of one component of raw values u[0], u[2], ...
+__device__ __forceinline__ FxI ko_d6_int_raw(const double *u)
+{
+    FxP q[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) q[k] = fx_prep(u[2 * k]);
+    return fx_d6_int(q);
+}
+
+// The dissipation's term kd D6 of a Pi row as an addend of its fixed-point
+// sum: P 2^(TP - 2103).  For eps/64 = 2^L the exact sum enters unrounded
+// (P = floor(-D / 16), TP = F + L + 1028); otherwise it is D6 rounded to FP64
+// times kd, formed as a product of the sum.  *bad: an input was not finite.
+__device__ __forceinline__ void ko_pi_term(const FxI &d, const KoCoef &kc, long long *P, int *TP, bool *bad)
+{
+    *P = 0;
+    *TP = -100000;
+    if (d.F >= 2047) {
+        *bad = true;
+        return;
+    }
+    if (d.D == 0) return;
+    if (kc.kd_shift != StepParams::kNotPow2) {
+        *P = fx_sar(-d.D, 4u);
+        *TP = d.F + kc.kd_shift + 1028;
+    } else {
+        const Fx g = fx_unpack(fx_ldexp_rn(d.D, d.F - 1079)), w = fx_unpack_coef(kc.kd);
+        const long long v = (long long)fx_prod47(w, g);
+        *P = (w.neg ^ g.neg) ? -v : v;
+        *TP = w.e + g.e;
+    }
 }
 
 // Theta index j of a row continued past the poles by the ghost rule: the
@@ -408,7 +446,9 @@ __device__ __forceinline__ KoIn ko_from_rows(const double2 *uph, const double2 *
     KoIn ko{};
     if (FX) {
         ko.dphi = ko_d6_raw(uph, c);
-        ko.dpi = ko_d6_raw(upi, c);
+        const double *b = (const double *)(upi + c - 3);
+        ko.ipr = ko_d6_int_raw(b);
+        ko.ipi = ko_d6_int_raw(b + 1);
     } else {
         ko.sphi = ko_sums(uph, c, ops);
         ko.spi = ko_sums(upi, c, ops);
@@ -444,12 +484,11 @@ __device__ __forceinline__ double2 corr_pi_fp64(const CorrCoef &c, const Ops ops
 template <bool REAL, bool FX, bool KO>
 __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, double2 pi, double2 tau,
                                            const HalfStep &hp, const HalfStep &hm, double2 sup, double2 sdn,
-                                           double k0, double2 kdpi)
+                                           double k0, double2 kdpi, const KoIn &ko, const KoCoef &kc)
 {
     if (!FX) return corr_pi_fp64<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, k0, kdpi);
     const Fx one = fx_unpack_coef(1.0);
-    // with KO: Pi enters with weight one and D6 Pi (kdpi) with weight kd (k0)
-    const Fx c0 = one, cg = KO ? fx_unpack_coef(k0) : one;
+    const Fx c0 = one;
     const Fx pr = fx_unpack(pi.x), pim = fx_unpack(pi.y), tr = fx_unpack(tau.x), ti = fx_unpack(tau.y);
     const Fx mr = fx_unpack(hm.pi.x), mi = fx_unpack(hm.pi.y);
     const Fx ar = fx_unpack(hp.phi.x), ai = fx_unpack(hp.phi.y), br = fx_unpack(hm.phi.x), bi = fx_unpack(hm.phi.y);
@@ -460,24 +499,31 @@ __device__ __forceinline__ double2 corr_pi(const CorrCoef &c, const Ops ops, dou
     double2 o;
     bool ok;
     if (KO) {
-        const Fx gr = fx_unpack(kdpi.x), gi = fx_unpack(kdpi.y);
+        // the dissipation's term kd D6 Pi, already formed (ko_pi_term)
+        long long Pr, Pi_;
+        int TPr, TPi;
+        bool bad = false;
+        ko_pi_term(ko.ipr, kc, &Pr, &TPr, &bad);
+        ko_pi_term(ko.ipi, kc, &Pi_, &TPi, &bad);
         if (REAL) {
-            const Fx C[8] = {c0, R1r, nt2, R3r, R4r, KA, KC, cg};
-            const Fx Xr[8] = {pr, tr, mr, ar, br, ur, dr, gr};
-            const Fx Xi[8] = {pim, ti, mi, ai, bi, ui, di, gi};
-            const uint32_t F[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            ok = fx_dot<8>(C, Xr, F, &o.x);
-            ok &= fx_dot<8>(C, Xi, F, &o.y);
+            const Fx C[7] = {c0, R1r, nt2, R3r, R4r, KA, KC};
+            const Fx Xr[7] = {pr, tr, mr, ar, br, ur, dr};
+            const Fx Xi[7] = {pim, ti, mi, ai, bi, ui, di};
+            const uint32_t F[7] = {0, 0, 0, 0, 0, 0, 0};
+            ok = fx_dot<7, true>(C, Xr, F, &o.x, Pr, TPr);
+            ok &= fx_dot<7, true>(C, Xi, F, &o.y, Pi_, TPi);
         } else {
             const Fx R1i = fx_unpack_coef(c.R1.y), R3i = fx_unpack_coef(c.R3.y), R4i = fx_unpack_coef(c.R4.y);
-            const Fx C[11] = {c0, R1r, R1i, nt2, R3r, R3i, R4r, R4i, KA, KC, cg};
-            const Fx Xr[11] = {pr, tr, ti, mr, ar, ai, br, bi, ur, dr, gr};
-            const uint32_t Fr[11] = {0, 0, 1, 0, 0, 1, 0, 1, 0, 0, 0};
-            const Fx Xi[11] = {pim, ti, tr, mi, ai, ar, bi, br, ui, di, gi};
-            const uint32_t Fi[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            ok = fx_dot<11>(C, Xr, Fr, &o.x);
-            ok &= fx_dot<11>(C, Xi, Fi, &o.y);
+            const Fx C[10] = {c0, R1r, R1i, nt2, R3r, R3i, R4r, R4i, KA, KC};
+            const Fx Xr[10] = {pr, tr, ti, mr, ar, ai, br, bi, ur, dr};
+            const uint32_t Fr[10] = {0, 0, 1, 0, 0, 1, 0, 1, 0, 0};
+            const Fx Xi[10] = {pim, ti, tr, mi, ai, ar, bi, br, ui, di};
+            const uint32_t Fi[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            ok = fx_dot<10, true>(C, Xr, Fr, &o.x, Pr, TPr);
+            ok &= fx_dot<10, true>(C, Xi, Fi, &o.y, Pi_, TPi);
         }
+        ok &= !bad;
+        if (!ok) kdpi = make_double2(fx_d6_round(ko.ipr), fx_d6_round(ko.ipi));
     } else if (REAL) {
         const Fx C[7] = {one, R1r, nt2, R3r, R4r, KA, KC};
         const Fx Xr[7] = {pr, tr, mr, ar, br, ur, dr};
@@ -520,8 +566,7 @@ __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, con
     double kw = kc.k0;
     if (KO && FX) {
         nphi = make_double2(fma_rn(kc.kd, ko.dphi.x, phi.x), fma_rn(kc.kd, ko.dphi.y, phi.y));
-        kdpi = ko.dpi;
-        kw = kc.kd;
+        kw = kc.kd;  // kdpi (D6 Pi rounded) is formed only if the FP64 fallback needs it
     } else if (KO) {
         const double2 kd = ko_combine(kc, ko.sphi, ops);
         nphi = make_double2(fma_rn(kc.k0, phi.x, kd.x), fma_rn(kc.k0, phi.y, kd.y));
@@ -531,7 +576,7 @@ __device__ __forceinline__ void correct_c(const CorrCoef &c, double half_dt, con
     rfma(nphi, c.tb, hm.phi);
     rfma(nphi, half_dt, tau);
     *phi_out = nphi;
-    *pi_out = corr_pi<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, kw, kdpi);
+    *pi_out = corr_pi<REAL, FX, KO>(c, ops, pi, tau, hp, hm, sup, sdn, kw, kdpi, ko, kc);
 }
 
 template <bool REAL, bool FX, bool KO>
@@ -993,7 +1038,8 @@ __device__ __forceinline__ void correct_split_tile(const TileIdx &ti, const Step
     KoIn ko{};
     if (KO && FX) {
         ko.dphi = ko_d6_prepared(kp, kp + KW, tx + 3);
-        ko.dpi = ko_d6_prepared(kp + 2 * KW, kp + 3 * KW, tx + 3);
+        ko.ipr = fx_d6_int(kp + 2 * KW + tx);
+        ko.ipi = fx_d6_int(kp + 3 * KW + tx);
     } else if (KO) {
         ko.sphi = ko_sums(uph, tx + 3, ops);
         ko.spi = ko_sums(upi, tx + 3, ops);
