@@ -238,6 +238,16 @@ TEUK_FX_HD FxP fx_prep(double x)
 TEUK_FX_HD double fx_ldexp_rn(long long D, int k)
 {
     if (D == 0) return 0.0;
+#ifdef __CUDA_ARCH__
+    // the hardware conversion rounds D to nearest (ties to even) like the
+    // integer path below; scaling by 2^k is then exact on the exponent field
+    // wherever the result is a normal number
+    {
+        const uint64_t cb = fx_bits(__ll2double_rn(D));
+        const int ef = (int)((cb >> 52) & 0x7FFu) + k;
+        if (ef >= 1 && ef <= 2046) return fx_double(cb + ((uint64_t)(long long)k << 52));
+    }
+#endif
     const uint64_t neg = D < 0 ? 1u : 0u;
     const uint64_t mag = neg ? (uint64_t)0 - (uint64_t)D : (uint64_t)D;
     const int lz = fx_clz64(mag);
