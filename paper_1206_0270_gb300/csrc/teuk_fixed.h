@@ -15,7 +15,10 @@
 //     truncated to units of 2^(E - 2103): the largest product keeps at least
 //     57 bits (2^104 <= m_c m_x), every product is below 2^59 units, and up
 //     to 16 of them sum without overflow in a signed 64-bit integer;
-//   * the integer sum is rounded once to FP64, to nearest, ties to even.
+//   * the integer sum is rounded once to FP64, to nearest, ties to even (on
+//     the device by the hardware int64 -> FP64 conversion, the frame's power
+//     of two added to the exponent field; on the host by integer rounding,
+//     with the same bits).
 //
 // Error: |result - exact| <= n 2^-57 max_k |c_k x_k| + 2^-53 |exact|
 // (truncation of n products, then one rounding), which is at or below the
@@ -178,6 +181,21 @@ TEUK_FX_HD bool fx_dot(const Fx *c, const Fx *x, const uint32_t *flip, double *o
         const uint64_t v = fx_shr(fx_prod47(c[k], x[k]), (uint32_t)(E - T[k]));
         acc += (c[k].neg ^ x[k].neg ^ flip[k]) ? (uint64_t)0 - v : v;
     }
+    // One rounding to nearest (ties to even) of the exact sum acc 2^(E - 2103);
+    // the sum applies when the rounded result's biased exponent ef lies in
+    // [200, 2045] (2^-823 <= |result| < 2^1023).
+#ifdef __CUDA_ARCH__
+    // the hardware int64 -> FP64 conversion rounds like the integer path
+    // below; the frame's power of two then goes onto the exponent field
+    if (acc == 0) {
+        *out = 0.0;
+        return braw < 0x7FFu;
+    }
+    const uint64_t cb = fx_bits(__ll2double_rn((long long)acc));
+    const int ef = (int)((cb >> 52) & 0x7FFu) + (E - 2103);
+    *out = fx_double(cb + ((uint64_t)(long long)(E - 2103) << 52));
+    return braw < 0x7FFu && ef >= 200 && ef <= 2045;
+#else
     const uint32_t neg = (uint32_t)(acc >> 63);
     const uint64_t mag = neg ? (uint64_t)0 - acc : acc;
     const int lz = fx_clz64(mag);
@@ -190,8 +208,10 @@ TEUK_FX_HD bool fx_dot(const Fx *c, const Fx *x, const uint32_t *flip, double *o
     // (eb - 1) 2^52 + m: the hidden bit lifts the exponent field to eb, and a
     // significand that rounds up to 2^53 carries into it
     const uint64_t r = (((uint64_t)(eb - 1) << 52) + m) | ((uint64_t)neg << 63);
+    const int ef = (int)((r >> 52) & 0x7FFu);
     *out = mag == 0 ? 0.0 : fx_double(r);
-    return braw < 0x7FFu && (mag == 0 || (eb >= 200 && eb <= 2045));
+    return braw < 0x7FFu && (mag == 0 || (ef >= 200 && ef <= 2045));
+#endif
 }
 
 // ---------------------------------------------------------------------------
