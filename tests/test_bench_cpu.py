@@ -83,11 +83,11 @@ def test_flop_and_instruction_counts_are_consistent():
 
 def test_issue_roofline_constants():
     # the ncu capture's warp instructions per launch of the 8192 x 128
-    # workload at step 40192: 894 thread instructions per mid-point and 1542 per node
+    # workload at step 40192: 851 thread instructions per mid-point and 1430 per node
     import bench
     pred = 32 * bench.NCU_TRAFFIC["predictor_inst"] / (8191 * 128)
     corr = 32 * bench.NCU_TRAFFIC["corrector_inst"] / (8190 * 128)
-    assert round(pred) == 894 and round(corr) == 1542
+    assert round(pred) == 851 and round(corr) == 1430
     assert bench.NUM_SMS * bench.ISSUE_PER_CLK_SM * 2.07e9 == pytest.approx(1.2586e12, rel=1e-4)
 
 
