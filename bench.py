@@ -63,13 +63,14 @@ ISSUE_PER_CLK_SM = 4
 # the FP64 pipe (20 instructions per update, adds and multiplies issued as
 # FMAs), the Pi rows as fixed-point sums of 38 exact integer products per
 # update on the integer pipes.  The dissipation adds 2 FP64 instructions (its
-# term in the Phi row), 2 products (its term in the Pi rows) and four exact
-# integer sixth differences per node.  Measured FP64 issue rate on GB300
-# (FMA-chain probe): 1.906 per clock per SM.
+# term in the Phi row) and four exact integer sixth differences per node; with
+# eps/64 a power of two (eps = 1 here) its term in the Pi rows enters their
+# fixed-point sums as an integer addend, not a product.  Measured FP64 issue
+# rate on GB300 (FMA-chain probe): 1.906 per clock per SM.
 FP64_INSTR_PER_UPDATE = 20
 FIXED_POINT_PRODUCTS_PER_UPDATE = 38
 FP64_INSTR_DISSIPATION = 2
-FIXED_POINT_PRODUCTS_DISSIPATION = 2
+FIXED_POINT_PRODUCTS_DISSIPATION = 0
 FP64_FMA_PER_CLK_SM = 1.906
 NUM_SMS = 152
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
