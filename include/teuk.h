@@ -227,7 +227,8 @@ int teuk_set_launch(teuk_handle *h, int rows_per_block);
  * complex planes.  Both give the same numbers. */
 #define TEUK_OPT_REAL_PATH 4
 /* TEUK_OPT_SPLIT_ROWS: r* rows per CTA tile of the split kernels; a tile is
- * up to 128 theta columns (a multiple of 32; wider rows are cut into tiles,
+ * up to 128 theta columns (16 for rows of at most 16 columns, else a
+ * multiple of 32; wider rows are cut into tiles,
  * the last one ragged), one thread per point.  1..128 / (tile width) with
  * the fixed-point Pi rows (their kernels launch at most 128 threads per CTA;
  * a larger height set earlier for FP64 is reduced to that), 1..512 / (tile

@@ -119,7 +119,7 @@ struct JobDesc {
     double2 *phiH, *piH;      // half step
     int cur;                  // buffer holding the state at the start of the slice
     int rows;                 // r* rows per tile
-    int tw;                   // theta columns per tile (a multiple of 32)
+    int tw;                   // theta columns per tile (16, 32, 64 or 128)
     int tiles;                // theta tiles per row
 };
 
@@ -191,8 +191,8 @@ cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long l
 cudaError_t launch_step_multi(const MultiArgs &a, int which, int real, int fixed_point, int ko, int block,
                               size_t smem, int ctas, int k, cudaStream_t st, bool pdl);
 const void *multi_kernel_ptr(int which, int real, int fixed_point, int ko);
-// Tile width of a job in a multi-job launch of `block`-thread CTAs: 32, 64
-// or 128 columns, dividing the CTA size.
+// Tile width of a job in a multi-job launch of `block`-thread CTAs: 16, 32,
+// 64 or 128 columns, dividing the CTA size.
 int multi_tile_width(int nth, int block);
 // Dynamic shared memory of a multi-job CTA for a job of tile width tw.
 size_t multi_smem_bytes(int tw, int block, int ko);

@@ -839,14 +839,16 @@ cudaError_t launch_step_unfused(const StepParams &p, const double2 *Phi, const d
 // and shared with the angular neighbours through shared memory.
 // ---------------------------------------------------------------------------
 
-// Split tiles: TW theta columns (a multiple of 32, at most 128) by R r* rows,
+// Split tiles: TW theta columns (16 for rows of at most 16 columns, else a
+// multiple of 32, at most 128) by R r* rows,
 // one thread per point.  Rows wider than a tile are cut into tiles of TW
 // columns, the last one ragged; each tile forms its two halo sums
 // sigma(j0 - 1) and sigma(j0 + TW) itself.  Small CTAs keep several tiles
 // resident per SM (the fixed-point Pi rows need up to 128 registers per
 // thread).
 constexpr int kSplitTileMax = 128;  // widest theta tile of the split kernels
-// Tile width for rows of nth columns, at most max_width: the multiple of 32
+// Tile width for rows of nth columns, at most max_width: 16 for nth <= 16,
+// otherwise the multiple of 32
 // (at least 64 unless nth <= 32) that wastes the fewest lanes in the ragged
 // last tile, less a penalty of 0.02 per 32 columns below 128 for the extra
 // halo sums and rows of narrower tiles.  Measured on GB300: 32000 x 304 runs
@@ -855,6 +857,7 @@ constexpr int kSplitTileMax = 128;  // widest theta tile of the split kernels
 // with 64 (both 100%).
 int tile_width_for(int nth, int max_width)
 {
+    if (nth <= 16) return 16;  // half-warp rows: 8 rows per 128-thread tile, no idle lanes
     if (nth <= 32 || max_width < 64) return 32;
     int best = 64;
     double best_score = -1.0;
@@ -1179,7 +1182,7 @@ int multi_tile_width(int nth, int block)
 {
     int best = 32;
     double best_score = -1.0;
-    for (int tw = 128; tw >= 32; tw /= 2) {
+    for (int tw = 128; tw >= 16; tw /= 2) {
         if (tw > block || block % tw) continue;
         const int lanes = (nth + tw - 1) / tw * tw;
         const double score = (double)nth / lanes - (tw < 128 ? 0.02 * (128 - tw) / 32 : 0.0);
