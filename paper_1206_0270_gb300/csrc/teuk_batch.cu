@@ -258,6 +258,7 @@ static int rebuild(teuk_batch *b)
     for (auto &g : b->groups) {
         g.ctas = 0;
         g.pred.sbuf_words = g.corr.sbuf_words = (int)(g.smem / sizeof(double2));
+        BCU(multi_allow_smem(g.real, g.fx, g.ko, g.smem));
         if (b->ctas_request > 0) {  // persistent: as many CTAs as stay resident, at most the request per SM
             int per_sm = b->ctas_request;
             for (int w = 0; w < 2; ++w) {

@@ -191,6 +191,9 @@ cudaError_t launch_nonfinite_count(const double2 *Phi, const double2 *Pi, long l
 cudaError_t launch_step_multi(const MultiArgs &a, int which, int real, int fixed_point, int ko, int block,
                               size_t smem, int ctas, int k, cudaStream_t st, bool pdl);
 const void *multi_kernel_ptr(int which, int real, int fixed_point, int ko);
+// Raise the multi-job kernels' dynamic shared-memory limit to `smem` per tile
+// (twice that for the persistent form) where it exceeds the 48 KB default.
+cudaError_t multi_allow_smem(int real, int fixed_point, int ko, size_t smem);
 // Tile width of a job in a multi-job launch of `block`-thread CTAs: 16, 32,
 // 64 or 128 columns, dividing the CTA size.
 int multi_tile_width(int nth, int block);

@@ -1125,6 +1125,16 @@ const void *split_kernel_ptr(int which, int real, int fixed_point, int ko)
 
 // part: 0 = predictor only, 1 = corrector only, 2 = both.  rows: r* rows per
 // CTA tile (0 = 256 / nth rounded to warps, at least 1).
+// Let kernel fn take `bytes` of dynamic shared memory: above the 48 KB default
+// a kernel launches only after its limit is raised (FP64 tiles of many rows
+// with the dissipation's staged rows; the persistent multi-job form's two
+// sets of rows).
+static cudaError_t allow_smem(const void *fn, size_t bytes)
+{
+    if (bytes <= 48u * 1024u) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const double2 *Pi, double2 *PhiO,
                               double2 *PiO, double2 *PhiH, double2 *PiH, int k, cudaStream_t st, bool pdl,
                               int part, int rows)
@@ -1146,6 +1156,8 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     cudaError_t e = cudaSuccess;
     if (part != 1) {
         cfg.gridDim = dim3((p.nr - 1 + R - 1) / R, tiles);
+        e = allow_smem(split_kernel_ptr(0, p.real_coef, p.fixed_point, p.ko), cfg.dynamicSmemBytes);
+        if (e != cudaSuccess) return e;
         e = cudaLaunchKernelEx(&cfg, TEUK_PICK(lw_predict_split, p.real_coef, p.fixed_point), p, Phi, Pi, PhiH, PiH,
                                k);
         if (e != cudaSuccess) return e;
@@ -1153,6 +1165,8 @@ cudaError_t launch_step_split(const StepParams &p, const double2 *Phi, const dou
     if (part != 0) {
         cfg.gridDim = dim3((p.nr - 2 + R - 1) / R, tiles);
         cfg.dynamicSmemBytes = split_smem_bytes(p.nth, R, p.ko);
+        e = allow_smem(split_kernel_ptr(1, p.real_coef, p.fixed_point, p.ko), cfg.dynamicSmemBytes);
+        if (e != cudaSuccess) return e;
         e = cudaLaunchKernelEx(&cfg, TEUK_PICK3(lw_correct_split, p.real_coef, p.fixed_point, p.ko), p, Phi, Pi,
                                (const double2 *)PhiH, (const double2 *)PiH, PhiO, PiO, k);
         if (e != cudaSuccess) return e;
@@ -1316,6 +1330,16 @@ static const void *multi_ptr(int which, int real, int fx, int ko, bool persist)
 const void *multi_kernel_ptr(int which, int real, int fixed_point, int ko)
 {
     return multi_ptr(which, real, fixed_point, ko, true);
+}
+
+cudaError_t multi_allow_smem(int real, int fixed_point, int ko, size_t smem)
+{
+    for (int w = 0; w < 2; ++w) {
+        cudaError_t e = allow_smem(multi_ptr(w, real, fixed_point, ko, false), smem);
+        if (e == cudaSuccess) e = allow_smem(multi_ptr(w, real, fixed_point, ko, true), 2 * smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_step_multi(const MultiArgs &a, int which, int real, int fixed_point, int ko, int block,

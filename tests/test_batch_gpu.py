@@ -375,3 +375,38 @@ def test_template_bank_at_full_size_every_launch_form(teuk):
             g.close()
         bad = [q for q in range(len(jobs)) if got[q] != alone[q]]
         assert not bad, (mode, ctas, bad[:10])
+
+
+def test_persistent_multi_job_fp64_rows_of_16_columns(teuk):
+    # FP64 jobs on rows of at most 16 columns in the persistent multi-job
+    # form: 16-column tiles of 16 rows, two sets of shared rows (54 KB per
+    # CTA, above the 48 KB default); every job equals itself stepped alone
+    specs = [dict(nr=n, nth=t, a=0.6, s=-2, m=2, steps=k, src=dict(r0=8.0, sigma=1.0), ext=(5.0, 3), eps=1.0)
+             for n, t, k in ((90, 16, 23), (140, 8, 31), (60, 12, 17))]
+
+    def build(q):
+        g, _ = make(teuk, specs[q], 500 + q)
+        g.set_option(teuk.TEUK_OPT_FIXED_POINT, 0)
+        return g, specs[q]
+    alone = []
+    for q in range(len(specs)):
+        g, j = build(q)
+        g.step(j["steps"])
+        alone.append(collect(g, j))
+        g.close()
+    for ctas in (0, 2):
+        B = teuk.Batch()
+        B.set_option(teuk.TEUK_OPT_BATCH_CTAS, ctas)
+        B.set_option(teuk.TEUK_OPT_BATCH_MODE, 0)
+        solvers = [build(q) for q in range(len(specs))]
+        for g, j in solvers:
+            B.add(g, j["steps"])
+        while B.step(10 ** 6):
+            pass
+        B.sync()
+        for (g, j), ref in zip(solvers, alone):
+            for x, y in zip(collect(g, j), ref):
+                np.testing.assert_array_equal(x, y)
+        B.close()
+        for g, _ in solvers:
+            g.close()

@@ -678,3 +678,32 @@ def test_device_allocation_failure_is_reported(teuk):
     g.step(4)
     assert g.check_finite()
     g.close()
+
+
+def test_fp64_tiles_of_many_rows_with_dissipation(teuk):
+    # FP64 Pi rows on rows of 16 columns: 16-column tiles of 32 rows stage the
+    # dissipation's rows in 54 KB of shared memory per CTA (above the 48 KB
+    # default).  Same bits as the default tile height, and the oracle's result.
+    nr, nth, a, s, m = 300, 16, 0.7, -2, 2
+    dt = O.stable_dt(nr, nth, -20.0, 40.0, a, s, m, 0.5, 0.8)
+    phi0, pi0 = inputs.random_fields(nr, nth, seed=16)
+    out = []
+    for rows in (0, 32):
+        g = teuk.Solver(nr, nth, -20.0, 40.0, dt, a, s, m)
+        g.set_option(teuk.TEUK_OPT_FIXED_POINT, 0)
+        g.set_option(teuk.TEUK_OPT_SPLIT_ROWS, rows)
+        g.set_dissipation(1.0)
+        g.set_initial(phi0, pi0)
+        g.set_source(r0=8.0, sigma=0.5)
+        g.step(101)
+        out.append(g.state())
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        np.testing.assert_array_equal(x, y)
+    ora = O.Solver(nr, nth, -20.0, 40.0, dt, a, s, m)
+    ora.set_dissipation(1.0)
+    ora.set_initial(phi0, pi0)
+    ora.set_source(r0=8.0, sigma=0.5)
+    ora.step(101)
+    for x, y in zip(out[1], ora.state()):
+        assert abs(x - y).max() <= 1e-10 * abs(y).max()
