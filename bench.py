@@ -636,7 +636,7 @@ def batch_result(T, kind, scale, batch_mode="auto"):
         if form == "auto":
             best = B.autotune()
         else:
-            best = {"1": 0, "0": 1, "p": 2}[form]
+            best = {"1": 0, "0": 1, "p": 3}[form]
             B.set_option(T.TEUK_OPT_BATCH_CTAS, 8 if form == "p" else 0)
             B.set_option(T.TEUK_OPT_BATCH_MODE, 1 if form == "1" else 0)
         launches = B.launches_for(1)

@@ -355,12 +355,13 @@ int teuk_batch_sync(teuk_batch *b);
  * TEUK_OPT_BATCH_CTAS (mode 0) or TEUK_OPT_BATCH_MODE. */
 int teuk_batch_set_option(teuk_batch *b, int option, long value);
 
-/* Time the launch forms on the batch's own jobs -- per-job launches, the
- * multi-job launches with one CTA per tile, and the persistent multi-job
- * launches -- and keep the fastest (TEUK_OPT_BATCH_MODE and
- * TEUK_OPT_BATCH_CTAS are set accordingly); the timed steps count as
- * progress.  *best (may be NULL) receives 0, 1 or 2 for those three forms.
- * Synchronises. */
+/* Time the launch forms and tile shapes on the batch's own jobs -- per-job
+ * launches, the multi-job launches with one CTA per tile at the default CTA
+ * size and at 64 threads (tiles of at most 64 theta columns, fewer rows),
+ * and the persistent multi-job launches -- and keep the fastest
+ * (TEUK_OPT_BATCH_MODE, TEUK_OPT_BATCH_CTAS and TEUK_OPT_BLOCK_THREADS are
+ * set accordingly); the timed steps count as progress.  *best (may be NULL)
+ * receives 0, 1, 2 or 3 for those four.  Synchronises. */
 int teuk_batch_autotune(teuk_batch *b, int *best);
 
 /* Kernel launches that teuk_batch_step(b, n) issues when no job finishes. */

@@ -457,17 +457,19 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best)
         if (rc) return rc;
     }
     if (b->active.empty()) return bfail(b, TEUK_ERR_STATE, "teuk_batch_autotune: no job has steps left");
-    // per-job launches, multi-job launches with one CTA per tile, and the
-    // persistent multi-job launch (resident CTAs); each candidate gets an
-    // equal share of the steps the shortest job has left
-    const int cands[][2] = {{1, 0}, {0, 0}, {0, 64}};  // {mode, CTAs per SM}
+    // per-job launches, multi-job launches with one CTA per tile in two tile
+    // shapes (the default CTA size, and 64-thread CTAs: tiles of at most 64
+    // columns, fewer rows), and the persistent multi-job launch (resident
+    // CTAs); each candidate gets an equal share of the steps the shortest job
+    // has left
+    const int cands[][3] = {{1, 0, 0}, {0, 0, 0}, {0, 0, 64}, {0, 64, 0}};  // {mode, CTAs per SM, CTA threads}
     const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
     long long share = 1LL << 62;
     for (int id : b->active) share = std::min(share, b->jobs[id].remaining / ncand);
     cudaEvent_t e0, e1;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));
-    int best_c = b->mode == 1 ? 0 : (b->ctas_request ? 2 : 1);
+    int best_c = b->mode == 1 ? 0 : (b->ctas_request ? 3 : (b->block_request == 64 ? 2 : 1));
     double best_rate = -1.0;
     for (int ci = 0; ci < ncand; ++ci) {
         const auto &c = cands[ci];
@@ -480,7 +482,10 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best)
         const long long budget = std::min(share, minrem) & ~1LL;
         if (b->active.empty() || budget < 8) break;
         b->mode = c[0];
-        if (c[0] == 0) b->ctas_request = c[1];
+        if (c[0] == 0) {
+            b->ctas_request = c[1];
+            b->block_request = c[2];
+        }
         b->layout_dirty = true;
         int rc = rebuild(b);
         if (rc) return rc;
@@ -511,7 +516,10 @@ extern "C" int teuk_batch_autotune(teuk_batch *b, int *best)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->mode = cands[best_c][0];
-    if (b->mode == 0) b->ctas_request = cands[best_c][1];
+    if (b->mode == 0) {
+        b->ctas_request = cands[best_c][1];
+        b->block_request = cands[best_c][2];
+    }
     b->layout_dirty = true;
     if (best) *best = best_c;
     return TEUK_OK;

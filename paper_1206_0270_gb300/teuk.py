@@ -35,7 +35,8 @@ TEUK_OPT_SPLIT_ROWS = 5
 TEUK_OPT_BATCH_MODE = 6
 TEUK_OPT_FIXED_POINT = 7
 TEUK_OPT_BATCH_CTAS = 8
-BATCH_FORMS = ("per-job launches", "multi-job launches, one CTA per tile", "persistent multi-job launches")
+BATCH_FORMS = ("per-job launches", "multi-job launches, one CTA per tile",
+               "multi-job launches, one CTA per tile, 64-thread tiles", "persistent multi-job launches")
 ERRORS = {-1: "TEUK_ERR_BAD_ARG", -2: "TEUK_ERR_OOM", -3: "TEUK_ERR_CUDA", -4: "TEUK_ERR_NONFINITE",
           -5: "TEUK_ERR_STATE", -6: "TEUK_ERR_OVERFLOW"}
 

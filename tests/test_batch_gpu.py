@@ -102,7 +102,7 @@ def test_batch_in_slices_remove_and_autotune(teuk):
         solvers.append(g)
         B.add(g, j["steps"])
     best = B.autotune()          # timed steps count as progress
-    assert best in (0, 1, 2)
+    assert best in (0, 1, 2, 3)
     B.step(5)
     B.set_option(teuk.TEUK_OPT_BATCH_MODE, 0)  # switch modes mid-run, odd slices
     B.step(33)
