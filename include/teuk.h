@@ -293,8 +293,8 @@ long teuk_launches_for(const teuk_handle *h, long n);
  * return TEUK_ERR_BAD_ARG).  All calls share that array and it keeps the last
  * call's contents, so calls that overlap on the GPU (different streams or
  * handles running at once) race: issue them one after another on one stream.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress, a synchronous runtime call.
  * The handle's device must be the current device. */
 int teuk_step_noalloc(teuk_handle *h, const double *phi_in, const double *pi_in, double *phi_out,
                       double *pi_out, long step_index);
