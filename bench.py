@@ -73,6 +73,9 @@ FP64_INSTR_DISSIPATION = 2
 FIXED_POINT_PRODUCTS_DISSIPATION = 0
 FP64_FMA_PER_CLK_SM = 1.906
 NUM_SMS = 152
+# --batch-mode letters -> index into the binding's BATCH_FORMS (the index
+# teuk_batch_autotune reports): per-job, multi-job one CTA per tile, persistent
+BATCH_FORM_INDEX = {"1": 0, "0": 1, "p": 3}
 # DRAM bytes (read + write) per launch of each step kernel from one ncu capture
 # of the split kernels on the 8192 x 128 workload at step 40192 (a developed
 # field), valid for the kernel and launch sources whose SHA-256 is recorded
@@ -636,7 +639,7 @@ def batch_result(T, kind, scale, batch_mode="auto"):
         if form == "auto":
             best = B.autotune()
         else:
-            best = {"1": 0, "0": 1, "p": 3}[form]
+            best = BATCH_FORM_INDEX[form]
             B.set_option(T.TEUK_OPT_BATCH_CTAS, 8 if form == "p" else 0)
             B.set_option(T.TEUK_OPT_BATCH_MODE, 1 if form == "1" else 0)
         launches = B.launches_for(1)

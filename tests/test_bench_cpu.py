@@ -103,3 +103,13 @@ def test_run_gpu_does_not_rebind_the_clock_sampler():
     withs = [it.optional_vars.id for node in ast.walk(tree) if isinstance(node, ast.With) for it in node.items
              if isinstance(it.optional_vars, ast.Name)]
     assert targets.count("clk") + withs.count("clk") == 1, (targets.count("clk"), withs.count("clk"))
+
+
+def test_batch_form_letters_name_the_binding_forms():
+    # each --batch-mode letter must label its results with the form it runs
+    from paper_1206_0270_gb300 import teuk as T
+    names = {k: T.BATCH_FORMS[i] for k, i in bench.BATCH_FORM_INDEX.items()}
+    assert names["1"].startswith("per-job")
+    assert names["0"] == "multi-job launches, one CTA per tile"
+    assert names["p"].startswith("persistent")
+    assert len(T.BATCH_FORMS) == 4
