@@ -184,8 +184,8 @@ def run_reference(args):
     upd, times = oracle_rate(per, args.steps, warmup=args.warmup)
     total = sum(times)
     value = upd * args.steps / total
-    sample = ("FP64 C oracle (OpenMP over r* rows), 8192x128 Kerr a=0.9 grid with source, "
-              "%d time steps per benchmark step" % per)
+    sample = ("FP64 C oracle (OpenMP over r* rows), 8192x128 Kerr a=0.9 grid with source and angular "
+              "dissipation (eps = 1), %d time steps per benchmark step" % per)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * total / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
@@ -501,7 +501,7 @@ def run_gpu(args):
         upd, times = oracle_rate(per, 1)
         line["cpu_baseline"] = dict(value=upd / times[0], unit=UNIT, cores=cores_used(), kind="oracle",
                                     sample="%d time steps of the 8192x128 workload grid, FP64 C oracle "
-                                           "(OpenMP over r* rows)" % per)
+                                           "(OpenMP over r* rows), source and angular dissipation (eps = 1)" % per)
     print(json.dumps(line), flush=True)
     S.close()
     return 0
