@@ -254,7 +254,9 @@ TEUK_FX_HD FxP fx_prep(double x)
 
 
 // RN(D 2^k) for |D| < 2^63 and D 2^k below the FP64 overflow threshold,
-// subnormal results included.
+// subnormal results included.  For a sixth difference (D from fx_d6_int,
+// k = F - 1079) a subnormal result is always exact: F <= 4 there, and every
+// aligned term is a multiple of 2^(5 - F), the subnormal branch's shift.
 TEUK_FX_HD double fx_ldexp_rn(long long D, int k)
 {
     if (D == 0) return 0.0;
