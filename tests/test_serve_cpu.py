@@ -13,6 +13,10 @@ import pytest
 
 from paper_1206_0270_gb300 import serve as S
 
+# a scheduling mistake can leave the service loop waiting for work that never
+# finishes; each test ends within seconds when the logic is right
+pytestmark = pytest.mark.timeout(120)
+
 
 class FakeSolver:
     def __init__(self, nr, nth, rstar_min, rstar_max, dt, a, s, m, stream=None):
