@@ -74,3 +74,30 @@ def test_bad_arguments_are_rejected_without_gpu(lib):
 def test_launch_count_null_handle(lib):
     assert lib.teuk_launches_for(None, 10) == -1
     assert lib.teuk_step_count(None) == -1
+
+
+def test_every_entry_point_rejects_null_objects_without_gpu(lib):
+    # Each call given a NULL handle, batch or output pointer reports
+    # TEUK_ERR_BAD_ARG (-1 for the counting calls, an empty message for the
+    # error-text calls) before it touches the device or dereferences anything.
+    import ctypes as C
+    zero = {C.c_int: 0, C.c_long: 0, C.c_double: 0.0, C.c_uint: 0}
+    special = {
+        "teuk_strerror": None,              # takes a code, not an object
+        "teuk_fixed_dot": ((0, 0, 1, None, None, None, None, None), -1),   # nterms 0
+        "teuk_fixed_d6": ((0, -1, None, None), -1),                        # count < 0
+    }
+    seen = []
+    for name in lib.EXPORTED:
+        f = getattr(lib, name)
+        if name in special:
+            if special[name] is None:
+                continue
+            args, want = special[name]
+        else:
+            args = tuple(zero.get(t) for t in f.argtypes)   # None for every pointer
+            want = b"" if f.restype is C.c_char_p else -1
+        assert f(*args) == want, name
+        seen.append(name)
+    assert len(seen) == len(lib.EXPORTED) - 1
+    assert lib.teuk_strerror(0).decode() == "ok"
