@@ -101,3 +101,26 @@ def test_every_entry_point_rejects_null_objects_without_gpu(lib):
         seen.append(name)
     assert len(seen) == len(lib.EXPORTED) - 1
     assert lib.teuk_strerror(0).decode() == "ok"
+
+
+def test_no_cpu_fallback(lib, tmp_path):
+    # The binding refuses to load without libteuk.so, and without a GPU the
+    # product calls fail with an error instead of computing on the host.
+    import importlib.util
+    import shutil
+    pkg = tmp_path / "nolib"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_1206_0270_gb300", "teuk.py"), pkg / "teuk.py")
+    spec = importlib.util.spec_from_file_location("teuk_without_library", str(pkg / "teuk.py"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        spec.loader.exec_module(importlib.util.module_from_spec(spec))
+    try:
+        g = lib.Solver(64, 8, -10.0, 10.0, 0.01, 0.5, -2, 2)
+    except lib.TeukError as e:
+        assert e.code == -3                                   # TEUK_ERR_CUDA: no device here
+    else:
+        g.close()
+        pytest.skip("a GPU is present: the device path ran")
+    with pytest.raises(lib.TeukError) as e:
+        lib.fixed_d6(np.ones((2, 7)), device=True)            # never served by the host build
+    assert e.value.code == -3
