@@ -476,35 +476,50 @@ def run_gpu(args):
         # step counts: batched waveforms/s against one job at a time, and the
         # serving stream's latency
         from paper_1206_0270_gb300 import inputs, serve as SV
-        line["batched"] = [batch_result(T, "batch_modes", 0.2, "all"), batch_result(T, "template_bank", 0.01, "all"),
-                           batch_result(T, "small_bank", 0.2, "all")]
-        line["serving"] = serving_result(T, SV, inputs.serving_requests(64, 4.0), slice_steps=640,
-                                         fill_points=2_000_000, memory_gb=200.0, policies=("async", "async-remaining"))
-        line["serving"].update(rate_per_s=4.0, step_fraction=1.0, steps="logU[1e3, 1e4]")
+        line["batched"] = optional_block(lambda: [
+            batch_result(T, "batch_modes", 0.2, "all"), batch_result(T, "template_bank", 0.01, "all"),
+            batch_result(T, "small_bank", 0.2, "all")])
+        line["serving"] = optional_block(lambda: dict(
+            serving_result(T, SV, inputs.serving_requests(64, 4.0), slice_steps=640, fill_points=2_000_000,
+                           memory_gb=200.0, policies=("async", "async-remaining")),
+            rate_per_s=4.0, step_fraction=1.0, steps="logU[1e3, 1e4]"))
         # a long request on the GPU while short ones arrive: 32 requests at
         # 4/s, the first an 8192 x 128 job of 1e5 steps
-        line["serving_long_tail"] = serving_result(
-            T, SV, inputs.serving_requests(32, 4.0, long_tail=1, long_steps=(1e5, 1e5), long_grids=((8192, 128),),
-                                           long_weights=None),
-            slice_steps=640, fill_points=2_000_000, memory_gb=200.0, policies=("async-remaining", "async"))
-        line["serving_long_tail"].update(rate_per_s=4.0, steps="logU[1e3, 1e4]; first request 8192x128, 1e5 steps")
+        line["serving_long_tail"] = optional_block(lambda: dict(
+            serving_result(T, SV, inputs.serving_requests(32, 4.0, long_tail=1, long_steps=(1e5, 1e5),
+                                                          long_grids=((8192, 128),), long_weights=None),
+                           slice_steps=640, fill_points=2_000_000, memory_gb=200.0,
+                           policies=("async-remaining", "async")),
+            rate_per_s=4.0, steps="logU[1e3, 1e4]; first request 8192x128, 1e5 steps"))
         # many small requests at once (overload): 128 requests at 200/s on
         # 256..512 x 16..32 grids, 2e3..8e3 steps each
         small = dict(grids=((256, 16), (256, 32), (512, 16), (512, 32)), grid_weights=(1, 1, 1, 1),
                      step_range=(2e3, 8e3))
-        line["serving_small"] = serving_result(
-            T, SV, inputs.serving_requests(128, 200.0, **small), slice_steps=640, fill_points=2_000_000,
-            memory_gb=200.0, policies=("fill+multi", "share+multi", "async"))
-        line["serving_small"].update(rate_per_s=200.0, grids="256..512 x 16..32", steps="logU[2e3, 8e3]")
+        line["serving_small"] = optional_block(lambda: dict(
+            serving_result(T, SV, inputs.serving_requests(128, 200.0, **small), slice_steps=640,
+                           fill_points=2_000_000, memory_gb=200.0, policies=("fill+multi", "share+multi", "async")),
+            rate_per_s=200.0, grids="256..512 x 16..32", steps="logU[2e3, 8e3]"))
     if ws == 1 and not args.no_cpu_baseline:
-        per = args.cpu_sample_steps
-        upd, times = oracle_rate(per, 1)
-        line["cpu_baseline"] = dict(value=upd / times[0], unit=UNIT, cores=cores_used(), kind="oracle",
-                                    sample="%d time steps of the 8192x128 workload grid, FP64 C oracle "
-                                           "(OpenMP over r* rows), source and angular dissipation (eps = 1)" % per)
+        def cpu_baseline():
+            per = args.cpu_sample_steps
+            upd, times = oracle_rate(per, 1)
+            return dict(value=upd / times[0], unit=UNIT, cores=cores_used(), kind="oracle",
+                        sample="%d time steps of the 8192x128 workload grid, FP64 C oracle "
+                               "(OpenMP over r* rows), source and angular dissipation (eps = 1)" % per)
+        line["cpu_baseline"] = optional_block(cpu_baseline)
     print(json.dumps(line), flush=True)
     S.close()
     return 0
+
+
+def optional_block(fn):
+    """Run one part of the bench line that follows the measured headline
+    (batched and serving blocks, the CPU baseline).  An exception there is
+    recorded in the line as {"error": ...} instead of losing the line."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 -- any failure of an optional part
+        return {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
 
 
 def run_hbm_probe(T, stream, ws, hbm_peak, hbm_src, same_src, chunk=64, reps=6):

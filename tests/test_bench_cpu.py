@@ -113,3 +113,14 @@ def test_batch_form_letters_name_the_binding_forms():
     assert names["0"] == "multi-job launches, one CTA per tile"
     assert names["p"].startswith("persistent")
     assert len(T.BATCH_FORMS) == 4
+
+
+def test_optional_block_keeps_the_line_when_a_part_fails():
+    assert bench.optional_block(lambda: dict(value=1.0)) == dict(value=1.0)
+
+    def broken():
+        raise RuntimeError("CUDA error: out of memory")
+    out = bench.optional_block(broken)
+    assert out == {"error": "RuntimeError: CUDA error: out of memory"}
+    import json
+    json.dumps({"value": 1.0, "serving": out})                 # still one printable JSON line
