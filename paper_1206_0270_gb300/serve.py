@@ -376,11 +376,19 @@ class WaveformService:
         return self.results
 
     def close(self):
+        """Release every job still admitted and the service's batch; safe to
+        call more than once."""
         self._pool.shutdown(wait=True)
         self.batch.close()          # releases the handles, which are then destroyed
         for st in self._running.values():
             st["solver"].close()
         self._running.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def latency_stats(results) -> dict:

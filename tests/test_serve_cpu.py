@@ -358,3 +358,14 @@ def test_batch_mode_option_reaches_the_batch(fake):
     svc = S.WaveformService(memory_budget=1 << 34, slice_steps=20, clock=Clock(), policy="share")
     assert FakeLib.TEUK_OPT_BATCH_MODE not in FakeBatch.made[-1].options
     svc.close()
+
+
+def test_service_as_context_manager_releases_jobs(fake):
+    # leaving the block early (here after one step) closes every admitted job
+    with S.WaveformService(memory_budget=1 << 40, slice_steps=20, clock=Clock(), policy="share") as svc:
+        for k in range(3):
+            svc.submit(request(steps=200))
+        svc.step()
+        assert svc.running() == 3
+    assert svc.running() == 0 and all(s.closed for s in fake)
+    svc.close()                                  # a second close is harmless
