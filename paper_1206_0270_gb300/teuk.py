@@ -318,6 +318,12 @@ class Batch:
     def __del__(self):
         self.close()
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def add(self, solver, steps):
         jid = C.c_int()
         _bcheck(teuk_batch_add(self.b, solver.h, int(steps), C.byref(jid)), self.b, "teuk_batch_add")
