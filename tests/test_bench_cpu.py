@@ -124,3 +124,23 @@ def test_optional_block_keeps_the_line_when_a_part_fails():
     assert out == {"error": "RuntimeError: CUDA error: out of memory"}
     import json
     json.dumps({"value": 1.0, "serving": out})                 # still one printable JSON line
+
+
+def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
+    # `bench.py --impl reference` times the oracle on the host cores and prints
+    # one JSON line with the headline metric, impl, cpu_baseline and a
+    # copy-free e2e block (here 2 timed steps of 2 oracle time steps each)
+    import argparse
+    import json
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    args = argparse.Namespace(steps=2, warmup=1, ref_steps=2)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == dict(value=line["value"], unit=bench.UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0)
