@@ -144,3 +144,12 @@ def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == dict(value=line["value"], unit=bench.UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+
+
+def test_reference_arm_other_ranks_exit_quietly(capsys, monkeypatch):
+    import argparse
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.run_reference(argparse.Namespace(steps=2, warmup=1, ref_steps=2)) == 0
+    assert capsys.readouterr().out == ""
