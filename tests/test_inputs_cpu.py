@@ -135,3 +135,18 @@ def test_kerr_workload_outer_boundary_stays_out_of_causal_contact():
     t_reflect = (w["rstar_max"] - r_src) + (w["rstar_max"] - w["extraction"]["rstar"])
     assert t_reflect == pytest.approx(1490.0, abs=10.0)
     assert t_end < t_reflect
+
+
+def test_mode_batch_and_workload_table():
+    # the mode batch: one a = 0.7, r0 = 8 orbit, m = 1..8 on 4096 r* points with
+    # the theta resolution doubling every two modes, 5e4 steps
+    mb = I.MODE_BATCH
+    assert (mb["a"], mb["r0"], mb["nr"], mb["steps"]) == (0.7, 8.0, 4096, 50000)
+    assert [m for m, _ in mb["modes"]] == list(range(1, 9))
+    assert [n for _, n in mb["modes"]] == [32, 32, 64, 64, 128, 128, 256, 256]
+    # every workload uses the dissipative step rule and keeps its observer
+    # inside the grid
+    for name, w in I.WORKLOADS.items():
+        assert (w["c_r"], w["c_theta"], w["eps"]) == (0.5, 0.8, 1.0), name
+        assert w["rstar_min"] < w["extraction"]["rstar"] < w["rstar_max"], name
+        assert name.endswith("%dx%d" % (w["nr"], w["nth"])) or "%dx%d_" % (w["nr"], w["nth"]) in name, name
