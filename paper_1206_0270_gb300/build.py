@@ -3,7 +3,11 @@
     python -m paper_1206_0270_gb300.build [--verbose]
 
 Compiles csrc/*.cu in parallel to objects under _build/ and links them into
-paper_1206_0270_gb300/libteuk.so (CUDA runtime linked statically).
+paper_1206_0270_gb300/libteuk.so (CUDA runtime linked statically).  The
+command line always rebuilds; build() from Python rebuilds only when a source
+is newer than the library.  Extra nvcc flags may be given in the environment
+variable TEUK_NVCC_EXTRA (for example "-Xptxas -v" to print register and
+shared-memory use); they take effect on the next full rebuild.
 """
 from __future__ import annotations
 
